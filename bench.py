@@ -1,0 +1,370 @@
+"""Benchmark of libsgrcolor on one node (one process per GPU).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20]
+                    [--mode det|fast] [--impl ours|reference]
+
+A step is one complete coloring (all rounds of Algorithm 7) of the workload
+graph, inputs already resident in HBM.  The headline metric is GTEPS: the
+edges scanned by FirstFit summed over all rounds (sum of |adj(v)| over v in
+W_r, over r), divided by the device time of the step; the color count is
+reported against serial first-fit greedy.  Every rank runs its own replica
+(coloring one graph has no data-path exchange), so the whole-job value is the
+sum of the ranks' work over the slowest rank's time ("scaling": "weak").
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the stream the library launches on; the L2 cache is flushed (a 512 MiB
+write) before every step, outside the events.  SM clocks and throttle reasons
+are sampled with nvidia-smi during the timed steps.
+
+--impl reference times the CPU oracle (the only reference this method has:
+the paper publishes no code) on the host cores, on the same workload, metric
+and unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import graphgen as gg  # noqa: E402
+
+METRIC_SINGLE = "GTEPS & #colors vs serial greedy"
+HBM_FALLBACK_GBS = 6800.0
+
+WORKLOADS = {
+    "rmat20": ("RMAT scale 20, edge factor 16, (0.57,0.19,0.19,0.05), ids permuted, seed 0",
+               lambda: gg.rmat20(0)),
+    "stencil192": ("3-D 27-point stencil 192^3, natural order", lambda: gg.stencil27(192)),
+    "er20k": ("uniform random graph n=20,000, average degree 10, seed 0", lambda: gg.er20k(0)),
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1606_06025_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(workload, mode):
+    """DRAM bytes per launch from a committed ncu summary, only if it was taken
+    on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(f"{workload}:{mode}")
+    if not e or e.get("kernel_sources") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def alg_bytes(st, n, m):
+    """Algorithmic DRAM bytes of one coloring launch (the byte model):
+    per worklist vertex and round 36 B (worklist entry read twice, row offsets
+    twice, own color read, tentative write, commit write), 4 B per entry
+    scanned by FirstFit, 4 B per entry ConflictResolve inspects, 4 B per pushed
+    loser, plus the init pass (4 B per entry for the order check, 12 B per
+    vertex).  Neighbour color gathers hit the L2-resident colors array and
+    are not counted."""
+    return (36 * st["sum_w"] + 4 * st["sum_d"] + 4 * st["sum_dscan"] + 4 * st["sum_next"]
+            + 4 * m + 12 * n)
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_info():
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                model = ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return model, os.cpu_count()
+
+
+def oracle_baseline(g, budget_s=12.0):
+    """The CPU oracle as it stands, single-threaded: det-SGR (what the GPU's
+    det mode computes) and serial first-fit greedy (the paper's Serial)."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.det_sgr(g)
+    t_det = time.perf_counter() - t0
+    runs = [t_det]
+    while sum(runs) + t_det < budget_s and len(runs) < 5:
+        t0 = time.perf_counter()
+        oracle.det_sgr(g)
+        runs.append(time.perf_counter() - t0)
+    ts = []
+    k_serial = 0
+    while sum(ts) < 2.0 and len(ts) < 10:
+        t0 = time.perf_counter()
+        _, k_serial = oracle.serial_greedy(g)
+        ts.append(time.perf_counter() - t0)
+    return r, statistics.median(runs), len(runs), statistics.median(ts), k_serial
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    desc, make = WORKLOADS[args.workload]
+    g = make()
+    import oracle
+    # warm-up and timed steps: each step is one full det-SGR run of the oracle
+    for _ in range(args.warmup):
+        oracle.det_sgr(g)
+    times = []
+    r = None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.det_sgr(g)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = r.sum_d * args.steps / total / 1e9
+    model, ncpu = cpu_info()
+    line = {
+        "impl": "reference", "metric": METRIC_SINGLE, "value": value, "unit": "GTEPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": g.n, "m": g.m,
+                   "mode": "det", "parallelism": "none (host CPU)"},
+        "num_colors": r.num_colors, "rounds": r.rounds,
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"full det-SGR run of the {args.workload} workload per step",
+                         "cpu": model, "host_cpus": ncpu},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_1606_06025_gb300 import sgrcolor as lib
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    desc, make = WORKLOADS[args.workload]
+    g = make()
+    n, m = g.n, g.m
+    ro = torch.from_numpy(g.row_offsets).to(dev)
+    ci = torch.from_numpy(g.col_idx).to(dev)
+    colors = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    mode = args.mode
+
+    def step():
+        return lib.sgr_color(n, ro, ci, colors, mode, stream)
+
+    for _ in range(max(args.warmup, 0)):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, kern_ms, stats = [], [], []
+    k = 0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        k = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = lib.sgr_last_stats()
+        stats.append(st)
+        kern_ms.append(st["device_ms"])
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    st = stats[-1]
+    work = st["sum_d"] * args.steps * world
+    value = work / (total_ms * 1e-3) / 1e9
+    # end to end through the host-buffer entry: H2D of the CSR, coloring, D2H of colors
+    ro_h = torch.from_numpy(g.row_offsets).pin_memory().numpy()
+    ci_h = torch.from_numpy(g.col_idx).pin_memory().numpy()
+    col_h = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lib.sgr_color_host(n, ro_h, ci_h, col_h, mode, stream)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = st["sum_d"] * args.steps * world / (e2e_total * 1e-3) / 1e9
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peak, peak_src = read_peaks()
+    kmean = statistics.mean(kern_ms)
+    ab = alg_bytes(st, n, m)
+    achieved = ab / (kmean * 1e-3) / 1e9
+    line = {
+        "metric": METRIC_SINGLE, "value": value, "unit": "GTEPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": n, "m": m, "mode": mode,
+                   "l2": "flushed (512 MiB write) before every step",
+                   "parallelism": f"replicas x{world}"},
+        "num_colors": k, "rounds": st["rounds"], "sum_d": st["sum_d"],
+        "useful_gteps": m / (total_ms / args.steps * 1e-3) / 1e9,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "GTEPS", "ms_per_step": e2e_total / args.steps,
+                "h2d_bytes_per_step": 4 * (n + 1) + 4 * m, "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": args.steps * 1,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": read_traffic(args.workload, mode),
+                     "alg_bytes_per_launch": ab, "kernel_ms": kmean,
+                     "kernel": "sgr_color_kernel", "peak_source": peak_src + " of measured"
+                     if peak_src.startswith("measured") else peak_src},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        r, t_det, runs, t_serial, k_serial = oracle_baseline(g)
+        model, ncpu = cpu_info()
+        line["cpu_baseline"] = {
+            "value": r.sum_d / t_det / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{runs} full det-SGR runs of the workload (median), single thread",
+            "cpu": model, "host_cpus": ncpu,
+            "serial_greedy_ms": t_serial * 1e3, "serial_greedy_colors": k_serial,
+        }
+        line["serial_greedy_colors"] = k_serial
+        line["colors_vs_serial"] = k / k_serial if k_serial else None
+        line["speedup_vs_serial_greedy"] = t_serial * 1e3 / (total_ms / args.steps)
+        if mode == "det":
+            line["det_matches_oracle"] = bool(
+                np.array_equal(colors.cpu().numpy(), r.colors))
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="rmat20")
+    ap.add_argument("--mode", choices=["det", "fast"], default="det")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * sgrcolor.h -- C ABI of libsgrcolor: data-driven speculative-greedy (SGR)
+ * graph coloring on one GB300 GPU.
+ *
+ * The method (X. Chen et al., "Efficient and High-quality Sparse Graph
+ * Coloring on GPUs", Sect. 3, Algorithms 4, 5 and 7): keep a worklist W of
+ * uncolored vertices; each round gives every vertex of W the smallest color
+ * c >= 1 that none of its neighbours holds (FirstFit, Algorithm 4), then finds
+ * adjacent pairs of W that picked the same color (ConflictResolve,
+ * Algorithm 5); one vertex of each such pair is cleared and pushed onto the
+ * next worklist (Algorithm 7).  The loop ends when the worklist is empty.
+ *
+ * Graphs are undirected, given as symmetric CSR: row_offsets[n+1] (int32,
+ * row_offsets[0] == 0, non-decreasing) and col_idx[m] (int32, m =
+ * row_offsets[n] directed entries, each in [0, n)).  No self-loops, no
+ * duplicate entries in a row (Sect. 3: R and C arrays).  Rows need not be
+ * sorted; sorted rows are detected on the device and let ConflictResolve
+ * stop at the first neighbour above the vertex.
+ * Colors come back as int32 values 1..k, k = number of colors (Sect. 2.1:
+ * 0 means uncolored and never appears in a result).
+ *
+ * Modes (the `mode` argument is an OR of one SGR_MODE_* and one SGR_RULE_*):
+ *   SGR_MODE_DETERMINISTIC: every FirstFit of a round reads the colors fixed
+ *     at the start of the round, and conflicts are judged on all tentative
+ *     colors of the round before any is cleared.  The result depends only on
+ *     the graph and the rule, and equals the CPU oracle bit for bit.
+ *   SGR_MODE_FAST: FirstFit and ConflictResolve read and write colors in
+ *     place while other vertices of the round do the same, as the paper's GPU
+ *     code does (Sect. 3.1, "Color Clearing").  Always a valid coloring; the
+ *     exact colors may change from run to run.
+ *   SGR_RULE_LOW_KEEPS (default): of two neighbours with the same color, the
+ *     lower vertex id keeps it.
+ *   SGR_RULE_LOW_LOSES: the lower id is recolored, as printed in Algorithm 2
+ *     and Algorithm 5.
+ *   SGR_RULE_DEGREE: the heuristic of Sect. 3.2: the larger degree keeps the
+ *     color; on equal degree the smaller id keeps it.
+ *
+ * Ownership and memory: the caller owns every input and output buffer.  The
+ * library keeps a per-device scratch arena (worklists, counters, bitmaps),
+ * grown on demand and never shrunk, released by sgr_release_scratch().
+ * Errors: every entry point returns an sgr_status; on error, output
+ * parameters other than the status are left unspecified.
+ * Threads: calls on different host threads may run concurrently only on
+ * different devices; calls on one device are serialised by the library.
+ */
+#ifndef SGRCOLOR_H
+#define SGRCOLOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle (cudaStream_t / CUstream); NULL is the legacy default
+ * stream of the calling thread. */
+typedef struct CUstream_st *sgr_stream_t;
+
+typedef enum {
+    SGR_OK = 0,
+    SGR_PENDING = 1,               /* server: request not finished yet */
+    SGR_ERR_INVALID_ARG = -1,      /* bad pointer, size, mode or alignment */
+    SGR_ERR_INVALID_GRAPH = -2,    /* CSR breaks the input contract */
+    SGR_ERR_OUT_OF_MEMORY = -3,    /* device or host allocation failed */
+    SGR_ERR_CUDA = -4,             /* a CUDA call failed */
+    SGR_ERR_NO_CONVERGENCE = -5,   /* round cap reached (only on broken input) */
+    SGR_ERR_TIMEOUT = -6,          /* a bounded device-side wait ran out */
+    SGR_ERR_NOT_FOUND = -7,        /* server: unknown request id */
+    SGR_ERR_BUSY = -8              /* server: over budget or queue full */
+} sgr_status;
+
+#define SGR_MODE_DETERMINISTIC 0
+#define SGR_MODE_FAST 1
+#define SGR_MODE_MASK 0x3
+#define SGR_RULE_LOW_KEEPS (0 << 4)
+#define SGR_RULE_LOW_LOSES (1 << 4)
+#define SGR_RULE_DEGREE (2 << 4)
+#define SGR_RULE_MASK (0x3 << 4)
+
+/* Statistics of the last coloring call made on this host thread. */
+typedef struct {
+    int64_t rounds;        /* iterations of Algorithm 7's loop */
+    int64_t sum_w;         /* sum over rounds of |W_r| */
+    int64_t sum_d;         /* sum over rounds of the degrees of W_r (FirstFit scan) */
+    int64_t sum_dscan;     /* col_idx entries ConflictResolve had to inspect */
+    int64_t sum_next;      /* sum over rounds of |W_{r+1}| (pushed losers) */
+    int32_t num_colors;    /* k (max color); per-graph values are returned separately */
+    int32_t rows_sorted;   /* 1 if every row was strictly ascending */
+    int32_t grid_blocks;   /* CTAs of the persistent kernel */
+    int32_t block_threads; /* threads per CTA */
+    double device_ms;      /* device time of the coloring kernel(s), CUDA events */
+} sgr_stats;
+
+/* Load-balance and launch parameters (Sect. 3.2 thread coarsening, Sect. 3.3
+ * load balancing).  Zero fields mean "library default". */
+typedef struct {
+    int32_t group_lanes;   /* lanes per low-degree vertex: 1, 2, 4, 8, 16 or 32 */
+    int32_t light_max;     /* degree bound of the group-per-vertex bin, <= 63 */
+    int32_t chunk;         /* edges per warp work item of the hub bin; also the
+                              degree bound of the warp-per-vertex bin (>= 64) */
+    int32_t blocks_per_sm; /* persistent CTAs per SM (capped by occupancy) */
+} sgr_tuning;
+
+/*
+ * Color one graph.  Algorithm 7 with Algorithms 4 and 5 (Sect. 3.1-3.3).
+ *   n            number of vertices, 0 <= n < 2^31.
+ *   row_offsets  DEVICE pointer, n+1 int32.
+ *   col_idx      DEVICE pointer, m = row_offsets[n] int32, 16-byte aligned
+ *                (any cudaMalloc / torch allocation is).
+ *   colors_out   DEVICE pointer, n int32; receives colors 1..k.
+ *   num_colors   HOST pointer; receives k (0 when n == 0).
+ *   mode         SGR_MODE_* | SGR_RULE_*.
+ *   stream       stream the work is ordered on.  The call blocks until the
+ *                coloring is done (one stream synchronisation to read m before
+ *                launch and one to read k and the statistics after).
+ * Returns SGR_OK, SGR_ERR_INVALID_ARG (null pointer with n > 0, unknown mode,
+ * unaligned col_idx), SGR_ERR_INVALID_GRAPH (row_offsets[0] != 0 or m < 0),
+ * SGR_ERR_OUT_OF_MEMORY, SGR_ERR_CUDA, SGR_ERR_TIMEOUT or
+ * SGR_ERR_NO_CONVERGENCE.  Behaviour on a CSR that is not symmetric or has
+ * out-of-range ids is unspecified but ends (round cap n+1); use
+ * sgr_validate_csr to check a graph first.
+ */
+int sgr_color(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
+              int32_t *colors_out, int32_t *num_colors, int mode, sgr_stream_t stream);
+
+/*
+ * Same as sgr_color with HOST buffers: copies the CSR to library-owned device
+ * memory on `stream`, colors it and copies the colors back.  Pinned host
+ * memory makes the copies faster but is not required.
+ */
+int sgr_color_host(int32_t n, const int32_t *row_offsets_host, const int32_t *col_idx_host,
+                   int32_t *colors_host, int32_t *num_colors, int mode, sgr_stream_t stream);
+
+/*
+ * Color G independent graphs packed into one concatenated CSR, all in one
+ * persistent kernel (rounds of all graphs advance together).  Coloring a
+ * disjoint union with per-graph id offsets gives each graph exactly the
+ * coloring it gets alone: the rules compare ids only within a graph.
+ *   vtx_off   HOST, G+1 int64: graph g owns global vertices [vtx_off[g], vtx_off[g+1]).
+ *   edge_off  HOST, G+1 int64: graph g's entries are col_idx[edge_off[g] .. edge_off[g+1]).
+ *   row_offsets DEVICE, vtx_off[G] + G int32: graph g's n_g+1 LOCAL offsets
+ *             start at row_offsets[vtx_off[g] + g] (first one 0).
+ *   col_idx   DEVICE, edge_off[G] int32 LOCAL ids, 16-byte aligned base.
+ *   colors_out DEVICE, vtx_off[G] int32; graph g's colors at vtx_off[g].
+ *   num_colors HOST, G int32: per-graph k.
+ * Requires vtx_off[G] < 2^31.  Errors as sgr_color.
+ */
+int sgr_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
+                    const int32_t *row_offsets, const int32_t *col_idx, int32_t *colors_out,
+                    int32_t *num_colors, int mode, sgr_stream_t stream);
+
+/*
+ * Check the input contract on the device: row_offsets[0] == 0,
+ * non-decreasing offsets, ids in [0, n), no self-loops, no duplicate entry in
+ * a row, and symmetry (w in adj(v) iff v in adj(w)).  Returns SGR_OK or
+ * SGR_ERR_INVALID_GRAPH; *rows_sorted (HOST, may be NULL) receives 1 when
+ * every row is strictly ascending.  Pointers as in sgr_color.
+ */
+int sgr_validate_csr(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
+                     int32_t *rows_sorted, sgr_stream_t stream);
+
+/* Statistics of the last sgr_color / sgr_color_host / sgr_color_batch call
+ * on this host thread. */
+int sgr_last_stats(sgr_stats *out);
+
+/* Get / set the process-wide tuning used by later calls. */
+int sgr_get_tuning(sgr_tuning *out);
+int sgr_set_tuning(const sgr_tuning *in);
+
+/* Free the scratch arena of the current device. */
+int sgr_release_scratch(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *sgr_status_string(int status);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int sgr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGRCOLOR_H */

@@ -1,0 +1,532 @@
+// sgr_api.cu -- the C ABI of libsgrcolor (declared in include/sgrcolor.h).
+//
+// Host side of the coloring call: argument checks, the per-device scratch
+// arena, the cooperative launch of the persistent coloring kernel, and the
+// single read-back of counters and statistics.  The CPU only controls
+// progress here, as in the paper's design (Sect. 3.1); all coloring work runs
+// in the kernels of sgr_kernels.cu.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "sgr_internal.cuh"
+#include "sgrcolor.h"
+
+namespace {
+
+using sgr::Counters;
+using sgr::Params;
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// A device buffer that only grows (freed by sgr_release_scratch).
+struct Arena {
+    char *ptr = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap) return cudaSuccess;
+        if (ptr) {
+            cudaError_t e = cudaFree(ptr);
+            ptr = nullptr;
+            cap = 0;
+            if (e != cudaSuccess) return e;
+        }
+        size_t want = std::max(bytes, cap + cap / 4);
+        cudaError_t e = cudaMalloc(&ptr, want);
+        if (e != cudaSuccess) {
+            ptr = nullptr;
+            e = cudaMalloc(&ptr, bytes);
+            if (e != cudaSuccess) {
+                ptr = nullptr;
+                return e;
+            }
+            want = bytes;
+        }
+        cap = want;
+        return cudaSuccess;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        cap = 0;
+    }
+};
+
+struct DevCtx {
+    int device = -1;
+    int sms = 0;
+    int occ[2][2] = {{0, 0}, {0, 0}};  // [fast][batched]
+    Arena scratch;                      // worklists, counters, bitmaps
+    Arena io;                           // device copies for the host-buffer entry
+    Counters *host_ctr = nullptr;       // pinned read-back
+    int64_t *host_small = nullptr;      // pinned staging (offsets, flags)
+    size_t host_small_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::mutex mu;
+    bool ready = false;
+};
+
+std::mutex g_ctx_mu;
+std::vector<DevCtx *> g_ctx;
+
+std::mutex g_tune_mu;
+sgr_tuning g_tune = {4, 32, 2048, 0};
+
+thread_local sgr_stats t_stats;
+
+int map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return SGR_OK;
+    if (e == cudaErrorMemoryAllocation) return SGR_ERR_OUT_OF_MEMORY;
+    return SGR_ERR_CUDA;
+}
+
+int get_ctx(DevCtx **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return SGR_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    if ((int)g_ctx.size() <= dev) g_ctx.resize(dev + 1, nullptr);
+    if (!g_ctx[dev]) g_ctx[dev] = new DevCtx();
+    DevCtx *c = g_ctx[dev];
+    if (!c->ready) {
+        c->device = dev;
+        if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return SGR_ERR_CUDA;
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (!coop) return SGR_ERR_CUDA;
+        for (int f = 0; f < 2; ++f)
+            for (int b = 0; b < 2; ++b)
+                if (sgr::occupancy_blocks_per_sm(f != 0, b != 0, &c->occ[f][b]) != 0)
+                    return SGR_ERR_CUDA;
+        if (cudaMallocHost(&c->host_ctr, sizeof(Counters)) != cudaSuccess) return SGR_ERR_OUT_OF_MEMORY;
+        if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
+            return SGR_ERR_CUDA;
+        c->ready = true;
+    }
+    *out = c;
+    return SGR_OK;
+}
+
+int ensure_host_small(DevCtx *c, size_t count) {
+    if (count <= c->host_small_cap) return SGR_OK;
+    if (c->host_small) cudaFreeHost(c->host_small);
+    c->host_small = nullptr;
+    c->host_small_cap = 0;
+    size_t want = std::max<size_t>(count, 1024);
+    if (cudaMallocHost(&c->host_small, want * sizeof(int64_t)) != cudaSuccess) return SGR_ERR_OUT_OF_MEMORY;
+    c->host_small_cap = want;
+    return SGR_OK;
+}
+
+bool valid_mode(int mode) {
+    if (mode & ~(SGR_MODE_MASK | SGR_RULE_MASK)) return false;
+    const int md = mode & SGR_MODE_MASK, rule = (mode & SGR_RULE_MASK) >> 4;
+    return (md == SGR_MODE_DETERMINISTIC || md == SGR_MODE_FAST) && rule <= 2;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+sgr_tuning current_tuning() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune;
+}
+
+// Everything a coloring launch needs beyond the CSR itself.
+struct Job {
+    int32_t n;
+    long long m;
+    const int32_t *ro;
+    const int32_t *ci;
+    int32_t *colors;
+    bool batched;
+    int G;
+    const long long *vbase_dev;
+    const long long *ebase_dev;
+    int32_t *gid_dev;  // filled by the caller for batched jobs
+};
+
+// Carve the scratch arena for a job.  Returns the byte size; fills p when
+// base != nullptr.
+size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *zero_bytes) {
+    const sgr::ScratchPlan sp = sgr::plan_scratch(j.n, j.m, t.chunk);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return base ? (void *)(base + o) : nullptr;
+    };
+    // zeroed region first: counters, hub completion counters / flags, hub bitmaps
+    Counters *ctr = (Counters *)take(sizeof(Counters));
+    unsigned *hdone = (unsigned *)take(sp.hub_max * 4);
+    unsigned *hconf = (unsigned *)take(sp.hub_max * 4);
+    unsigned *hbits = (unsigned *)take(sp.hub_words * 4);
+    if (zero_bytes) *zero_bytes = off;
+    long long *trace = (long long *)take(sizeof(long long) * sgr::kTraceCap);
+    int32_t *lw0 = (int32_t *)take((size_t)j.n * 4), *lw1 = (int32_t *)take((size_t)j.n * 4);
+    int32_t *mw0 = (int32_t *)take((size_t)j.n * 4), *mw1 = (int32_t *)take((size_t)j.n * 4);
+    int32_t *hw0 = (int32_t *)take(sp.hub_max * 4), *hw1 = (int32_t *)take(sp.hub_max * 4);
+    unsigned *hcb0 = (unsigned *)take(sp.hub_max * 4), *hcb1 = (unsigned *)take(sp.hub_max * 4);
+    int32_t *hvert = (int32_t *)take(sp.hub_max * 4);
+    unsigned *hbase = (unsigned *)take(sp.hub_max * 4);
+    if (p && base) {
+        std::memset(p, 0, sizeof(*p));
+        p->ro = j.ro;
+        p->ci = j.ci;
+        p->gid = j.gid_dev;
+        p->vbase = j.vbase_dev;
+        p->ebase = j.ebase_dev;
+        p->m = j.m;
+        p->n = j.n;
+        p->colors = j.colors;
+        p->lw[0] = lw0; p->lw[1] = lw1;
+        p->mw[0] = mw0; p->mw[1] = mw1;
+        p->hw[0] = hw0; p->hw[1] = hw1;
+        p->hcb[0] = hcb0; p->hcb[1] = hcb1;
+        p->hvert = hvert;
+        p->hbase = hbase;
+        p->hbits = hbits;
+        p->hdone = hdone;
+        p->hconf = hconf;
+        p->ctr = ctr;
+        p->trace = trace;
+        p->G = t.group_lanes;
+        p->light_max = t.light_max;
+        p->chunk = t.chunk;
+    }
+    return off;
+}
+
+void fill_stats(const Counters &h, float ms, int grid, int colors) {
+    sgr_stats s;
+    std::memset(&s, 0, sizeof(s));
+    s.rounds = h.rounds;
+    s.sum_w = (int64_t)h.sum_w;
+    s.sum_d = (int64_t)h.sum_d;
+    s.sum_dscan = (int64_t)h.sum_dscan;
+    s.sum_next = (int64_t)h.sum_next;
+    s.num_colors = colors;
+    s.rows_sorted = h.unsorted_pairs == h.boundary_pairs ? 1 : 0;
+    s.grid_blocks = grid;
+    s.block_threads = sgr::kBlock;
+    s.device_ms = ms;
+    t_stats = s;
+}
+
+// Run one persistent coloring launch for a job (single graph or batch) and
+// read back the counters.  Caller holds the device mutex.
+int run_job(DevCtx *c, Job &j, int mode, cudaStream_t st, int32_t *k_out) {
+    const sgr_tuning t = current_tuning();
+    const bool fast = (mode & SGR_MODE_MASK) == SGR_MODE_FAST;
+    const int rule = (mode & SGR_RULE_MASK) >> 4;
+    size_t zero_bytes = 0;
+    size_t need = layout(j, t, nullptr, nullptr, &zero_bytes);
+    const size_t gid_off = need;
+    if (j.batched) need = align_up(need + (size_t)j.n * 4) + align_up((size_t)(j.G + 1) * 8) * 2 +
+                          align_up((size_t)j.G * 4);
+    cudaError_t e = c->scratch.ensure(need);
+    if (e != cudaSuccess) return map_cuda(e);
+    if (j.batched) {
+        j.gid_dev = (int32_t *)(c->scratch.ptr + gid_off);
+    }
+    Params p;
+    layout(j, t, c->scratch.ptr, &p, nullptr);
+    p.rule = rule;
+    p.max_rounds = (long long)j.n + 1;
+    int per_sm = c->occ[fast][j.batched];
+    if (t.blocks_per_sm > 0) per_sm = std::min(per_sm, t.blocks_per_sm);
+    if (per_sm < 1) return SGR_ERR_CUDA;
+    const int grid = per_sm * c->sms;
+    p.nblocks = (unsigned)grid;
+    if ((e = cudaMemsetAsync(c->scratch.ptr, 0, zero_bytes, st)) != cudaSuccess) return map_cuda(e);
+    if (j.batched) {
+        if ((e = sgr::launch_fill_gid(j.gid_dev, j.vbase_dev, j.G, j.n, st)) != cudaSuccess)
+            return map_cuda(e);
+    }
+    if ((e = cudaEventRecord(c->ev0, st)) != cudaSuccess) return map_cuda(e);
+    if ((e = sgr::launch_color(p, fast, j.batched, grid, st)) != cudaSuccess) return map_cuda(e);
+    if ((e = cudaEventRecord(c->ev1, st)) != cudaSuccess) return map_cuda(e);
+    if ((e = cudaMemcpyAsync(c->host_ctr, p.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    const Counters h = *c->host_ctr;
+    fill_stats(h, ms, grid, h.kmax);
+    if (h.err != 0) return h.err;
+    if (k_out) *k_out = h.kmax;
+    return SGR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sgr_version(void) { return 10000; }
+
+const char *sgr_status_string(int s) {
+    switch (s) {
+        case SGR_OK: return "SGR_OK";
+        case SGR_PENDING: return "SGR_PENDING";
+        case SGR_ERR_INVALID_ARG: return "SGR_ERR_INVALID_ARG";
+        case SGR_ERR_INVALID_GRAPH: return "SGR_ERR_INVALID_GRAPH";
+        case SGR_ERR_OUT_OF_MEMORY: return "SGR_ERR_OUT_OF_MEMORY";
+        case SGR_ERR_CUDA: return "SGR_ERR_CUDA";
+        case SGR_ERR_NO_CONVERGENCE: return "SGR_ERR_NO_CONVERGENCE";
+        case SGR_ERR_TIMEOUT: return "SGR_ERR_TIMEOUT";
+        case SGR_ERR_NOT_FOUND: return "SGR_ERR_NOT_FOUND";
+        case SGR_ERR_BUSY: return "SGR_ERR_BUSY";
+        default: return "SGR_UNKNOWN_STATUS";
+    }
+}
+
+int sgr_get_tuning(sgr_tuning *out) {
+    if (!out) return SGR_ERR_INVALID_ARG;
+    *out = current_tuning();
+    return SGR_OK;
+}
+
+int sgr_set_tuning(const sgr_tuning *in) {
+    if (!in) return SGR_ERR_INVALID_ARG;
+    sgr_tuning t = current_tuning();
+    if (in->group_lanes) {
+        const int g = in->group_lanes;
+        if (g < 1 || g > 32 || (g & (g - 1))) return SGR_ERR_INVALID_ARG;
+        t.group_lanes = g;
+    }
+    if (in->light_max) {
+        if (in->light_max < 1 || in->light_max > 63) return SGR_ERR_INVALID_ARG;
+        t.light_max = in->light_max;
+    }
+    if (in->chunk) {
+        if (in->chunk < 64 || in->chunk > (1 << 24)) return SGR_ERR_INVALID_ARG;
+        t.chunk = in->chunk;
+    }
+    if (in->blocks_per_sm < 0 || in->blocks_per_sm > 64) return SGR_ERR_INVALID_ARG;
+    t.blocks_per_sm = in->blocks_per_sm;
+    if (t.light_max >= t.chunk) return SGR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune = t;
+    return SGR_OK;
+}
+
+int sgr_last_stats(sgr_stats *out) {
+    if (!out) return SGR_ERR_INVALID_ARG;
+    *out = t_stats;
+    return SGR_OK;
+}
+
+int sgr_release_scratch(void) {
+    DevCtx *c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc != SGR_OK) return rc;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->scratch.release();
+    c->io.release();
+    return SGR_OK;
+}
+
+int sgr_color(int32_t n, const int32_t *row_offsets, const int32_t *col_idx, int32_t *colors_out,
+              int32_t *num_colors, int mode, sgr_stream_t stream) {
+    std::memset(&t_stats, 0, sizeof(t_stats));
+    if (n < 0 || !num_colors || !valid_mode(mode)) return SGR_ERR_INVALID_ARG;
+    if (n == 0) {
+        *num_colors = 0;
+        return SGR_OK;
+    }
+    if (!row_offsets || !col_idx || !colors_out) return SGR_ERR_INVALID_ARG;
+    if (!is_device_ptr(row_offsets) || !is_device_ptr(colors_out)) return SGR_ERR_INVALID_ARG;
+    DevCtx *c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc != SGR_OK) return rc;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *hs = (int32_t *)c->host_ctr;  // reuse pinned memory for two ints
+    cudaError_t e = cudaMemcpyAsync(hs, row_offsets, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs + 1, row_offsets + n, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return map_cuda(e);
+    const int32_t r0 = hs[0], m = hs[1];
+    if (r0 != 0 || m < 0) return SGR_ERR_INVALID_GRAPH;
+    if (m > 0 && (((uintptr_t)col_idx & 15) != 0 || !is_device_ptr(col_idx))) return SGR_ERR_INVALID_ARG;
+    Job j;
+    std::memset(&j, 0, sizeof(j));
+    j.n = n;
+    j.m = m;
+    j.ro = row_offsets;
+    j.ci = col_idx;
+    j.colors = colors_out;
+    return run_job(c, j, mode, st, num_colors);
+}
+
+int sgr_color_host(int32_t n, const int32_t *ro_h, const int32_t *ci_h, int32_t *colors_h,
+                   int32_t *num_colors, int mode, sgr_stream_t stream) {
+    std::memset(&t_stats, 0, sizeof(t_stats));
+    if (n < 0 || !num_colors || !valid_mode(mode)) return SGR_ERR_INVALID_ARG;
+    if (n == 0) {
+        *num_colors = 0;
+        return SGR_OK;
+    }
+    if (!ro_h || !colors_h) return SGR_ERR_INVALID_ARG;
+    const long long m = ro_h[n];
+    if (ro_h[0] != 0 || m < 0) return SGR_ERR_INVALID_GRAPH;
+    if (m > 0 && !ci_h) return SGR_ERR_INVALID_ARG;
+    DevCtx *c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc != SGR_OK) return rc;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t b_ro = align_up((size_t)(n + 1) * 4), b_ci = align_up((size_t)m * 4 + 16);
+    const size_t b_co = align_up((size_t)n * 4);
+    cudaError_t e = c->io.ensure(b_ro + b_ci + b_co);
+    if (e != cudaSuccess) return map_cuda(e);
+    int32_t *ro_d = (int32_t *)c->io.ptr;
+    int32_t *ci_d = (int32_t *)(c->io.ptr + b_ro);
+    int32_t *co_d = (int32_t *)(c->io.ptr + b_ro + b_ci);
+    if ((e = cudaMemcpyAsync(ro_d, ro_h, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return map_cuda(e);
+    if (m > 0 && (e = cudaMemcpyAsync(ci_d, ci_h, (size_t)m * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return map_cuda(e);
+    Job j;
+    std::memset(&j, 0, sizeof(j));
+    j.n = n;
+    j.m = m;
+    j.ro = ro_d;
+    j.ci = ci_d;
+    j.colors = co_d;
+    rc = run_job(c, j, mode, st, num_colors);
+    if (rc != SGR_OK) return rc;
+    if ((e = cudaMemcpyAsync(colors_h, co_d, (size_t)n * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);
+    return SGR_OK;
+}
+
+int sgr_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
+                    const int32_t *row_offsets, const int32_t *col_idx, int32_t *colors_out,
+                    int32_t *num_colors, int mode, sgr_stream_t stream) {
+    std::memset(&t_stats, 0, sizeof(t_stats));
+    if (G < 0 || !valid_mode(mode)) return SGR_ERR_INVALID_ARG;
+    if (G == 0) return SGR_OK;
+    if (!vtx_off || !edge_off || !num_colors || !row_offsets) return SGR_ERR_INVALID_ARG;
+    if (vtx_off[0] != 0 || edge_off[0] != 0) return SGR_ERR_INVALID_GRAPH;
+    for (int g = 0; g < G; ++g)
+        if (vtx_off[g + 1] < vtx_off[g] || edge_off[g + 1] < edge_off[g]) return SGR_ERR_INVALID_GRAPH;
+    const long long n = vtx_off[G], m = edge_off[G];
+    if (n + G >= (1ll << 31)) return SGR_ERR_INVALID_ARG;
+    if (n == 0) {
+        for (int g = 0; g < G; ++g) num_colors[g] = 0;
+        return SGR_OK;
+    }
+    if (!colors_out || !is_device_ptr(row_offsets) || !is_device_ptr(colors_out)) return SGR_ERR_INVALID_ARG;
+    if (m > 0 && (!col_idx || ((uintptr_t)col_idx & 15) != 0 || !is_device_ptr(col_idx)))
+        return SGR_ERR_INVALID_ARG;
+    DevCtx *c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc != SGR_OK) return rc;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ensure_host_small(c, 2 * (size_t)(G + 1) + (size_t)G)) != SGR_OK) return rc;
+    Job j;
+    std::memset(&j, 0, sizeof(j));
+    j.n = (int32_t)n;
+    j.m = m;
+    j.ro = row_offsets;
+    j.ci = col_idx;
+    j.colors = colors_out;
+    j.batched = true;
+    j.G = G;
+    // the batch tail of the arena: gid, vbase, ebase, per-graph k (see run_job)
+    const sgr_tuning t = current_tuning();
+    size_t zero_bytes = 0;
+    const size_t base_need = layout(j, t, nullptr, nullptr, &zero_bytes);
+    const size_t need = align_up(base_need + (size_t)n * 4) + align_up((size_t)(G + 1) * 8) * 2 +
+                        align_up((size_t)G * 4);
+    cudaError_t e = c->scratch.ensure(need);
+    if (e != cudaSuccess) return map_cuda(e);
+    char *tail = c->scratch.ptr + align_up(base_need + (size_t)n * 4);
+    long long *vb_d = (long long *)tail;
+    long long *eb_d = (long long *)(tail + align_up((size_t)(G + 1) * 8));
+    int32_t *k_d = (int32_t *)(tail + 2 * align_up((size_t)(G + 1) * 8));
+    std::memcpy(c->host_small, vtx_off, (size_t)(G + 1) * 8);
+    std::memcpy(c->host_small + (G + 1), edge_off, (size_t)(G + 1) * 8);
+    if ((e = cudaMemcpyAsync(vb_d, c->host_small, (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaMemcpyAsync(eb_d, c->host_small + (G + 1), (size_t)(G + 1) * 8, cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+        return map_cuda(e);
+    j.vbase_dev = vb_d;
+    j.ebase_dev = eb_d;
+    int32_t kall = 0;
+    rc = run_job(c, j, mode, st, &kall);
+    if (rc != SGR_OK) return rc;
+    if ((e = sgr::launch_segmented_max(colors_out, vb_d, G, k_d, st)) != cudaSuccess) return map_cuda(e);
+    int32_t *kh = (int32_t *)(c->host_small + 2 * (G + 1));
+    if ((e = cudaMemcpyAsync(kh, k_d, (size_t)G * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);
+    std::memcpy(num_colors, kh, (size_t)G * 4);
+    return SGR_OK;
+}
+
+int sgr_validate_csr(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
+                     int32_t *rows_sorted, sgr_stream_t stream) {
+    if (n < 0) return SGR_ERR_INVALID_ARG;
+    if (n == 0) {
+        if (rows_sorted) *rows_sorted = 1;
+        return SGR_OK;
+    }
+    if (!row_offsets || !is_device_ptr(row_offsets)) return SGR_ERR_INVALID_ARG;
+    DevCtx *c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc != SGR_OK) return rc;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *hs = (int32_t *)c->host_ctr;
+    cudaError_t e = cudaMemcpyAsync(hs, row_offsets, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs + 1, row_offsets + n, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return map_cuda(e);
+    if (hs[0] != 0 || hs[1] < 0) return SGR_ERR_INVALID_GRAPH;
+    const long long m_v = hs[1];
+    if (m_v > 0 && (!col_idx || !is_device_ptr(col_idx))) return SGR_ERR_INVALID_ARG;
+    if ((e = c->scratch.ensure(256)) != cudaSuccess) return map_cuda(e);
+    unsigned long long *flags = (unsigned long long *)c->scratch.ptr;
+    unsigned long long *fh = (unsigned long long *)c->host_ctr;
+    if ((e = cudaMemsetAsync(flags, 0, 24, st)) != cudaSuccess) return map_cuda(e);
+    if ((e = sgr::launch_validate(n, m_v, row_offsets, col_idx, flags, st)) != cudaSuccess) return map_cuda(e);
+    if ((e = cudaMemcpyAsync(fh, flags, 24, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return map_cuda(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);
+    const unsigned long long f = fh[0], h1 = fh[1], h2 = fh[2];
+    const int sorted = (f & 8) ? 0 : 1;
+    if (rows_sorted) *rows_sorted = sorted;
+    if (f & (1 | 2 | 4 | 16)) return SGR_ERR_INVALID_GRAPH;
+    if (h1 != h2) return SGR_ERR_INVALID_GRAPH;
+    if (sorted) {
+        if ((e = cudaMemsetAsync(flags, 0, 24, st)) != cudaSuccess) return map_cuda(e);
+        if ((e = sgr::launch_validate_exact(n, m_v, row_offsets, col_idx, flags, st)) != cudaSuccess)
+            return map_cuda(e);
+        if ((e = cudaMemcpyAsync(fh, flags, 24, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return map_cuda(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);
+        if (fh[0] & (1 | 2 | 4 | 16 | 32)) return SGR_ERR_INVALID_GRAPH;
+    }
+    return SGR_OK;
+}
+
+}  // extern "C"
+

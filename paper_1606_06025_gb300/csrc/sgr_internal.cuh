@@ -1,0 +1,109 @@
+// sgr_internal.cuh -- device-side state shared by the kernels and the C ABI.
+//
+// Data layout in device memory (one coloring call):
+//   colors[n]            int32; > 0 final (or, in fast mode, live) color,
+//                        < 0 tentative color of the current round (det mode),
+//                        0 uncolored.
+//   light lists lw[2]    vertex ids of degree <= light_max, double buffered by
+//                        round parity (Algorithm 7's W_in / W_out swap).
+//   medium lists mw[2]   vertex ids of degree in (light_max, chunk].
+//   hub lists hw[2]      hub slot ids (degree > chunk) + chunk base hcb[2].
+//   hub slots            hvert (slot -> vertex), hbase (offset of the slot's
+//                        forbidden-color bitmap in hbits), hdone / hconf
+//                        (per-round completion counter and conflict flag).
+//   Counters             list sizes, work-grab counters, grid barrier, max
+//                        color so far, error code, statistics.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sgr {
+
+constexpr int kBlock = 256;                      // threads per CTA
+constexpr int kWarps = kBlock / 32;
+constexpr int kLightUnroll = 4;                  // 32-vertex sub-tiles per warp and light tile
+constexpr int kLightTile = kBlock * kLightUnroll;
+constexpr int kMediumBatch = 4;                  // medium vertices per warp grab
+constexpr int kTraceCap = 1 << 16;               // per-round |W_r| entries recorded
+constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;  // bounded device waits
+
+// status codes mirrored from sgrcolor.h (device code cannot include it twice)
+constexpr int kErrNoConvergence = -5;
+constexpr int kErrTimeout = -6;
+
+struct Counters {
+    unsigned int nl[2];             // light list sizes by round parity
+    unsigned int nm[2];             // medium list sizes
+    unsigned long long h64[2];      // hub lists: (entries << 32) | total chunks
+    unsigned int grab[3][2];        // dynamic work-grab counters (medium, hub), 3 phases rotating
+    unsigned int bar_count;         // grid barrier arrivals
+    unsigned int bar_gen;           // grid barrier generation
+    unsigned int nslots;            // hub slots handed out
+    unsigned int hwords;            // hub bitmap words handed out
+    int kmax;                       // largest committed color
+    int err;                        // 0 or a negative status
+    unsigned long long unsorted_pairs;   // adjacent col_idx pairs with a[i] >= a[i+1]
+    unsigned long long boundary_pairs;   // ... of them across row boundaries
+    unsigned long long sum_w, sum_d, sum_dscan, sum_next;
+    long long rounds;
+    long long pad[4];
+};
+
+struct Params {
+    const int32_t *ro;
+    const int32_t *ci;
+    const int32_t *gid;        // batched: vertex -> graph id
+    const long long *vbase;    // batched: graph -> first global vertex
+    const long long *ebase;    // batched: graph -> first global entry
+    long long m;               // total col_idx entries
+    int32_t n;                 // total vertices
+    int32_t *colors;
+    int32_t *lw[2];
+    int32_t *mw[2];
+    int32_t *hw[2];
+    unsigned int *hcb[2];
+    int32_t *hvert;
+    unsigned int *hbase;
+    unsigned int *hbits;
+    unsigned int *hdone;
+    unsigned int *hconf;
+    Counters *ctr;
+    long long *trace;
+    int G;                     // lanes per light vertex (power of two <= 32)
+    int light_max;             // <= 63
+    int chunk;                 // hub chunk edges; medium degree bound
+    int rule;                  // 0 low keeps, 1 low loses, 2 degree
+    long long max_rounds;
+    unsigned int nblocks;
+};
+
+// Scratch sizes for a graph of n vertices / m entries under a chunk size.
+struct ScratchPlan {
+    size_t hub_max;     // upper bound on hub vertices
+    size_t hub_words;   // upper bound on hub bitmap words
+};
+
+inline ScratchPlan plan_scratch(long long n, long long m, int chunk) {
+    ScratchPlan p;
+    long long h = m / (chunk + 1) + 1;
+    if (h > n) h = n;
+    if (h < 1) h = 1;
+    p.hub_max = (size_t)h;
+    p.hub_words = (size_t)((m + 2 * h) / 32 + 2 * h + 8);
+    return p;
+}
+
+// Launches (implemented in sgr_kernels.cu).
+int occupancy_blocks_per_sm(bool fast, bool batched, int *out);
+cudaError_t launch_color(const Params &p, bool fast, bool batched, int grid, cudaStream_t s);
+cudaError_t launch_fill_gid(int32_t *gid, const long long *vbase_dev, int G, int32_t n,
+                            cudaStream_t s);
+cudaError_t launch_segmented_max(const int32_t *colors, const long long *vbase_dev, int G,
+                                 int32_t *out_dev, cudaStream_t s);
+cudaError_t launch_validate(int32_t n, long long m, const int32_t *ro, const int32_t *ci,
+                            unsigned long long *flags_dev, cudaStream_t s);
+cudaError_t launch_validate_exact(int32_t n, long long m, const int32_t *ro, const int32_t *ci,
+                                  unsigned long long *flags_dev, cudaStream_t s);
+
+}  // namespace sgr

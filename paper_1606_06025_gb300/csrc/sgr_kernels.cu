@@ -1,0 +1,971 @@
+// sgr_kernels.cu -- the speculative-greedy coloring loop as one persistent
+// kernel for sm_103a.
+//
+// One cooperative launch runs Algorithm 7 (Sect. 3.1) to completion:
+//
+//   init:    W_1 = V, binned by degree; colors = 0 (fast) or -1 (det: the
+//            round-1 FirstFit answer is 1 for every vertex, since all frozen
+//            colors are 0); strictly-ascending rows are detected.
+//   round r: phase A = FirstFit (Algorithm 4) over W_r,
+//            grid barrier,
+//            phase B = ConflictResolve (Algorithm 5) over W_r: keepers commit,
+//            losers are compacted into W_{r+1} (Sect. 3.1 "Atomic Operation
+//            Reduction": one atomic per CTA tile, positions from a block scan),
+//            grid barrier, swap W_in / W_out by parity (Algorithm 7's swap).
+//
+// The two phases share one kernel with a software grid barrier, which is the
+// paper's kernel fusion (Sect. 3.3) and its forced thread coarsening
+// (Sect. 3.2): a fixed grid of co-resident CTAs loops over the worklist.
+// Every wait is bounded by %globaltimer; on expiry the kernel records
+// SGR_ERR_TIMEOUT and returns.
+//
+// Deterministic mode keeps the tentative color of a worklist vertex as a
+// negative value in `colors`.  FirstFit only counts positive (final) colors,
+// so it sees exactly the colors frozen at the start of the round whatever
+// the interleaving; ConflictResolve compares magnitudes, so a neighbour's
+// commit (-c -> +c) during the phase does not change what it sees; losers
+// keep -c until their next FirstFit overwrites it.  This is the
+// judge-before-clear reading: a loser still counts against higher ids.
+//
+// Load balance (Sect. 3.3, Merrill's thread / warp / CTA mapping): a vertex
+// of degree <= light_max is handled by a group of G lanes, a vertex of degree
+// <= chunk by one warp, a hub by ceil(deg / chunk) warp-sized work items that
+// merge their forbidden-color bitmaps with atomicOr; the item that finishes
+// last (completion counter) resolves the vertex.
+//
+// First permissible color (Sect. 3.2 "Bitset Operation"): forbidden colors
+// are gathered into bit masks and the answer is the first zero bit (__ffsll /
+// __ffs on the complement).
+//
+// Reads of col_idx and row_offsets use the read-only path (__ldg, Sect. 3.3
+// "Read-only Data Caching") with 16-byte vector loads; colors, worklists and
+// counters change during the launch and are read through L2 (__ldcg).
+
+#include <climits>
+#include <cstdint>
+
+#include "sgr_internal.cuh"
+
+namespace sgr {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded sense-by-generation grid barrier.  Returns false if this CTA must
+// stop (timeout or a recorded error).
+__device__ bool grid_barrier(const Params &p, unsigned &gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Counters *c = p.ctr;
+        gen += 1;
+        int ok = 1;
+        __threadfence();
+        unsigned arrived = atomicAdd(&c->bar_count, 1u);
+        if (arrived == p.nblocks - 1) {
+            c->bar_count = 0;
+            st_release(&c->bar_gen, gen);
+        } else {
+            unsigned long long t0 = globaltimer();
+            while ((int)(ld_acquire(&c->bar_gen) - gen) < 0) {
+                __nanosleep(40);
+                if (globaltimer() - t0 > kWaitTimeoutNs) {
+                    atomicCAS(&c->err, 0, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        if (ok && *(volatile int *)&c->err != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <bool kBatched>
+__device__ __forceinline__ void row_of(const Params &p, int32_t v, long long &s, long long &e,
+                                       int32_t &vb) {
+    if (kBatched) {
+        const int g = __ldg(p.gid + v);
+        const long long eb = __ldg(p.ebase + g);
+        s = eb + __ldg(p.ro + v + g);
+        e = eb + __ldg(p.ro + v + g + 1);
+        vb = (int32_t)__ldg(p.vbase + g);
+    } else {
+        s = __ldg(p.ro + v);
+        e = __ldg(p.ro + v + 1);
+        vb = 0;
+    }
+}
+
+// 16-byte load of col_idx entries [4q, 4q+4); entries past m read as 0.
+__device__ __forceinline__ int4 load4(const int32_t *__restrict__ ci, long long q, long long m) {
+    const long long i = q << 2;
+    if (i + 4 <= m) return __ldg(reinterpret_cast<const int4 *>(ci) + q);
+    int4 r = make_int4(0, 0, 0, 0);
+    if (i < m) r.x = __ldg(ci + i);
+    if (i + 1 < m) r.y = __ldg(ci + i + 1);
+    if (i + 2 < m) r.z = __ldg(ci + i + 2);
+    return r;
+}
+
+__device__ __forceinline__ int elem(const int4 &x, int k) {
+    return k == 0 ? x.x : (k == 1 ? x.y : (k == 2 ? x.z : x.w));
+}
+
+// Does v lose its color to neighbour w that holds the same color?
+template <bool kBatched>
+__device__ __forceinline__ bool loses_to(const Params &p, int32_t v, int32_t w, int32_t dv) {
+    if (p.rule == 0) return w < v;
+    if (p.rule == 1) return w > v;
+    long long s, e;
+    int32_t vb;
+    row_of<kBatched>(p, w, s, e, vb);
+    const int32_t dw = (int32_t)(e - s);
+    return dw != dv ? dw > dv : w < v;
+}
+
+struct Acc {
+    unsigned long long w = 0, d = 0, dscan = 0, next = 0;
+    int kmax = 0;
+};
+
+// ------------------------------------------------------------ forbidden masks
+
+// Colors 1..64 of the entries [s, e) this lane covers (lanes gl, gl+G, ...),
+// as bits 0..63.  Only positive colors forbid (final colors in det mode).
+__device__ __forceinline__ unsigned long long mask64_lane(const int32_t *__restrict__ ci,
+                                                          long long m,
+                                                          const int32_t *colors, long long s,
+                                                          long long e, int32_t vb, int gl,
+                                                          int G, int32_t nv) {
+    unsigned long long mask = 0;
+    for (long long q = (s >> 2) + gl; (q << 2) < e; q += G) {
+        const int4 x = load4(ci, q, m);
+        const long long i0 = q << 2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long i = i0 + k;
+            const int32_t w = vb + elem(x, k);
+            if (i >= s && i < e && (unsigned)w < (unsigned)nv) {
+                const int c = __ldcg(colors + w);
+                if (c > 0 && c <= 64) mask |= 1ull << (c - 1);
+            }
+        }
+    }
+    return mask;
+}
+
+// Colors wb+1 .. wb+256 of entries [a, b) (lanes lane0, lane0+stride, ...)
+// into eight 32-bit words.
+__device__ __forceinline__ void mask256_lane(const int32_t *__restrict__ ci, long long m,
+                                             const int32_t *colors, long long a, long long b,
+                                             int32_t vb, int lane0, int stride, int wb,
+                                             int32_t nv, unsigned (&mw)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) mw[j] = 0;
+    for (long long q = (a >> 2) + lane0; (q << 2) < b; q += stride) {
+        const int4 x = load4(ci, q, m);
+        const long long i0 = q << 2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long i = i0 + k;
+            const int32_t w = vb + elem(x, k);
+            if (i >= a && i < b && (unsigned)w < (unsigned)nv) {
+                const int c = __ldcg(colors + w);
+                const unsigned off = (unsigned)(c - wb - 1);
+                if (c > 0 && off < 256u) {
+                    const unsigned bit = 1u << (off & 31);
+                    const unsigned wd = off >> 5;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) mw[j] |= (wd == (unsigned)j) ? bit : 0u;
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void warp_or8(unsigned (&mw)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) mw[j] = __reduce_or_sync(kFull, mw[j]);
+}
+
+// first zero bit of the 256-bit window, 256 if none
+__device__ __forceinline__ int first_zero8(const unsigned (&mw)[8]) {
+    int z = 256;
+#pragma unroll
+    for (int j = 7; j >= 0; --j)
+        if (~mw[j]) z = j * 32 + __ffs(~mw[j]) - 1;
+    return z;
+}
+
+__device__ __forceinline__ unsigned pick8(const unsigned (&mw)[8], int j) {
+    unsigned r = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r = (k == j) ? mw[k] : r;
+    return r;
+}
+
+// Whole-row first fit by one warp, windows of 256 colors (medium vertices and
+// the rare hub fallback).
+__device__ __forceinline__ int warp_first_fit(const int32_t *__restrict__ ci, long long m,
+                                              const int32_t *colors, long long s, long long e,
+                                              int32_t vb, int lane, int32_t nv) {
+    for (int wb = 0;; wb += 256) {
+        unsigned mw[8];
+        mask256_lane(ci, m, colors, s, e, vb, lane, 32, wb, nv, mw);
+        warp_or8(mw);
+        const int z = first_zero8(mw);
+        if (z < 256) return wb + z + 1;
+    }
+}
+
+// ------------------------------------------------------------ conflict scan
+
+// Does v (tentative color c, degree dv) lose in this round?  Scans the
+// entries [a, b) covered by this lane (lanes lane0, lane0+stride, ...).
+// With ascending rows and the low-keeps rule only ids below v matter, so the
+// scan stops at the first entry >= v.  Stops early at a conflict.
+template <bool kFast, bool kBatched>
+__device__ __forceinline__ bool conflict_lane(const Params &p, const int32_t *colors, int32_t v,
+                                              int c, int32_t dv, long long a, long long b,
+                                              int32_t vb, int lane0, int stride, bool prefix,
+                                              unsigned long long &scanned) {
+    for (long long q = (a >> 2) + lane0; (q << 2) < b; q += stride) {
+        const int4 x = load4(p.ci, q, p.m);
+        const long long i0 = q << 2;
+        bool stop = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long i = i0 + k;
+            if (i >= a && i < b) {
+                const int32_t w = vb + elem(x, k);
+                if (prefix && w >= v) {
+                    stop = true;
+                } else if ((unsigned)w < (unsigned)p.n) {
+                    if (p.rule == 0 && w > v) continue;
+                    if (p.rule == 1 && w < v) continue;
+                    scanned++;
+                    const int cw = __ldcg(colors + w);
+                    const int mag = kFast ? cw : (cw < 0 ? -cw : cw);
+                    if (mag == c && w != v && loses_to<kBatched>(p, v, w, dv)) return true;
+                }
+            }
+        }
+        if (stop) break;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------ block compaction
+
+// Each thread pushes cnt (<= kLightUnroll) items; one atomicAdd per CTA.
+__device__ __forceinline__ void block_push(int cnt, const int32_t (&items)[kLightUnroll],
+                                           unsigned *counter, int32_t *out,
+                                           unsigned long long &pushed) {
+    __shared__ unsigned s_wsum[kWarps];
+    __shared__ unsigned s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = (unsigned)x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const unsigned c = s_wsum[w];
+            s_wsum[w] = tot;
+            tot += c;
+        }
+        s_base = tot ? atomicAdd(counter, tot) : 0u;
+        pushed += tot;
+    }
+    __syncthreads();
+    const unsigned pos = s_base + s_wsum[warp] + (unsigned)(x - cnt);
+#pragma unroll
+    for (int k = 0; k < kLightUnroll; ++k)
+        if (k < cnt) out[pos + k] = items[k];
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long group_or64(unsigned long long x, int G) {
+    for (int o = G >> 1; o > 0; o >>= 1) x |= __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+__device__ __forceinline__ bool group_any(bool x, int G) {
+    unsigned v = x ? 1u : 0u;
+    for (int o = G >> 1; o > 0; o >>= 1) v |= __shfl_xor_sync(kFull, v, o);
+    return v != 0;
+}
+
+// ------------------------------------------------------------ phase A pieces
+
+template <bool kFast, bool kBatched>
+__device__ void light_assign(const Params &p, const int32_t *list, unsigned cnt, Acc &acc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int G = p.G, gl = lane & (G - 1), per = 32 / G;
+    const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
+    for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const unsigned base = t * kLightTile + warp * (32 * kLightUnroll);
+        for (int step = 0; step < kLightUnroll * G; ++step) {
+            const unsigned idx = base + step * per + lane / G;
+            const bool act = idx < cnt;
+            int32_t v = 0, vb = 0;
+            long long s = 0, e = 0;
+            unsigned long long mask = 0;
+            if (act) {
+                v = __ldcg(list + idx);
+                row_of<kBatched>(p, v, s, e, vb);
+                mask = mask64_lane(p.ci, p.m, p.colors, s, e, vb, gl, G, p.n);
+            }
+            mask = group_or64(mask, G);
+            if (act && gl == 0) {
+                const int c = __ffsll((long long)~mask);
+                __stcg(p.colors + v, kFast ? c : -c);
+                acc.w += 1;
+                acc.d += (unsigned long long)(e - s);
+            }
+        }
+    }
+}
+
+template <bool kFast, bool kBatched>
+__device__ void medium_assign(const Params &p, const int32_t *list, unsigned cnt,
+                              unsigned *grab, Acc &acc) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned i0 = 0;
+        if (lane == 0) i0 = atomicAdd(grab, (unsigned)kMediumBatch);
+        i0 = __shfl_sync(kFull, i0, 0);
+        if (i0 >= cnt) break;
+        const unsigned i1 = min(i0 + kMediumBatch, cnt);
+        for (unsigned i = i0; i < i1; ++i) {
+            const int32_t v = __ldcg(list + i);
+            long long s, e;
+            int32_t vb;
+            row_of<kBatched>(p, v, s, e, vb);
+            const int c = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);
+            if (lane == 0) {
+                __stcg(p.colors + v, kFast ? c : -c);
+                acc.w += 1;
+                acc.d += (unsigned long long)(e - s);
+            }
+        }
+    }
+}
+
+// index of the hub entry owning chunk q: largest i with cb[i] <= q
+__device__ __forceinline__ unsigned hub_entry(const unsigned *cb, unsigned cnt, unsigned q) {
+    unsigned lo = 0, hi = cnt;  // invariant: cb[lo] <= q < cb[hi]
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (__ldcg(cb + mid) <= q) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <bool kFast, bool kBatched>
+__device__ void hub_assign(const Params &p, int par, unsigned long long h64, unsigned *grab,
+                           int kmax, Acc &acc) {
+    const int lane = threadIdx.x & 31;
+    const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
+    const long long CH = p.chunk;
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(grab, 1u);
+        q = __shfl_sync(kFull, q, 0);
+        if (q >= nch) break;
+        const unsigned i = hub_entry(p.hcb[par], cnt, q);
+        const int32_t slot = __ldcg(p.hw[par] + i);
+        const unsigned j = q - __ldcg(p.hcb[par] + i);
+        const int32_t v = __ldcg(p.hvert + slot);
+        long long s, e;
+        int32_t vb;
+        row_of<kBatched>(p, v, s, e, vb);
+        const long long deg = e - s;
+        const long long a = s + (long long)j * CH, b = min(e, a + CH);
+        // det: every forbidden color is final, hence <= kmax; fast: a guess with a fallback
+        long long nb = kFast ? (long long)kmax + 64 : (long long)kmax;
+        if (nb > deg) nb = deg;
+        const int nbits = (int)nb + 1;
+        const int words = (nbits + 31) >> 5;
+        const unsigned base = __ldcg(p.hbase + slot);
+        for (int wb = 0; wb < words; wb += 8) {
+            unsigned mw[8];
+            mask256_lane(p.ci, p.m, p.colors, a, b, vb, lane, 32, wb * 32, p.n, mw);
+            warp_or8(mw);
+            if (lane < 8 && wb + lane < words) {
+                const unsigned x = pick8(mw, lane);
+                if (x) atomicOr(p.hbits + base + wb + lane, x);
+            }
+        }
+        const unsigned nchunks = (unsigned)((deg + CH - 1) / CH);
+        __syncwarp();
+        unsigned last = 0;
+        if (lane == 0) {
+            __threadfence();
+            last = (atomicAdd(p.hdone + slot, 1u) == nchunks - 1) ? 1u : 0u;
+            if (last) __threadfence();
+        }
+        last = __shfl_sync(kFull, last, 0);
+        if (last) {
+            unsigned best = UINT_MAX;
+            for (int k = lane; k < words; k += 32) {
+                const unsigned wv = __ldcg(p.hbits + base + k);
+                if (~wv) best = min(best, (unsigned)(k * 32 + __ffs(~wv) - 1));
+                __stcg(p.hbits + base + k, 0u);
+            }
+            best = __reduce_min_sync(kFull, best);
+            int c;
+            if (best < (unsigned)nbits) c = (int)best + 1;
+            else c = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);  // fast mode only
+            if (lane == 0) {
+                __stcg(p.colors + v, kFast ? c : -c);
+                __stcg(p.hdone + slot, 0u);
+                acc.w += 1;
+                acc.d += (unsigned long long)deg;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ phase B pieces
+
+template <bool kFast, bool kBatched>
+__device__ void light_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
+                             unsigned *out_cnt, bool prefix, Acc &acc) {
+    __shared__ int32_t s_flag[kWarps][32 * kLightUnroll];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int G = p.G, gl = lane & (G - 1), per = 32 / G;
+    const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
+    for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const unsigned base = t * kLightTile + warp * (32 * kLightUnroll);
+        for (int step = 0; step < kLightUnroll * G; ++step) {
+            const int jslot = step * per + lane / G;
+            const unsigned idx = base + jslot;
+            const bool act = idx < cnt;
+            int32_t v = 0, vb = 0;
+            long long s = 0, e = 0;
+            int c = 0;
+            bool conf = false;
+            if (act) {
+                v = __ldcg(list + idx);
+                row_of<kBatched>(p, v, s, e, vb);
+                const int own = __ldcg(p.colors + v);
+                c = kFast ? own : -own;
+                conf = conflict_lane<kFast, kBatched>(p, p.colors, v, c, (int32_t)(e - s), s, e, vb,
+                                                      gl, G, prefix, acc.dscan);
+            }
+            conf = group_any(conf, G);
+            if (gl == 0) {
+                int32_t flag = -1;
+                if (act) {
+                    if (conf) {
+                        flag = v;
+                        if (kFast) __stcg(p.colors + v, 0);
+                    } else {
+                        if (!kFast) __stcg(p.colors + v, c);
+                        acc.kmax = max(acc.kmax, c);
+                    }
+                }
+                s_flag[warp][jslot] = flag;
+            }
+        }
+        __syncwarp();
+        int32_t items[kLightUnroll];
+        int n_items = 0;
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) {
+            const int32_t f = s_flag[warp][u * 32 + lane];
+            items[u] = f;
+            n_items += (f >= 0);
+        }
+        // compact the valid entries to the front (static indices only)
+        int32_t packed[kLightUnroll];
+        int k = 0;
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) packed[u] = 0;
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) {
+            if (items[u] >= 0) {
+#pragma unroll
+                for (int z = 0; z < kLightUnroll; ++z)
+                    if (z == k) packed[z] = items[u];
+                ++k;
+            }
+        }
+        block_push(n_items, packed, out_cnt, out, acc.next);
+    }
+}
+
+template <bool kFast, bool kBatched>
+__device__ void medium_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
+                              unsigned *out_cnt, unsigned *grab, bool prefix, Acc &acc) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned i0 = 0;
+        if (lane == 0) i0 = atomicAdd(grab, (unsigned)kMediumBatch);
+        i0 = __shfl_sync(kFull, i0, 0);
+        if (i0 >= cnt) break;
+        const unsigned i1 = min(i0 + kMediumBatch, cnt);
+        int32_t lost[kMediumBatch];
+        int nlost = 0;
+        for (unsigned i = i0; i < i1; ++i) {
+            const int32_t v = __ldcg(list + i);
+            long long s, e;
+            int32_t vb;
+            row_of<kBatched>(p, v, s, e, vb);
+            const int own = __ldcg(p.colors + v);
+            const int c = kFast ? own : -own;
+            bool conf = false;
+            // warp-uniform trip count; lanes stop contributing after their own stop
+            for (long long q0 = (s >> 2); (q0 << 2) < e; q0 += 32) {
+                const long long q = q0 + lane;
+                bool my = false, past = false;
+                if ((q << 2) < e) {
+                    my = conflict_lane<kFast, kBatched>(p, p.colors, v, c, (int32_t)(e - s),
+                                                        (q << 2) > s ? (q << 2) : s, e, vb, 0,
+                                                        1 << 30, prefix, acc.dscan);
+                    if (prefix) past = vb + __ldg(p.ci + min((q << 2) + 3, e - 1)) >= v;
+                } else {
+                    past = true;
+                }
+                if (__any_sync(kFull, my)) { conf = true; break; }
+                if (prefix && __any_sync(kFull, past)) break;
+            }
+            if (lane == 0) {
+                if (conf) {
+                    if (kFast) __stcg(p.colors + v, 0);
+#pragma unroll
+                    for (int z = 0; z < kMediumBatch; ++z)
+                        if (z == nlost) lost[z] = v;
+                    ++nlost;
+                } else {
+                    if (!kFast) __stcg(p.colors + v, c);
+                    acc.kmax = max(acc.kmax, c);
+                }
+            }
+        }
+        if (lane == 0 && nlost) {
+            const unsigned pos = atomicAdd(out_cnt, (unsigned)nlost);
+#pragma unroll
+            for (int z = 0; z < kMediumBatch; ++z)
+                if (z < nlost) out[pos + z] = lost[z];
+            acc.next += (unsigned long long)nlost;
+        }
+    }
+}
+
+template <bool kFast, bool kBatched>
+__device__ void hub_detect(const Params &p, int par, unsigned long long h64, unsigned *grab,
+                           bool prefix, Acc &acc) {
+    const int lane = threadIdx.x & 31;
+    const int pn = par ^ 1;
+    const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
+    const long long CH = p.chunk;
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(grab, 1u);
+        q = __shfl_sync(kFull, q, 0);
+        if (q >= nch) break;
+        const unsigned i = hub_entry(p.hcb[par], cnt, q);
+        const int32_t slot = __ldcg(p.hw[par] + i);
+        const unsigned j = q - __ldcg(p.hcb[par] + i);
+        const int32_t v = __ldcg(p.hvert + slot);
+        long long s, e;
+        int32_t vb;
+        row_of<kBatched>(p, v, s, e, vb);
+        const long long deg = e - s;
+        const long long a = s + (long long)j * CH, b = min(e, a + CH);
+        const int own = __ldcg(p.colors + v);
+        const int c = kFast ? own : -own;
+        bool conf = false;
+        const bool skip = prefix && (vb + __ldg(p.ci + a)) >= v;
+        if (!skip) {
+            for (long long q0 = (a >> 2); (q0 << 2) < b; q0 += 32) {
+                const long long qq = q0 + lane;
+                bool my = false, past = false;
+                if ((qq << 2) < b) {
+                    const long long lo = (qq << 2) > a ? (qq << 2) : a;
+                    my = conflict_lane<kFast, kBatched>(p, p.colors, v, c, (int32_t)deg, lo, b, vb,
+                                                        0, 1 << 30, prefix, acc.dscan);
+                    if (prefix) past = vb + __ldg(p.ci + min((qq << 2) + 3, b - 1)) >= v;
+                } else {
+                    past = true;
+                }
+                if (__any_sync(kFull, my)) { conf = true; break; }
+                if (prefix && __any_sync(kFull, past)) break;
+            }
+        }
+        const unsigned nchunks = (unsigned)((deg + CH - 1) / CH);
+        unsigned last = 0;
+        if (lane == 0) {
+            if (conf) atomicOr(p.hconf + slot, 1u);
+            __threadfence();
+            last = (atomicAdd(p.hdone + slot, 1u) == nchunks - 1) ? 1u : 0u;
+            if (last) {
+                __threadfence();
+                const unsigned lost = __ldcg(p.hconf + slot);
+                __stcg(p.hconf + slot, 0u);
+                __stcg(p.hdone + slot, 0u);
+                if (lost) {
+                    if (kFast) __stcg(p.colors + v, 0);
+                    const unsigned long long old =
+                        atomicAdd(&p.ctr->h64[pn], (1ull << 32) | (unsigned long long)nchunks);
+                    const unsigned k = (unsigned)(old >> 32);
+                    p.hw[pn][k] = slot;
+                    p.hcb[pn][k] = (unsigned)old;
+                    acc.next += 1;
+                } else {
+                    if (!kFast) __stcg(p.colors + v, c);
+                    acc.kmax = max(acc.kmax, c);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ init
+
+template <bool kFast, bool kBatched>
+__device__ void init_phase(const Params &p, Acc &acc) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    // (1) adjacent col_idx pairs out of strict ascending order
+    unsigned long long bad = 0;
+    const long long nq = (p.m + 3) >> 2;
+    for (long long q = tid; q < nq; q += nthreads) {
+        const int4 x = load4(p.ci, q, p.m);
+        const long long i0 = q << 2;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (i0 + k + 1 < p.m && elem(x, k) >= elem(x, k + 1)) bad++;
+        if (i0 + 4 < p.m && x.w >= __ldg(p.ci + i0 + 4)) bad++;
+    }
+    // (2) binning of all vertices into W_1 (parity 1)
+    unsigned long long boundary = 0;
+    const unsigned nt = ((unsigned)p.n + kLightTile - 1) / kLightTile;
+    for (unsigned t = blockIdx.x; t < nt; t += gridDim.x) {
+        int32_t light[kLightUnroll], medium[kLightUnroll];
+        int nlight = 0, nmed = 0;
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) {
+            light[u] = 0;
+            medium[u] = 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) {
+            const long long v64 = (long long)t * kLightTile + u * kBlock + threadIdx.x;
+            if (v64 >= p.n) continue;
+            const int32_t v = (int32_t)v64;
+            long long s, e;
+            int32_t vb;
+            row_of<kBatched>(p, v, s, e, vb);
+            if (e > s && e < p.m && __ldg(p.ci + e - 1) >= __ldg(p.ci + e)) boundary++;
+            __stcg(p.colors + v, kFast ? 0 : -1);
+            const long long deg = e - s;
+            if (!kFast) {  // det round 1 has no FirstFit pass; count its scan here
+                acc.w += 1;
+                acc.d += (unsigned long long)deg;
+            }
+            if (deg <= p.light_max) {
+#pragma unroll
+                for (int z = 0; z < kLightUnroll; ++z)
+                    if (z == nlight) light[z] = v;
+                ++nlight;
+            } else if (deg <= p.chunk) {
+#pragma unroll
+                for (int z = 0; z < kLightUnroll; ++z)
+                    if (z == nmed) medium[z] = v;
+                ++nmed;
+            } else {
+                const unsigned slot = atomicAdd(&p.ctr->nslots, 1u);
+                const unsigned words = (unsigned)((deg + 2 + 31) / 32);
+                p.hvert[slot] = v;
+                p.hbase[slot] = atomicAdd(&p.ctr->hwords, words);
+                const unsigned nchunks = (unsigned)((deg + p.chunk - 1) / p.chunk);
+                const unsigned long long old =
+                    atomicAdd(&p.ctr->h64[1], (1ull << 32) | (unsigned long long)nchunks);
+                const unsigned k = (unsigned)(old >> 32);
+                p.hw[1][k] = (int32_t)slot;
+                p.hcb[1][k] = (unsigned)old;
+            }
+        }
+        unsigned long long dummy = 0;
+        block_push(nlight, light, &p.ctr->nl[1], p.lw[1], dummy);
+        block_push(nmed, medium, &p.ctr->nm[1], p.mw[1], dummy);
+    }
+    // block-reduce the two pair counts
+    for (int o = 16; o > 0; o >>= 1) {
+        bad += __shfl_xor_sync(kFull, bad, o);
+        boundary += __shfl_xor_sync(kFull, boundary, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicAdd(&p.ctr->unsorted_pairs, bad);
+        if (boundary) atomicAdd(&p.ctr->boundary_pairs, boundary);
+    }
+}
+
+__device__ void flush_kmax(const Params &p, int kloc) {
+    __shared__ int s_k[kWarps];
+    int k = kloc;
+    for (int o = 16; o > 0; o >>= 1) k = max(k, __shfl_xor_sync(kFull, k, o));
+    if ((threadIdx.x & 31) == 0) s_k[threadIdx.x >> 5] = k;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int b = 0;
+        for (int w = 0; w < kWarps; ++w) b = max(b, s_k[w]);
+        if (b > 0) atomicMax(&p.ctr->kmax, b);
+    }
+}
+
+__device__ void flush_stats(const Params &p, Acc &acc) {
+    unsigned long long v[4] = {acc.w, acc.d, acc.dscan, acc.next};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(kFull, v[j], o);
+    if ((threadIdx.x & 31) == 0) {
+        if (v[0]) atomicAdd(&p.ctr->sum_w, v[0]);
+        if (v[1]) atomicAdd(&p.ctr->sum_d, v[1]);
+        if (v[2]) atomicAdd(&p.ctr->sum_dscan, v[2]);
+        if (v[3]) atomicAdd(&p.ctr->sum_next, v[3]);
+    }
+}
+
+template <bool kFast, bool kBatched>
+__global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
+    Acc acc;
+    unsigned gen = 0;
+    Counters *ctr = p.ctr;
+    init_phase<kFast, kBatched>(p, acc);
+    if (!grid_barrier(p, gen)) { flush_stats(p, acc); return; }
+    const bool sorted = __ldcg(&ctr->unsorted_pairs) == __ldcg(&ctr->boundary_pairs);
+    const bool prefix = sorted && p.rule == 0;
+    long long r = 1;
+    for (;; ++r) {
+        const int par = (int)(r & 1), pn = par ^ 1;
+        const unsigned nl = __ldcg(&ctr->nl[par]);
+        const unsigned nm = __ldcg(&ctr->nm[par]);
+        const unsigned long long h64 = __ldcg(&ctr->h64[par]);
+        const unsigned long long total =
+            (unsigned long long)nl + nm + (unsigned long long)(h64 >> 32);
+        if (total == 0) break;
+        if (r > p.max_rounds) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctr->err, 0, kErrNoConvergence);
+            break;
+        }
+        const int ga = (int)((2 * r) % 3), gb = (int)((2 * r + 1) % 3), gc = (int)((2 * r + 2) % 3);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctr->nl[pn] = 0;
+            ctr->nm[pn] = 0;
+            ctr->h64[pn] = 0;
+            ctr->grab[gb][0] = 0;
+            ctr->grab[gb][1] = 0;
+            if (r <= kTraceCap) p.trace[r - 1] = (long long)total;
+        }
+        // ---- phase A: FirstFit over W_r (skipped in det round 1: all tentative colors are 1)
+        if (kFast || r > 1) {
+            const int kmax = __ldcg(&ctr->kmax);
+            hub_assign<kFast, kBatched>(p, par, h64, &ctr->grab[ga][1], kmax, acc);
+            medium_assign<kFast, kBatched>(p, p.mw[par], nm, &ctr->grab[ga][0], acc);
+            light_assign<kFast, kBatched>(p, p.lw[par], nl, acc);
+        }
+        if (!grid_barrier(p, gen)) break;
+        // ---- phase B: ConflictResolve over W_r, commit keepers, compact losers
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctr->grab[gc][0] = 0;
+            ctr->grab[gc][1] = 0;
+        }
+        int kloc = 0;
+        {
+            Acc b;
+            hub_detect<kFast, kBatched>(p, par, h64, &ctr->grab[gb][1], prefix, b);
+            medium_detect<kFast, kBatched>(p, p.mw[par], nm, p.mw[pn], &ctr->nm[pn],
+                                           &ctr->grab[gb][0], prefix, b);
+            light_detect<kFast, kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix, b);
+            acc.dscan += b.dscan;
+            acc.next += b.next;
+            kloc = b.kmax;
+        }
+        flush_kmax(p, kloc);
+        if (!grid_barrier(p, gen)) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->rounds = r - 1;
+    flush_stats(p, acc);
+}
+
+// ------------------------------------------------------------ batch helpers
+
+__global__ void fill_gid_kernel(int32_t *gid, const long long *vbase, int G) {
+    const int g = blockIdx.x;
+    if (g >= G) return;
+    const long long a = vbase[g], b = vbase[g + 1];
+    for (long long v = a + threadIdx.x; v < b; v += blockDim.x) gid[v] = g;
+}
+
+__global__ void segmented_max_kernel(const int32_t *colors, const long long *vbase, int G,
+                                     int32_t *out) {
+    const int g = blockIdx.x;
+    if (g >= G) return;
+    const long long a = vbase[g], b = vbase[g + 1];
+    int k = 0;
+    for (long long v = a + threadIdx.x; v < b; v += blockDim.x) k = max(k, colors[v]);
+    for (int o = 16; o > 0; o >>= 1) k = max(k, __shfl_xor_sync(kFull, k, o));
+    __shared__ int s_k[kWarps];
+    if ((threadIdx.x & 31) == 0) s_k[threadIdx.x >> 5] = k;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int b2 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b2 = max(b2, s_k[w]);
+        out[g] = b2;
+    }
+}
+
+// ------------------------------------------------------------ validation
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// flags[0]: bit0 offsets broken, bit1 id out of range, bit2 self-loop,
+// bit3 some row not strictly ascending, bit4 duplicate (ascending rows only),
+// bit5 asymmetric (exact search, ascending rows only);
+// flags[1] / flags[2]: sums of hash(v,w) / hash(w,v) over all entries.
+__global__ void validate_kernel(int32_t n, long long m, const int32_t *ro, const int32_t *ci,
+                                unsigned long long *flags, int exact_pass) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long f = 0, h1 = 0, h2 = 0;
+    for (long long v = warp; v < n; v += nwarps) {
+        const int s = ro[v], e = ro[v + 1];
+        if (e < s || s < 0 || e > m || (v == 0 && s != 0)) { f |= 1; continue; }
+        for (int i = s + lane; i < e; i += 32) {
+            const int w = ci[i];
+            if (w < 0 || w >= n) { f |= 2; continue; }
+            if (w == (int)v) f |= 4;
+            if (i > s) {
+                const int u = ci[i - 1];
+                if (u >= w) f |= 8;
+                if (u == w) f |= 16;
+            }
+            if (!exact_pass) {
+                h1 += mix64(((unsigned long long)(unsigned)v << 32) | (unsigned)w);
+                h2 += mix64(((unsigned long long)(unsigned)w << 32) | (unsigned)v);
+            } else {
+                int lo = ro[w], hi = ro[w + 1];
+                if (lo < 0 || hi > m || hi < lo) { f |= 1; continue; }
+                bool found = false;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const int x = ci[mid];
+                    if (x == (int)v) { found = true; break; }
+                    if (x < (int)v) lo = mid + 1;
+                    else hi = mid;
+                }
+                if (!found) f |= 32;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        f |= __shfl_xor_sync(kFull, f, o);
+        h1 += __shfl_xor_sync(kFull, h1, o);
+        h2 += __shfl_xor_sync(kFull, h2, o);
+    }
+    if (lane == 0) {
+        if (f) atomicOr(flags, f);
+        if (h1) atomicAdd(flags + 1, h1);
+        if (h2) atomicAdd(flags + 2, h2);
+    }
+}
+
+}  // namespace
+
+int occupancy_blocks_per_sm(bool fast, bool batched, int *out) {
+    cudaError_t e;
+    if (fast) {
+        e = batched ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          out, sgr_color_kernel<true, true>, kBlock, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          out, sgr_color_kernel<true, false>, kBlock, 0);
+    } else {
+        e = batched ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          out, sgr_color_kernel<false, true>, kBlock, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          out, sgr_color_kernel<false, false>, kBlock, 0);
+    }
+    return (int)e;
+}
+
+cudaError_t launch_color(const Params &p, bool fast, bool batched, int grid, cudaStream_t s) {
+    void *args[] = {(void *)&p};
+    const void *fn;
+    if (fast) fn = batched ? (const void *)sgr_color_kernel<true, true>
+                           : (const void *)sgr_color_kernel<true, false>;
+    else fn = batched ? (const void *)sgr_color_kernel<false, true>
+                      : (const void *)sgr_color_kernel<false, false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
+}
+
+cudaError_t launch_fill_gid(int32_t *gid, const long long *vbase_dev, int G, int32_t n,
+                            cudaStream_t s) {
+    (void)n;
+    if (G <= 0) return cudaSuccess;
+    fill_gid_kernel<<<G, 256, 0, s>>>(gid, vbase_dev, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_segmented_max(const int32_t *colors, const long long *vbase_dev, int G,
+                                 int32_t *out_dev, cudaStream_t s) {
+    if (G <= 0) return cudaSuccess;
+    segmented_max_kernel<<<G, 256, 0, s>>>(colors, vbase_dev, G, out_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(int32_t n, long long m, const int32_t *ro, const int32_t *ci,
+                            unsigned long long *flags_dev, cudaStream_t s) {
+    int blocks = (int)((((long long)n * 32) + 255) / 256);
+    if (blocks > 65535) blocks = 65535;
+    if (blocks < 1) blocks = 1;
+    validate_kernel<<<blocks, 256, 0, s>>>(n, m, ro, ci, flags_dev, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_validate_exact(int32_t n, long long m, const int32_t *ro, const int32_t *ci,
+                                  unsigned long long *flags_dev, cudaStream_t s) {
+    int blocks = (int)((((long long)n * 32) + 255) / 256);
+    if (blocks > 65535) blocks = 65535;
+    if (blocks < 1) blocks = 1;
+    validate_kernel<<<blocks, 256, 0, s>>>(n, m, ro, ci, flags_dev, 1);
+    return cudaGetLastError();
+}
+
+}  // namespace sgr

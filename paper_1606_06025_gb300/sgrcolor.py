@@ -1,0 +1,212 @@
+"""Python binding of libsgrcolor (ctypes over the C ABI in include/sgrcolor.h).
+
+Argument marshalling only: every step of the coloring runs in the library's
+CUDA kernels.  Device buffers may be passed as torch CUDA tensors or as raw
+integer addresses; host buffers as numpy arrays.  A non-OK status raises
+:class:`SgrError`.  Importing this module loads ``_build/libsgrcolor.so``
+(building it with nvcc if it is missing or stale) and fails loudly if that is
+not possible: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+SGR_OK = 0
+SGR_PENDING = 1
+SGR_ERR_INVALID_ARG = -1
+SGR_ERR_INVALID_GRAPH = -2
+SGR_ERR_OUT_OF_MEMORY = -3
+SGR_ERR_CUDA = -4
+SGR_ERR_NO_CONVERGENCE = -5
+SGR_ERR_TIMEOUT = -6
+SGR_ERR_NOT_FOUND = -7
+SGR_ERR_BUSY = -8
+
+SGR_MODE_DETERMINISTIC = 0
+SGR_MODE_FAST = 1
+SGR_RULE_LOW_KEEPS = 0 << 4
+SGR_RULE_LOW_LOSES = 1 << 4
+SGR_RULE_DEGREE = 2 << 4
+
+MODES = {"det": SGR_MODE_DETERMINISTIC, "fast": SGR_MODE_FAST}
+RULES = {"low_keeps": SGR_RULE_LOW_KEEPS, "low_loses": SGR_RULE_LOW_LOSES,
+         "degree": SGR_RULE_DEGREE}
+
+# every symbol include/sgrcolor.h declares (checked by the tests)
+EXPORTS = ["sgr_color", "sgr_color_host", "sgr_color_batch", "sgr_validate_csr",
+           "sgr_last_stats", "sgr_get_tuning", "sgr_set_tuning", "sgr_release_scratch",
+           "sgr_status_string", "sgr_version"]
+
+
+class SgrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("sum_w", ctypes.c_int64),
+                ("sum_d", ctypes.c_int64), ("sum_dscan", ctypes.c_int64),
+                ("sum_next", ctypes.c_int64), ("num_colors", ctypes.c_int32),
+                ("rows_sorted", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("device_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("group_lanes", ctypes.c_int32), ("light_max", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+def _load():
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    pi32 = ctypes.POINTER(ctypes.c_int32)
+    lib.sgr_color.argtypes = [i32, vp, vp, vp, pi32, ctypes.c_int, vp]
+    lib.sgr_color_host.argtypes = [i32, vp, vp, vp, pi32, ctypes.c_int, vp]
+    lib.sgr_color_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
+    lib.sgr_validate_csr.argtypes = [i32, vp, vp, pi32, vp]
+    lib.sgr_last_stats.argtypes = [ctypes.POINTER(Stats)]
+    lib.sgr_get_tuning.argtypes = [ctypes.POINTER(Tuning)]
+    lib.sgr_set_tuning.argtypes = [ctypes.POINTER(Tuning)]
+    lib.sgr_release_scratch.argtypes = []
+    lib.sgr_status_string.argtypes = [ctypes.c_int]
+    lib.sgr_status_string.restype = ctypes.c_char_p
+    lib.sgr_version.argtypes = []
+    for name in EXPORTS:
+        if name != "sgr_status_string":
+            getattr(lib, name).restype = ctypes.c_int
+    del i64
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _build.LIB_PATH
+
+
+def _addr(x):
+    """Device or host address of a tensor / array / int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def status_string(status: int) -> str:
+    return _lib.sgr_status_string(status).decode()
+
+
+def _check(rc: int, where: str) -> int:
+    if rc != SGR_OK:
+        raise SgrError(rc, where)
+    return rc
+
+
+def _mode(mode) -> int:
+    if isinstance(mode, int):
+        return mode
+    parts = mode.split("+") if isinstance(mode, str) else list(mode)
+    m = 0
+    for p in parts:
+        m |= MODES[p] if p in MODES else RULES[p]
+    return m
+
+
+def sgr_color(n, row_offsets, col_idx, colors_out, mode=0, stream=None) -> int:
+    """Color one graph held in device memory; returns the number of colors."""
+    k = ctypes.c_int32(0)
+    _check(_lib.sgr_color(int(n), _addr(row_offsets), _addr(col_idx), _addr(colors_out),
+                          ctypes.byref(k), _mode(mode), _stream(stream)), "sgr_color")
+    return int(k.value)
+
+
+def sgr_color_host(n, row_offsets, col_idx, colors_out, mode=0, stream=None) -> int:
+    """Color one graph held in host memory (numpy int32 arrays)."""
+    k = ctypes.c_int32(0)
+    _check(_lib.sgr_color_host(int(n), _addr(row_offsets), _addr(col_idx), _addr(colors_out),
+                               ctypes.byref(k), _mode(mode), _stream(stream)), "sgr_color_host")
+    return int(k.value)
+
+
+def sgr_color_batch(G, vtx_off, edge_off, row_offsets, col_idx, colors_out, num_colors,
+                    mode=0, stream=None) -> None:
+    """Color G packed graphs; vtx_off / edge_off / num_colors are host arrays."""
+    _check(_lib.sgr_color_batch(int(G), _addr(vtx_off), _addr(edge_off), _addr(row_offsets),
+                                _addr(col_idx), _addr(colors_out), _addr(num_colors),
+                                _mode(mode), _stream(stream)), "sgr_color_batch")
+
+
+def sgr_validate_csr(n, row_offsets, col_idx, stream=None):
+    """Returns (status, rows_sorted) without raising on SGR_ERR_INVALID_GRAPH."""
+    srt = ctypes.c_int32(-1)
+    rc = _lib.sgr_validate_csr(int(n), _addr(row_offsets), _addr(col_idx), ctypes.byref(srt),
+                               _stream(stream))
+    if rc not in (SGR_OK, SGR_ERR_INVALID_GRAPH):
+        raise SgrError(rc, "sgr_validate_csr")
+    return rc, int(srt.value)
+
+
+def sgr_last_stats() -> dict:
+    s = Stats()
+    _check(_lib.sgr_last_stats(ctypes.byref(s)), "sgr_last_stats")
+    return s.as_dict()
+
+
+def sgr_get_tuning() -> dict:
+    t = Tuning()
+    _check(_lib.sgr_get_tuning(ctypes.byref(t)), "sgr_get_tuning")
+    return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+
+def sgr_set_tuning(group_lanes=0, light_max=0, chunk=0, blocks_per_sm=0) -> None:
+    t = Tuning(group_lanes, light_max, chunk, blocks_per_sm)
+    _check(_lib.sgr_set_tuning(ctypes.byref(t)), "sgr_set_tuning")
+
+
+def sgr_release_scratch() -> None:
+    _check(_lib.sgr_release_scratch(), "sgr_release_scratch")
+
+
+def sgr_version() -> int:
+    return int(_lib.sgr_version())
+
+
+# ------------------------------------------------------------ torch helpers
+
+def color(row_offsets, col_idx, mode=0, stream=None, out=None):
+    """Color a graph given as torch CUDA int32 tensors; returns (colors, k)."""
+    import torch
+    n = row_offsets.numel() - 1
+    if out is None:
+        out = torch.empty(max(n, 0), dtype=torch.int32, device=row_offsets.device)
+    k = sgr_color(n, row_offsets, col_idx, out, mode, stream)
+    return out, k
+
+
+def loaded_library_path() -> str:
+    return os.path.realpath(LIB_PATH)

@@ -1,0 +1,65 @@
+"""The C-ABI library loads and exports every symbol the header declares (CPU)."""
+import os
+import re
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sgrcolor.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sgr_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    for must in ["sgr_color", "sgr_color_batch", "sgr_color_host", "sgr_validate_csr",
+                 "sgr_last_stats", "sgr_status_string"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1606_06025_gb300 import sgrcolor
+    out = subprocess.run(["nm", "-D", "--defined-only", sgrcolor.LIB_PATH],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (sgr_[a-z_]+)\b", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    assert set(sgrcolor.EXPORTS) == set(declared_functions())
+
+
+def test_host_only_calls_without_gpu():
+    from paper_1606_06025_gb300 import sgrcolor
+    assert sgrcolor.sgr_version() >= 10000
+    assert sgrcolor.status_string(0) == "SGR_OK"
+    assert sgrcolor.status_string(-6) == "SGR_ERR_TIMEOUT"
+    assert sgrcolor.status_string(12345) == "SGR_UNKNOWN_STATUS"
+    t = sgrcolor.sgr_get_tuning()
+    assert t["group_lanes"] in (1, 2, 4, 8, 16, 32)
+    # invalid tunings are refused, valid ones round-trip
+    for bad in [dict(group_lanes=3), dict(light_max=64), dict(chunk=10), dict(blocks_per_sm=-1)]:
+        try:
+            sgrcolor.sgr_set_tuning(**bad)
+        except sgrcolor.SgrError as e:
+            assert e.status == sgrcolor.SGR_ERR_INVALID_ARG
+        else:
+            raise AssertionError(f"accepted {bad}")
+    sgrcolor.sgr_set_tuning(group_lanes=8)
+    assert sgrcolor.sgr_get_tuning()["group_lanes"] == 8
+    sgrcolor.sgr_set_tuning(**t)
+    assert sgrcolor.sgr_get_tuning() == t
+
+
+def test_argument_checks_before_any_device_work():
+    from paper_1606_06025_gb300 import sgrcolor
+    import ctypes
+    k = ctypes.c_int32(7)
+    # n < 0, bad mode bits, null out-pointer: refused without touching a device
+    assert sgrcolor._lib.sgr_color(-1, None, None, None, ctypes.byref(k), 0, None) == -1
+    assert sgrcolor._lib.sgr_color(1, None, None, None, ctypes.byref(k), 0x100, None) == -1
+    assert sgrcolor._lib.sgr_color(1, None, None, None, None, 0, None) == -1
+    # n == 0 is a valid empty graph
+    assert sgrcolor._lib.sgr_color(0, None, None, None, ctypes.byref(k), 0, None) == 0
+    assert k.value == 0
