@@ -283,8 +283,13 @@ def run_ours(args, rank, world, local):
     ro_h = torch.from_numpy(g.row_offsets).pin_memory().numpy()
     ci_h = torch.from_numpy(g.col_idx).pin_memory().numpy()
     col_h = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+    if args.timeline and rank == 0:
+        tw, ta, tb, tinit = lib.sgr_last_trace()
+        with open(args.timeline, "w") as f:
+            json.dump({"workload": args.workload, "mode": mode, "init_ns": tinit,
+                       "w": tw.tolist(), "end_a_ns": ta.tolist(), "end_b_ns": tb.tolist()}, f)
     e2e_ms = []
-    for i in range(args.warmup + args.steps):
+    for i in range(0 if args.no_e2e else args.warmup + args.steps):
         flush.fill_(1)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -295,7 +300,7 @@ def run_ours(args, rank, world, local):
         e1.synchronize()
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_ms)
+    e2e_total = sum(e2e_ms) if e2e_ms else float("nan")
     if world > 1:
         t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -358,6 +363,8 @@ def main():
     ap.add_argument("--workload", choices=list(WORKLOADS), default="rmat20")
     ap.add_argument("--mode", choices=["det", "fast"], default="det")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--timeline", default="", help="write the per-round device timeline here")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

@@ -117,9 +117,10 @@ typedef struct {
  * Returns SGR_OK, SGR_ERR_INVALID_ARG (null pointer with n > 0, unknown mode,
  * unaligned col_idx), SGR_ERR_INVALID_GRAPH (row_offsets[0] != 0 or m < 0),
  * SGR_ERR_OUT_OF_MEMORY, SGR_ERR_CUDA, SGR_ERR_TIMEOUT or
- * SGR_ERR_NO_CONVERGENCE.  Behaviour on a CSR that is not symmetric or has
- * out-of-range ids is unspecified but ends (round cap n+1); use
- * sgr_validate_csr to check a graph first.
+ * SGR_ERR_NO_CONVERGENCE.  On a CSR that breaks the contract (not symmetric,
+ * ids outside [0, n)) the coloring is unspecified, but the call ends (round
+ * cap n + 1) and never reads outside the given arrays: out-of-range ids are
+ * skipped.  sgr_validate_csr checks a graph first.
  */
 int sgr_color(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
               int32_t *colors_out, int32_t *num_colors, int mode, sgr_stream_t stream);
@@ -163,6 +164,17 @@ int sgr_validate_csr(int32_t n, const int32_t *row_offsets, const int32_t *col_i
 /* Statistics of the last sgr_color / sgr_color_host / sgr_color_batch call
  * on this host thread. */
 int sgr_last_stats(sgr_stats *out);
+
+/*
+ * Device timeline of the last coloring launch on the current device: for
+ * round r (0-based, at most cap_rounds and 65536 rounds) out[3r] = |W_r|,
+ * out[3r+1] / out[3r+2] = nanoseconds from kernel start to the end of the
+ * FirstFit / ConflictResolve phase (read from %globaltimer by CTA 0 after each
+ * grid barrier).  *init_ns (HOST, may be NULL) receives the end of the
+ * initial binning pass.  Returns the number of rounds written (>= 0) or a
+ * negative status.  Valid until the next call on the device.  out is HOST.
+ */
+int sgr_last_trace(int64_t *out, int64_t cap_rounds, int64_t *init_ns);
 
 /* Get / set the process-wide tuning used by later calls. */
 int sgr_get_tuning(sgr_tuning *out);

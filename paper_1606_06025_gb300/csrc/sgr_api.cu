@@ -69,6 +69,9 @@ struct DevCtx {
     int64_t *host_small = nullptr;      // pinned staging (offsets, flags)
     size_t host_small_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    const long long *last_trace = nullptr;  // device timeline of the last launch
+    long long last_rounds = 0;
+    long long last_t_init = 0;
     std::mutex mu;
     bool ready = false;
 };
@@ -176,7 +179,7 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     unsigned *hconf = (unsigned *)take(sp.hub_max * 4);
     unsigned *hbits = (unsigned *)take(sp.hub_words * 4);
     if (zero_bytes) *zero_bytes = off;
-    long long *trace = (long long *)take(sizeof(long long) * sgr::kTraceCap);
+    long long *trace = (long long *)take(sizeof(long long) * sgr::kTraceCap * sgr::kTraceFields);
     int32_t *lw0 = (int32_t *)take((size_t)j.n * 4), *lw1 = (int32_t *)take((size_t)j.n * 4);
     int32_t *mw0 = (int32_t *)take((size_t)j.n * 4), *mw1 = (int32_t *)take((size_t)j.n * 4);
     int32_t *hw0 = (int32_t *)take(sp.hub_max * 4), *hw1 = (int32_t *)take(sp.hub_max * 4);
@@ -268,6 +271,9 @@ int run_job(DevCtx *c, Job &j, int mode, cudaStream_t st, int32_t *k_out) {
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
     const Counters h = *c->host_ctr;
     fill_stats(h, ms, grid, h.kmax);
+    c->last_trace = p.trace;
+    c->last_rounds = h.rounds;
+    c->last_t_init = h.t_init_ns;
     if (h.err != 0) return h.err;
     if (k_out) *k_out = h.kmax;
     return SGR_OK;
@@ -331,6 +337,23 @@ int sgr_last_stats(sgr_stats *out) {
     return SGR_OK;
 }
 
+int sgr_last_trace(int64_t *out, int64_t cap_rounds, int64_t *init_ns) {
+    if (!out || cap_rounds < 0) return SGR_ERR_INVALID_ARG;
+    DevCtx *c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc != SGR_OK) return rc;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->last_trace) return 0;
+    long long r = std::min<long long>(std::min<long long>(c->last_rounds, sgr::kTraceCap), cap_rounds);
+    if (r > 0) {
+        cudaError_t e = cudaMemcpy(out, c->last_trace, (size_t)r * sgr::kTraceFields * 8,
+                                   cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    if (init_ns) *init_ns = c->last_t_init;
+    return (int)r;
+}
+
 int sgr_release_scratch(void) {
     DevCtx *c = nullptr;
     int rc = get_ctx(&c);
@@ -338,6 +361,7 @@ int sgr_release_scratch(void) {
     std::lock_guard<std::mutex> lk(c->mu);
     c->scratch.release();
     c->io.release();
+    c->last_trace = nullptr;
     return SGR_OK;
 }
 

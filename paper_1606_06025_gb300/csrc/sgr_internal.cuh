@@ -25,7 +25,8 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kLightUnroll = 4;                  // 32-vertex sub-tiles per warp and light tile
 constexpr int kLightTile = kBlock * kLightUnroll;
 constexpr int kMediumBatch = 4;                  // medium vertices per warp grab
-constexpr int kTraceCap = 1 << 16;               // per-round |W_r| entries recorded
+constexpr int kTraceCap = 1 << 16;               // rounds recorded in the timeline
+constexpr int kTraceFields = 3;                  // |W_r|, ns at end of phase A, ns at end of phase B
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;  // bounded device waits
 
 // status codes mirrored from sgrcolor.h (device code cannot include it twice)
@@ -47,7 +48,8 @@ struct Counters {
     unsigned long long boundary_pairs;   // ... of them across row boundaries
     unsigned long long sum_w, sum_d, sum_dscan, sum_next;
     long long rounds;
-    long long pad[4];
+    long long t_init_ns;            // globaltimer: end of the init pass (after its barrier)
+    long long pad[3];
 };
 
 struct Params {

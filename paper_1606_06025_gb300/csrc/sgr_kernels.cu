@@ -761,8 +761,11 @@ __global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
     Acc acc;
     unsigned gen = 0;
     Counters *ctr = p.ctr;
+    const bool recorder = blockIdx.x == 0 && threadIdx.x == 0;
+    const unsigned long long t0 = globaltimer();
     init_phase<kFast, kBatched>(p, acc);
     if (!grid_barrier(p, gen)) { flush_stats(p, acc); return; }
+    if (recorder) ctr->t_init_ns = (long long)(globaltimer() - t0);
     const bool sorted = __ldcg(&ctr->unsorted_pairs) == __ldcg(&ctr->boundary_pairs);
     const bool prefix = sorted && p.rule == 0;
     long long r = 1;
@@ -785,7 +788,7 @@ __global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
             ctr->h64[pn] = 0;
             ctr->grab[gb][0] = 0;
             ctr->grab[gb][1] = 0;
-            if (r <= kTraceCap) p.trace[r - 1] = (long long)total;
+            if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)total;
         }
         // ---- phase A: FirstFit over W_r (skipped in det round 1: all tentative colors are 1)
         if (kFast || r > 1) {
@@ -795,6 +798,8 @@ __global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
             light_assign<kFast, kBatched>(p, p.lw[par], nl, acc);
         }
         if (!grid_barrier(p, gen)) break;
+        if (recorder && r <= kTraceCap)
+            p.trace[kTraceFields * (r - 1) + 1] = (long long)(globaltimer() - t0);
         // ---- phase B: ConflictResolve over W_r, commit keepers, compact losers
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             ctr->grab[gc][0] = 0;
@@ -813,6 +818,8 @@ __global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
         }
         flush_kmax(p, kloc);
         if (!grid_barrier(p, gen)) break;
+        if (recorder && r <= kTraceCap)
+            p.trace[kTraceFields * (r - 1) + 2] = (long long)(globaltimer() - t0);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->rounds = r - 1;
     flush_stats(p, acc);

@@ -37,7 +37,7 @@ RULES = {"low_keeps": SGR_RULE_LOW_KEEPS, "low_loses": SGR_RULE_LOW_LOSES,
 
 # every symbol include/sgrcolor.h declares (checked by the tests)
 EXPORTS = ["sgr_color", "sgr_color_host", "sgr_color_batch", "sgr_validate_csr",
-           "sgr_last_stats", "sgr_get_tuning", "sgr_set_tuning", "sgr_release_scratch",
+           "sgr_last_stats", "sgr_last_trace", "sgr_get_tuning", "sgr_set_tuning", "sgr_release_scratch",
            "sgr_status_string", "sgr_version"]
 
 
@@ -73,6 +73,7 @@ def _load():
     lib.sgr_color_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
     lib.sgr_validate_csr.argtypes = [i32, vp, vp, pi32, vp]
     lib.sgr_last_stats.argtypes = [ctypes.POINTER(Stats)]
+    lib.sgr_last_trace.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64)]
     lib.sgr_get_tuning.argtypes = [ctypes.POINTER(Tuning)]
     lib.sgr_set_tuning.argtypes = [ctypes.POINTER(Tuning)]
     lib.sgr_release_scratch.argtypes = []
@@ -82,7 +83,6 @@ def _load():
     for name in EXPORTS:
         if name != "sgr_status_string":
             getattr(lib, name).restype = ctypes.c_int
-    del i64
     return lib
 
 
@@ -175,6 +175,19 @@ def sgr_last_stats() -> dict:
     s = Stats()
     _check(_lib.sgr_last_stats(ctypes.byref(s)), "sgr_last_stats")
     return s.as_dict()
+
+
+def sgr_last_trace(cap_rounds: int = 1 << 16):
+    """Per-round timeline of the last launch: (W sizes, ns at end of phase A,
+    ns at end of phase B, ns at end of the init pass) as numpy arrays."""
+    import numpy as np
+    buf = np.zeros(3 * cap_rounds, dtype=np.int64)
+    init = ctypes.c_int64(0)
+    r = _lib.sgr_last_trace(buf.ctypes.data, cap_rounds, ctypes.byref(init))
+    if r < 0:
+        raise SgrError(r, "sgr_last_trace")
+    t = buf[:3 * r].reshape(r, 3)
+    return t[:, 0].copy(), t[:, 1].copy(), t[:, 2].copy(), int(init.value)
 
 
 def sgr_get_tuning() -> dict:
