@@ -95,11 +95,11 @@ typedef struct {
 /* Load-balance and launch parameters (Sect. 3.2 thread coarsening, Sect. 3.3
  * load balancing).  Zero fields mean "library default". */
 typedef struct {
-    int32_t group_lanes;   /* lanes per low-degree vertex: 1, 2, 4, 8, 16 or 32 */
-    int32_t light_max;     /* degree bound of the group-per-vertex bin, <= 63 */
+    int32_t light_max;     /* degree bound of the lane-per-vertex bin, 1..32 */
     int32_t chunk;         /* edges per warp work item of the hub bin; also the
                               degree bound of the warp-per-vertex bin (>= 64) */
     int32_t blocks_per_sm; /* persistent CTAs per SM (capped by occupancy) */
+    int32_t reserved;      /* must be 0 */
 } sgr_tuning;
 
 /*

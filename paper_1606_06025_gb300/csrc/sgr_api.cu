@@ -80,7 +80,7 @@ std::mutex g_ctx_mu;
 std::vector<DevCtx *> g_ctx;
 
 std::mutex g_tune_mu;
-sgr_tuning g_tune = {4, 32, 2048, 0};
+sgr_tuning g_tune = {32, 2048, 0, 0};
 
 thread_local sgr_stats t_stats;
 
@@ -207,7 +207,6 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         p->hconf = hconf;
         p->ctr = ctr;
         p->trace = trace;
-        p->G = t.group_lanes;
         p->light_max = t.light_max;
         p->chunk = t.chunk;
     }
@@ -310,13 +309,9 @@ int sgr_get_tuning(sgr_tuning *out) {
 int sgr_set_tuning(const sgr_tuning *in) {
     if (!in) return SGR_ERR_INVALID_ARG;
     sgr_tuning t = current_tuning();
-    if (in->group_lanes) {
-        const int g = in->group_lanes;
-        if (g < 1 || g > 32 || (g & (g - 1))) return SGR_ERR_INVALID_ARG;
-        t.group_lanes = g;
-    }
+    if (in->reserved) return SGR_ERR_INVALID_ARG;
     if (in->light_max) {
-        if (in->light_max < 1 || in->light_max > 63) return SGR_ERR_INVALID_ARG;
+        if (in->light_max < 1 || in->light_max > sgr::kLightMaxStage) return SGR_ERR_INVALID_ARG;
         t.light_max = in->light_max;
     }
     if (in->chunk) {

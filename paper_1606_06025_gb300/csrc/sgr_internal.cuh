@@ -11,7 +11,7 @@
 //   hub slots            hvert (slot -> vertex), hbase (offset of the slot's
 //                        forbidden-color bitmap in hbits), hdone / hconf
 //                        (per-round completion counter and conflict flag).
-//   Counters             list sizes, work-grab counters, grid barrier, max
+//   Counters             list sizes, grid barrier, max
 //                        color so far, error code, statistics.
 #pragma once
 
@@ -24,7 +24,7 @@ constexpr int kBlock = 256;                      // threads per CTA
 constexpr int kWarps = kBlock / 32;
 constexpr int kLightUnroll = 4;                  // 32-vertex sub-tiles per warp and light tile
 constexpr int kLightTile = kBlock * kLightUnroll;
-constexpr int kMediumBatch = 4;                  // medium vertices per warp grab
+constexpr int kLightMaxStage = 32;               // largest light degree (staged rows per lane)
 constexpr int kTraceCap = 1 << 16;               // rounds recorded in the timeline
 constexpr int kTraceFields = 3;                  // |W_r|, ns at end of phase A, ns at end of phase B
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;  // bounded device waits
@@ -37,7 +37,6 @@ struct Counters {
     unsigned int nl[2];             // light list sizes by round parity
     unsigned int nm[2];             // medium list sizes
     unsigned long long h64[2];      // hub lists: (entries << 32) | total chunks
-    unsigned int grab[3][2];        // dynamic work-grab counters (medium, hub), 3 phases rotating
     unsigned int bar_count;         // grid barrier arrivals
     unsigned int bar_gen;           // grid barrier generation
     unsigned int nslots;            // hub slots handed out
@@ -72,8 +71,7 @@ struct Params {
     unsigned int *hconf;
     Counters *ctr;
     long long *trace;
-    int G;                     // lanes per light vertex (power of two <= 32)
-    int light_max;             // <= 63
+    int light_max;             // <= kLightMaxStage
     int chunk;                 // hub chunk edges; medium degree bound
     int rule;                  // 0 low keeps, 1 low loses, 2 degree
     long long max_rounds;

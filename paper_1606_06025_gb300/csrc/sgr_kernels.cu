@@ -28,7 +28,8 @@
 // judge-before-clear reading: a loser still counts against higher ids.
 //
 // Load balance (Sect. 3.3, Merrill's thread / warp / CTA mapping): a vertex
-// of degree <= light_max is handled by a group of G lanes, a vertex of degree
+// of degree <= light_max is handled by one lane after its warp staged the
+// rows of 32 such vertices in shared memory, a vertex of degree
 // <= chunk by one warp, a hub by ceil(deg / chunk) warp-sized work items that
 // merge their forbidden-color bitmaps with atomicOr; the item that finishes
 // last (completion counter) resolves the vertex.
@@ -150,30 +151,6 @@ struct Acc {
 
 // ------------------------------------------------------------ forbidden masks
 
-// Colors 1..64 of the entries [s, e) this lane covers (lanes gl, gl+G, ...),
-// as bits 0..63.  Only positive colors forbid (final colors in det mode).
-__device__ __forceinline__ unsigned long long mask64_lane(const int32_t *__restrict__ ci,
-                                                          long long m,
-                                                          const int32_t *colors, long long s,
-                                                          long long e, int32_t vb, int gl,
-                                                          int G, int32_t nv) {
-    unsigned long long mask = 0;
-    for (long long q = (s >> 2) + gl; (q << 2) < e; q += G) {
-        const int4 x = load4(ci, q, m);
-        const long long i0 = q << 2;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long i = i0 + k;
-            const int32_t w = vb + elem(x, k);
-            if (i >= s && i < e && (unsigned)w < (unsigned)nv) {
-                const int c = __ldcg(colors + w);
-                if (c > 0 && c <= 64) mask |= 1ull << (c - 1);
-            }
-        }
-    }
-    return mask;
-}
-
 // Colors wb+1 .. wb+256 of entries [a, b) (lanes lane0, lane0+stride, ...)
 // into eight 32-bit words.
 __device__ __forceinline__ void mask256_lane(const int32_t *__restrict__ ci, long long m,
@@ -238,43 +215,6 @@ __device__ __forceinline__ int warp_first_fit(const int32_t *__restrict__ ci, lo
     }
 }
 
-// ------------------------------------------------------------ conflict scan
-
-// Does v (tentative color c, degree dv) lose in this round?  Scans the
-// entries [a, b) covered by this lane (lanes lane0, lane0+stride, ...).
-// With ascending rows and the low-keeps rule only ids below v matter, so the
-// scan stops at the first entry >= v.  Stops early at a conflict.
-template <bool kFast, bool kBatched>
-__device__ __forceinline__ bool conflict_lane(const Params &p, const int32_t *colors, int32_t v,
-                                              int c, int32_t dv, long long a, long long b,
-                                              int32_t vb, int lane0, int stride, bool prefix,
-                                              unsigned long long &scanned) {
-    for (long long q = (a >> 2) + lane0; (q << 2) < b; q += stride) {
-        const int4 x = load4(p.ci, q, p.m);
-        const long long i0 = q << 2;
-        bool stop = false;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long i = i0 + k;
-            if (i >= a && i < b) {
-                const int32_t w = vb + elem(x, k);
-                if (prefix && w >= v) {
-                    stop = true;
-                } else if ((unsigned)w < (unsigned)p.n) {
-                    if (p.rule == 0 && w > v) continue;
-                    if (p.rule == 1 && w < v) continue;
-                    scanned++;
-                    const int cw = __ldcg(colors + w);
-                    const int mag = kFast ? cw : (cw < 0 ? -cw : cw);
-                    if (mag == c && w != v && loses_to<kBatched>(p, v, w, dv)) return true;
-                }
-            }
-        }
-        if (stop) break;
-    }
-    return false;
-}
-
 // ------------------------------------------------------------ block compaction
 
 // Each thread pushes cnt (<= kLightUnroll) items; one atomicAdd per CTA.
@@ -310,63 +250,249 @@ __device__ __forceinline__ void block_push(int cnt, const int32_t (&items)[kLigh
     __syncthreads();
 }
 
-__device__ __forceinline__ unsigned long long group_or64(unsigned long long x, int G) {
-    for (int o = G >> 1; o > 0; o >>= 1) x |= __shfl_xor_sync(kFull, x, o);
-    return x;
-}
+// ------------------------------------------------------------ light vertices
+//
+// A warp takes 32 consecutive worklist entries (one vertex per lane), copies
+// their rows into shared memory with coalesced loads (one streaming copy when
+// the rows are contiguous, i.e. consecutive vertex ids; otherwise a flattened
+// copy where each lane finds the row that owns its position), then every lane
+// works on its own row with independent color gathers in flight.
 
-__device__ __forceinline__ bool group_any(bool x, int G) {
-    unsigned v = x ? 1u : 0u;
-    for (int o = G >> 1; o > 0; o >>= 1) v |= __shfl_xor_sync(kFull, v, o);
-    return v != 0;
+// Stage rows [s, s + deg) of the warp's vertices (deg <= 32 each) into sbuf;
+// returns this lane's offset.  All lanes of the warp must call it.
+__device__ __forceinline__ int stage_rows(const int32_t *__restrict__ ci, long long m, long long s,
+                                          int deg, bool act, int32_t *sbuf) {
+    const int lane = threadIdx.x & 31;
+    int incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int pre = incl - deg;
+    const int total = __shfl_sync(kFull, incl, 31);
+    const long long e = s + deg;
+    const long long s_next = __shfl_down_sync(kFull, s, 1);
+    const bool act_next = __shfl_down_sync(kFull, act ? 1 : 0, 1) != 0;
+    const bool contig = __all_sync(kFull, !act || lane == 31 || !act_next || e == s_next);
+    if (contig) {
+        const long long s0 = __shfl_sync(kFull, s, 0);
+        const long long end = s0 + total;
+        for (long long q = (s0 >> 2) + lane; (q << 2) < end; q += 32) {
+            const int4 x = load4(ci, q, m);
+            const long long i0 = q << 2;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long i = i0 + k;
+                if (i >= s0 && i < end) sbuf[i - s0] = elem(x, k);
+            }
+        }
+    } else {
+        for (int p0 = 0; p0 < total; p0 += 32) {
+            const int pos = p0 + lane;
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int cand = lo + step;
+                if (__shfl_sync(kFull, pre, cand) <= pos) lo = cand;
+            }
+            const long long src = __shfl_sync(kFull, s, lo) + (pos - __shfl_sync(kFull, pre, lo));
+            if (pos < total) sbuf[pos] = __ldg(ci + src);
+        }
+    }
+    __syncwarp();
+    return pre;
 }
-
-// ------------------------------------------------------------ phase A pieces
 
 template <bool kFast, bool kBatched>
-__device__ void light_assign(const Params &p, const int32_t *list, unsigned cnt, Acc &acc) {
+__device__ void light_assign(const Params &p, const int32_t *list, unsigned cnt,
+                             int32_t *sbuf, Acc &acc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int G = p.G, gl = lane & (G - 1), per = 32 / G;
     const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
     for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const unsigned base = t * kLightTile + warp * (32 * kLightUnroll);
-        for (int step = 0; step < kLightUnroll * G; ++step) {
-            const unsigned idx = base + step * per + lane / G;
+        for (int u = 0; u < kLightUnroll; ++u) {
+            const unsigned idx = t * kLightTile + (u * kWarps + warp) * 32 + lane;
             const bool act = idx < cnt;
             int32_t v = 0, vb = 0;
             long long s = 0, e = 0;
-            unsigned long long mask = 0;
             if (act) {
                 v = __ldcg(list + idx);
                 row_of<kBatched>(p, v, s, e, vb);
-                mask = mask64_lane(p.ci, p.m, p.colors, s, e, vb, gl, G, p.n);
             }
-            mask = group_or64(mask, G);
-            if (act && gl == 0) {
+            const int deg = (int)(e - s);
+            const int pre = stage_rows(p.ci, p.m, s, deg, act, sbuf);
+            if (act) {
+                unsigned long long mask = 0;
+#pragma unroll 8
+                for (int j = 0; j < deg; ++j) {
+                    const int32_t w = vb + sbuf[pre + j];
+                    if ((unsigned)w < (unsigned)p.n) {
+                        const int c = __ldcg(p.colors + w);
+                        if (c > 0 && c <= 64) mask |= 1ull << (c - 1);
+                    }
+                }
                 const int c = __ffsll((long long)~mask);
                 __stcg(p.colors + v, kFast ? c : -c);
                 acc.w += 1;
-                acc.d += (unsigned long long)(e - s);
+                acc.d += (unsigned long long)deg;
             }
+            __syncwarp();
         }
     }
 }
 
+// Conflict test of one lane's vertex against its staged row.
 template <bool kFast, bool kBatched>
-__device__ void medium_assign(const Params &p, const int32_t *list, unsigned cnt,
-                              unsigned *grab, Acc &acc) {
+__device__ __forceinline__ bool light_conflict(const Params &p, const int32_t *row, int deg,
+                                               int32_t v, int32_t vb, int c, bool prefix,
+                                               unsigned long long &scanned) {
+    bool conf = false;
+    for (int j0 = 0; j0 < deg && !conf; j0 += 8) {
+        int cw[8];
+        int32_t ww[8];
+        bool ok[8];
+        bool past = false;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int j = j0 + k;
+            ww[k] = j < deg ? vb + row[j] : -1;
+            ok[k] = j < deg && (unsigned)ww[k] < (unsigned)p.n;
+            if (prefix && ok[k] && ww[k] >= v) {
+                ok[k] = false;
+                past = true;
+            }
+            if (p.rule == 0 && ww[k] > v) ok[k] = false;
+            if (p.rule == 1 && ww[k] < v) ok[k] = false;
+            cw[k] = ok[k] ? __ldcg(p.colors + ww[k]) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (!ok[k]) continue;
+            scanned++;
+            const int mag = kFast ? cw[k] : (cw[k] < 0 ? -cw[k] : cw[k]);
+            if (mag == c && loses_to<kBatched>(p, v, ww[k], deg)) conf = true;
+        }
+        if (past) break;
+    }
+    return conf;
+}
+
+template <bool kFast, bool kBatched>
+__device__ void light_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
+                             unsigned *out_cnt, bool prefix, int32_t *sbuf, Acc &acc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
+    for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
+        int32_t items[kLightUnroll];
+        int n_items = 0;
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) items[u] = 0;
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) {
+            const unsigned idx = t * kLightTile + (u * kWarps + warp) * 32 + lane;
+            const bool act = idx < cnt;
+            int32_t v = 0, vb = 0;
+            long long s = 0, e = 0;
+            if (act) {
+                v = __ldcg(list + idx);
+                row_of<kBatched>(p, v, s, e, vb);
+            }
+            const int deg = (int)(e - s);
+            const int pre = stage_rows(p.ci, p.m, s, deg, act, sbuf);
+            if (act) {
+                const int own = __ldcg(p.colors + v);
+                const int c = kFast ? own : -own;
+                const bool conf =
+                    light_conflict<kFast, kBatched>(p, sbuf + pre, deg, v, vb, c, prefix, acc.dscan);
+                if (conf) {
+                    if (kFast) __stcg(p.colors + v, 0);
+#pragma unroll
+                    for (int z = 0; z < kLightUnroll; ++z)
+                        if (z == n_items) items[z] = v;
+                    ++n_items;
+                } else {
+                    if (!kFast) __stcg(p.colors + v, c);
+                    acc.kmax = max(acc.kmax, c);
+                }
+            }
+            __syncwarp();
+        }
+        block_push(n_items, items, out_cnt, out, acc.next);
+    }
+}
+
+// ------------------------------------------------------------ medium vertices
+//
+// One warp per vertex; warps take vertices round-robin (no work-grab atomics).
+// The warp fetches the list entries and row bounds of its next 32 vertices in
+// one go, then walks them.
+
+__device__ __forceinline__ unsigned global_warp() {
+    return (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+
+__device__ __forceinline__ unsigned total_warps() { return (gridDim.x * blockDim.x) >> 5; }
+
+// Warp-wide conflict test of v (tentative color c) over entries [a, b).
+template <bool kFast, bool kBatched>
+__device__ __forceinline__ bool warp_conflict(const Params &p, int32_t v, int c, int32_t dv,
+                                              long long a, long long b, int32_t vb, bool prefix,
+                                              unsigned long long &scanned) {
     const int lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned i0 = 0;
-        if (lane == 0) i0 = atomicAdd(grab, (unsigned)kMediumBatch);
-        i0 = __shfl_sync(kFull, i0, 0);
-        if (i0 >= cnt) break;
-        const unsigned i1 = min(i0 + kMediumBatch, cnt);
-        for (unsigned i = i0; i < i1; ++i) {
-            const int32_t v = __ldcg(list + i);
-            long long s, e;
-            int32_t vb;
-            row_of<kBatched>(p, v, s, e, vb);
+    for (long long q0 = (a >> 2); (q0 << 2) < b; q0 += 32) {
+        const long long q = q0 + lane;
+        bool my = false, past = false;
+        if ((q << 2) < b) {
+            const int4 x = load4(p.ci, q, p.m);
+            const long long i0 = q << 2;
+            int cw[4];
+            int32_t ww[4];
+            bool ok[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long i = i0 + k;
+                ww[k] = vb + elem(x, k);
+                ok[k] = i >= a && i < b && (unsigned)ww[k] < (unsigned)p.n;
+                if (prefix && ok[k] && ww[k] >= v) {
+                    ok[k] = false;
+                    past = true;
+                }
+                if (p.rule == 0 && ww[k] > v) ok[k] = false;
+                if (p.rule == 1 && ww[k] < v) ok[k] = false;
+                cw[k] = ok[k] ? __ldcg(p.colors + ww[k]) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!ok[k]) continue;
+                scanned++;
+                const int mag = kFast ? cw[k] : (cw[k] < 0 ? -cw[k] : cw[k]);
+                if (mag == c && loses_to<kBatched>(p, v, ww[k], dv)) my = true;
+            }
+        } else {
+            past = true;
+        }
+        if (__any_sync(kFull, my)) return true;
+        if (prefix && __any_sync(kFull, past)) return false;
+    }
+    return false;
+}
+
+template <bool kFast, bool kBatched>
+__device__ void medium_assign(const Params &p, const int32_t *list, unsigned cnt, Acc &acc) {
+    const int lane = threadIdx.x & 31;
+    const unsigned gw = global_warp(), NW = total_warps();
+    for (unsigned b = gw; b < cnt; b += 32 * NW) {
+        const unsigned i = b + lane * NW;
+        int32_t vl = 0, vbl = 0;
+        long long sl = 0, el = 0;
+        if (i < cnt) {
+            vl = __ldcg(list + i);
+            row_of<kBatched>(p, vl, sl, el, vbl);
+        }
+        for (int j = 0; j < 32; ++j) {
+            if (b + j * NW >= cnt) break;
+            const int32_t v = __shfl_sync(kFull, vl, j), vb = __shfl_sync(kFull, vbl, j);
+            const long long s = __shfl_sync(kFull, sl, j), e = __shfl_sync(kFull, el, j);
             const int c = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);
             if (lane == 0) {
                 __stcg(p.colors + v, kFast ? c : -c);
@@ -377,28 +503,76 @@ __device__ void medium_assign(const Params &p, const int32_t *list, unsigned cnt
     }
 }
 
-// index of the hub entry owning chunk q: largest i with cb[i] <= q
+template <bool kFast, bool kBatched>
+__device__ void medium_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
+                              unsigned *out_cnt, bool prefix, Acc &acc) {
+    const int lane = threadIdx.x & 31;
+    const unsigned gw = global_warp(), NW = total_warps();
+    for (unsigned b = gw; b < cnt; b += 32 * NW) {
+        const unsigned i = b + lane * NW;
+        int32_t vl = 0, vbl = 0;
+        long long sl = 0, el = 0;
+        if (i < cnt) {
+            vl = __ldcg(list + i);
+            row_of<kBatched>(p, vl, sl, el, vbl);
+        }
+        unsigned lost = 0;
+        for (int j = 0; j < 32; ++j) {
+            if (b + j * NW >= cnt) break;
+            const int32_t v = __shfl_sync(kFull, vl, j), vb = __shfl_sync(kFull, vbl, j);
+            const long long s = __shfl_sync(kFull, sl, j), e = __shfl_sync(kFull, el, j);
+            const int own = __ldcg(p.colors + v);
+            const int c = kFast ? own : -own;
+            const bool conf =
+                warp_conflict<kFast, kBatched>(p, v, c, (int32_t)(e - s), s, e, vb, prefix, acc.dscan);
+            if (conf) {
+                lost |= 1u << j;
+                if (lane == 0 && kFast) __stcg(p.colors + v, 0);
+            } else if (lane == 0) {
+                if (!kFast) __stcg(p.colors + v, c);
+                acc.kmax = max(acc.kmax, c);
+            }
+        }
+        if (lost) {
+            unsigned pos = 0;
+            if (lane == 0) pos = atomicAdd(out_cnt, (unsigned)__popc(lost));
+            pos = __shfl_sync(kFull, pos, 0);
+            if ((lost >> lane) & 1u) out[pos + __popc(lost & ((1u << lane) - 1u))] = vl;
+            if (lane == 0) acc.next += (unsigned long long)__popc(lost);
+        }
+    }
+}
+
+// ------------------------------------------------------------ hubs
+//
+// A hub (degree > chunk) is split into ceil(deg / chunk) warp work items.
+// Items are taken round-robin by the warps of the grid; the item that
+// finishes last for a vertex (completion counter) resolves it.
+
+// index of the hub entry owning chunk q: largest i with cb[i] <= q (32-ary
+// search by the whole warp; cb is ascending and cb[0] == 0).
 __device__ __forceinline__ unsigned hub_entry(const unsigned *cb, unsigned cnt, unsigned q) {
-    unsigned lo = 0, hi = cnt;  // invariant: cb[lo] <= q < cb[hi]
+    const int lane = threadIdx.x & 31;
+    unsigned lo = 0, hi = cnt;
     while (hi - lo > 1) {
-        const unsigned mid = (lo + hi) >> 1;
-        if (__ldcg(cb + mid) <= q) lo = mid;
-        else hi = mid;
+        const unsigned step = (hi - lo + 31) / 32;
+        const unsigned idx = lo + lane * step;
+        const bool ok = idx < hi && __ldcg(cb + idx) <= q;
+        const unsigned bal = __ballot_sync(kFull, ok);
+        const int last = 31 - __clz(bal);
+        lo = lo + (unsigned)last * step;
+        hi = min(hi, lo + step);
     }
     return lo;
 }
 
 template <bool kFast, bool kBatched>
-__device__ void hub_assign(const Params &p, int par, unsigned long long h64, unsigned *grab,
-                           int kmax, Acc &acc) {
+__device__ void hub_assign(const Params &p, int par, unsigned long long h64, int kmax, Acc &acc) {
     const int lane = threadIdx.x & 31;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const long long CH = p.chunk;
-    for (;;) {
-        unsigned q = 0;
-        if (lane == 0) q = atomicAdd(grab, 1u);
-        q = __shfl_sync(kFull, q, 0);
-        if (q >= nch) break;
+    const unsigned NW = total_warps();
+    for (unsigned q = global_warp(); q < nch; q += NW) {
         const unsigned i = hub_entry(p.hcb[par], cnt, q);
         const int32_t slot = __ldcg(p.hw[par] + i);
         const unsigned j = q - __ldcg(p.hcb[par] + i);
@@ -453,145 +627,14 @@ __device__ void hub_assign(const Params &p, int par, unsigned long long h64, uns
     }
 }
 
-// ------------------------------------------------------------ phase B pieces
-
 template <bool kFast, bool kBatched>
-__device__ void light_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
-                             unsigned *out_cnt, bool prefix, Acc &acc) {
-    __shared__ int32_t s_flag[kWarps][32 * kLightUnroll];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int G = p.G, gl = lane & (G - 1), per = 32 / G;
-    const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
-    for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const unsigned base = t * kLightTile + warp * (32 * kLightUnroll);
-        for (int step = 0; step < kLightUnroll * G; ++step) {
-            const int jslot = step * per + lane / G;
-            const unsigned idx = base + jslot;
-            const bool act = idx < cnt;
-            int32_t v = 0, vb = 0;
-            long long s = 0, e = 0;
-            int c = 0;
-            bool conf = false;
-            if (act) {
-                v = __ldcg(list + idx);
-                row_of<kBatched>(p, v, s, e, vb);
-                const int own = __ldcg(p.colors + v);
-                c = kFast ? own : -own;
-                conf = conflict_lane<kFast, kBatched>(p, p.colors, v, c, (int32_t)(e - s), s, e, vb,
-                                                      gl, G, prefix, acc.dscan);
-            }
-            conf = group_any(conf, G);
-            if (gl == 0) {
-                int32_t flag = -1;
-                if (act) {
-                    if (conf) {
-                        flag = v;
-                        if (kFast) __stcg(p.colors + v, 0);
-                    } else {
-                        if (!kFast) __stcg(p.colors + v, c);
-                        acc.kmax = max(acc.kmax, c);
-                    }
-                }
-                s_flag[warp][jslot] = flag;
-            }
-        }
-        __syncwarp();
-        int32_t items[kLightUnroll];
-        int n_items = 0;
-#pragma unroll
-        for (int u = 0; u < kLightUnroll; ++u) {
-            const int32_t f = s_flag[warp][u * 32 + lane];
-            items[u] = f;
-            n_items += (f >= 0);
-        }
-        // compact the valid entries to the front (static indices only)
-        int32_t packed[kLightUnroll];
-        int k = 0;
-#pragma unroll
-        for (int u = 0; u < kLightUnroll; ++u) packed[u] = 0;
-#pragma unroll
-        for (int u = 0; u < kLightUnroll; ++u) {
-            if (items[u] >= 0) {
-#pragma unroll
-                for (int z = 0; z < kLightUnroll; ++z)
-                    if (z == k) packed[z] = items[u];
-                ++k;
-            }
-        }
-        block_push(n_items, packed, out_cnt, out, acc.next);
-    }
-}
-
-template <bool kFast, bool kBatched>
-__device__ void medium_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
-                              unsigned *out_cnt, unsigned *grab, bool prefix, Acc &acc) {
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned i0 = 0;
-        if (lane == 0) i0 = atomicAdd(grab, (unsigned)kMediumBatch);
-        i0 = __shfl_sync(kFull, i0, 0);
-        if (i0 >= cnt) break;
-        const unsigned i1 = min(i0 + kMediumBatch, cnt);
-        int32_t lost[kMediumBatch];
-        int nlost = 0;
-        for (unsigned i = i0; i < i1; ++i) {
-            const int32_t v = __ldcg(list + i);
-            long long s, e;
-            int32_t vb;
-            row_of<kBatched>(p, v, s, e, vb);
-            const int own = __ldcg(p.colors + v);
-            const int c = kFast ? own : -own;
-            bool conf = false;
-            // warp-uniform trip count; lanes stop contributing after their own stop
-            for (long long q0 = (s >> 2); (q0 << 2) < e; q0 += 32) {
-                const long long q = q0 + lane;
-                bool my = false, past = false;
-                if ((q << 2) < e) {
-                    my = conflict_lane<kFast, kBatched>(p, p.colors, v, c, (int32_t)(e - s),
-                                                        (q << 2) > s ? (q << 2) : s, e, vb, 0,
-                                                        1 << 30, prefix, acc.dscan);
-                    if (prefix) past = vb + __ldg(p.ci + min((q << 2) + 3, e - 1)) >= v;
-                } else {
-                    past = true;
-                }
-                if (__any_sync(kFull, my)) { conf = true; break; }
-                if (prefix && __any_sync(kFull, past)) break;
-            }
-            if (lane == 0) {
-                if (conf) {
-                    if (kFast) __stcg(p.colors + v, 0);
-#pragma unroll
-                    for (int z = 0; z < kMediumBatch; ++z)
-                        if (z == nlost) lost[z] = v;
-                    ++nlost;
-                } else {
-                    if (!kFast) __stcg(p.colors + v, c);
-                    acc.kmax = max(acc.kmax, c);
-                }
-            }
-        }
-        if (lane == 0 && nlost) {
-            const unsigned pos = atomicAdd(out_cnt, (unsigned)nlost);
-#pragma unroll
-            for (int z = 0; z < kMediumBatch; ++z)
-                if (z < nlost) out[pos + z] = lost[z];
-            acc.next += (unsigned long long)nlost;
-        }
-    }
-}
-
-template <bool kFast, bool kBatched>
-__device__ void hub_detect(const Params &p, int par, unsigned long long h64, unsigned *grab,
-                           bool prefix, Acc &acc) {
+__device__ void hub_detect(const Params &p, int par, unsigned long long h64, bool prefix, Acc &acc) {
     const int lane = threadIdx.x & 31;
     const int pn = par ^ 1;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const long long CH = p.chunk;
-    for (;;) {
-        unsigned q = 0;
-        if (lane == 0) q = atomicAdd(grab, 1u);
-        q = __shfl_sync(kFull, q, 0);
-        if (q >= nch) break;
+    const unsigned NW = total_warps();
+    for (unsigned q = global_warp(); q < nch; q += NW) {
         const unsigned i = hub_entry(p.hcb[par], cnt, q);
         const int32_t slot = __ldcg(p.hw[par] + i);
         const unsigned j = q - __ldcg(p.hcb[par] + i);
@@ -603,30 +646,14 @@ __device__ void hub_detect(const Params &p, int par, unsigned long long h64, uns
         const long long a = s + (long long)j * CH, b = min(e, a + CH);
         const int own = __ldcg(p.colors + v);
         const int c = kFast ? own : -own;
-        bool conf = false;
         const bool skip = prefix && (vb + __ldg(p.ci + a)) >= v;
-        if (!skip) {
-            for (long long q0 = (a >> 2); (q0 << 2) < b; q0 += 32) {
-                const long long qq = q0 + lane;
-                bool my = false, past = false;
-                if ((qq << 2) < b) {
-                    const long long lo = (qq << 2) > a ? (qq << 2) : a;
-                    my = conflict_lane<kFast, kBatched>(p, p.colors, v, c, (int32_t)deg, lo, b, vb,
-                                                        0, 1 << 30, prefix, acc.dscan);
-                    if (prefix) past = vb + __ldg(p.ci + min((qq << 2) + 3, b - 1)) >= v;
-                } else {
-                    past = true;
-                }
-                if (__any_sync(kFull, my)) { conf = true; break; }
-                if (prefix && __any_sync(kFull, past)) break;
-            }
-        }
+        const bool conf =
+            !skip && warp_conflict<kFast, kBatched>(p, v, c, (int32_t)deg, a, b, vb, prefix, acc.dscan);
         const unsigned nchunks = (unsigned)((deg + CH - 1) / CH);
-        unsigned last = 0;
         if (lane == 0) {
             if (conf) atomicOr(p.hconf + slot, 1u);
             __threadfence();
-            last = (atomicAdd(p.hdone + slot, 1u) == nchunks - 1) ? 1u : 0u;
+            const bool last = atomicAdd(p.hdone + slot, 1u) == nchunks - 1;
             if (last) {
                 __threadfence();
                 const unsigned lost = __ldcg(p.hconf + slot);
@@ -739,7 +766,7 @@ __device__ void flush_kmax(const Params &p, int kloc) {
     if (threadIdx.x == 0) {
         int b = 0;
         for (int w = 0; w < kWarps; ++w) b = max(b, s_k[w]);
-        if (b > 0) atomicMax(&p.ctr->kmax, b);
+        if (b > 0 && b > *(volatile int *)&p.ctr->kmax) atomicMax(&p.ctr->kmax, b);
     }
 }
 
@@ -758,6 +785,8 @@ __device__ void flush_stats(const Params &p, Acc &acc) {
 
 template <bool kFast, bool kBatched>
 __global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
+    __shared__ int32_t s_stage[kWarps][32 * kLightMaxStage];
+    int32_t *sbuf = s_stage[threadIdx.x >> 5];
     Acc acc;
     unsigned gen = 0;
     Counters *ctr = p.ctr;
@@ -781,37 +810,29 @@ __global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctr->err, 0, kErrNoConvergence);
             break;
         }
-        const int ga = (int)((2 * r) % 3), gb = (int)((2 * r + 1) % 3), gc = (int)((2 * r + 2) % 3);
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             ctr->nl[pn] = 0;
             ctr->nm[pn] = 0;
             ctr->h64[pn] = 0;
-            ctr->grab[gb][0] = 0;
-            ctr->grab[gb][1] = 0;
             if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)total;
         }
         // ---- phase A: FirstFit over W_r (skipped in det round 1: all tentative colors are 1)
         if (kFast || r > 1) {
             const int kmax = __ldcg(&ctr->kmax);
-            hub_assign<kFast, kBatched>(p, par, h64, &ctr->grab[ga][1], kmax, acc);
-            medium_assign<kFast, kBatched>(p, p.mw[par], nm, &ctr->grab[ga][0], acc);
-            light_assign<kFast, kBatched>(p, p.lw[par], nl, acc);
+            hub_assign<kFast, kBatched>(p, par, h64, kmax, acc);
+            medium_assign<kFast, kBatched>(p, p.mw[par], nm, acc);
+            light_assign<kFast, kBatched>(p, p.lw[par], nl, sbuf, acc);
         }
         if (!grid_barrier(p, gen)) break;
         if (recorder && r <= kTraceCap)
             p.trace[kTraceFields * (r - 1) + 1] = (long long)(globaltimer() - t0);
         // ---- phase B: ConflictResolve over W_r, commit keepers, compact losers
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            ctr->grab[gc][0] = 0;
-            ctr->grab[gc][1] = 0;
-        }
         int kloc = 0;
         {
             Acc b;
-            hub_detect<kFast, kBatched>(p, par, h64, &ctr->grab[gb][1], prefix, b);
-            medium_detect<kFast, kBatched>(p, p.mw[par], nm, p.mw[pn], &ctr->nm[pn],
-                                           &ctr->grab[gb][0], prefix, b);
-            light_detect<kFast, kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix, b);
+            hub_detect<kFast, kBatched>(p, par, h64, prefix, b);
+            medium_detect<kFast, kBatched>(p, p.mw[par], nm, p.mw[pn], &ctr->nm[pn], prefix, b);
+            light_detect<kFast, kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix, sbuf, b);
             acc.dscan += b.dscan;
             acc.next += b.next;
             kloc = b.kmax;

@@ -59,8 +59,8 @@ class Stats(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("group_lanes", ctypes.c_int32), ("light_max", ctypes.c_int32),
-                ("chunk", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+    _fields_ = [("light_max", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def _load():
@@ -196,8 +196,8 @@ def sgr_get_tuning() -> dict:
     return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
 
-def sgr_set_tuning(group_lanes=0, light_max=0, chunk=0, blocks_per_sm=0) -> None:
-    t = Tuning(group_lanes, light_max, chunk, blocks_per_sm)
+def sgr_set_tuning(light_max=0, chunk=0, blocks_per_sm=0, reserved=0) -> None:
+    t = Tuning(light_max, chunk, blocks_per_sm, reserved)
     _check(_lib.sgr_set_tuning(ctypes.byref(t)), "sgr_set_tuning")
 
 

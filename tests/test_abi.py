@@ -37,17 +37,17 @@ def test_host_only_calls_without_gpu():
     assert sgrcolor.status_string(-6) == "SGR_ERR_TIMEOUT"
     assert sgrcolor.status_string(12345) == "SGR_UNKNOWN_STATUS"
     t = sgrcolor.sgr_get_tuning()
-    assert t["group_lanes"] in (1, 2, 4, 8, 16, 32)
+    assert 1 <= t["light_max"] <= 32
     # invalid tunings are refused, valid ones round-trip
-    for bad in [dict(group_lanes=3), dict(light_max=64), dict(chunk=10), dict(blocks_per_sm=-1)]:
+    for bad in [dict(reserved=3), dict(light_max=33), dict(chunk=10), dict(blocks_per_sm=-1)]:
         try:
             sgrcolor.sgr_set_tuning(**bad)
         except sgrcolor.SgrError as e:
             assert e.status == sgrcolor.SGR_ERR_INVALID_ARG
         else:
             raise AssertionError(f"accepted {bad}")
-    sgrcolor.sgr_set_tuning(group_lanes=8)
-    assert sgrcolor.sgr_get_tuning()["group_lanes"] == 8
+    sgrcolor.sgr_set_tuning(light_max=8)
+    assert sgrcolor.sgr_get_tuning()["light_max"] == 8
     sgrcolor.sgr_set_tuning(**t)
     assert sgrcolor.sgr_get_tuning() == t
 

@@ -109,12 +109,12 @@ def test_det_parity_small(lib, make, rule):
 # Tunings that move vertices between the three bins and split hubs into many
 # work items even on small graphs.
 TUNINGS = [
-    dict(group_lanes=1, light_max=63, chunk=4096),
-    dict(group_lanes=2, light_max=8, chunk=64),
-    dict(group_lanes=8, light_max=4, chunk=100),
-    dict(group_lanes=16, light_max=1, chunk=64),
-    dict(group_lanes=32, light_max=32, chunk=2048),
-    dict(group_lanes=4, light_max=32, chunk=2048, blocks_per_sm=1),
+    dict(light_max=32, chunk=4096),
+    dict(light_max=8, chunk=64),
+    dict(light_max=4, chunk=100),
+    dict(light_max=1, chunk=64),
+    dict(light_max=32, chunk=2048),
+    dict(light_max=32, chunk=2048, blocks_per_sm=1),
 ]
 
 
@@ -129,7 +129,7 @@ def test_det_parity_across_bins(tuning, tune):
 
 @pytest.mark.parametrize("rule", ["low_keeps", "low_loses", "degree"])
 def test_det_parity_unsorted_rows(tuning, rule):
-    tuning.sgr_set_tuning(group_lanes=4, light_max=16, chunk=128)
+    tuning.sgr_set_tuning(light_max=16, chunk=128)
     for seed, g in enumerate([gg.rmat(12, 16, seed=2), gg.uniform(4000, 12.0, seed=9),
                               gg.stencil(8, 7, 6, 27)]):
         h = shuffled_rows(g, seed)
