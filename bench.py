@@ -47,6 +47,8 @@ WORKLOADS = {
                lambda: gg.rmat20(0)),
     "stencil192": ("3-D 27-point stencil 192^3, natural order", lambda: gg.stencil27(192)),
     "er20k": ("uniform random graph n=20,000, average degree 10, seed 0", lambda: gg.er20k(0)),
+    "stencil128": ("3-D 27-point stencil 128^3, natural order (profiling size)",
+                   lambda: gg.stencil27(128)),
 }
 
 
@@ -90,16 +92,23 @@ def read_traffic(workload, mode):
     return e.get("dram_bytes_per_launch")
 
 
-def alg_bytes(st, n, m):
-    """Algorithmic DRAM bytes of one coloring launch (the byte model):
-    per worklist vertex and round 36 B (worklist entry read twice, row offsets
-    twice, own color read, tentative write, commit write), 4 B per entry
-    scanned by FirstFit, 4 B per entry ConflictResolve inspects, 4 B per pushed
-    loser, plus the init pass (4 B per entry for the order check, 12 B per
-    vertex).  Neighbour color gathers hit the L2-resident colors array and
-    are not counted."""
-    return (36 * st["sum_w"] + 4 * st["sum_d"] + 4 * st["sum_dscan"] + 4 * st["sum_next"]
-            + 4 * m + 12 * n)
+def alg_bytes(st, n, m, mode):
+    """Algorithmic DRAM bytes of one coloring launch (the byte model).
+
+    Per worklist vertex and round, 36 B: FirstFit reads the worklist entry (4)
+    and either the first word of the vertex's forbidden-color bitmap (det, 4)
+    or its row offsets (fast, counted with the scan below) and writes the
+    tentative color (4); ConflictResolve reads the entry (4), the row offsets
+    (8), the vertex's color (4) and its lower-neighbour count (4) and writes
+    the commit (4).  4 B per col_idx entry ConflictResolve inspects, 4 B per
+    pushed loser; det mode adds 4 B per entry a committing vertex scatters its
+    color to, fast mode 4 B per entry FirstFit gathers (sum of D_r).  The init
+    pass reads col_idx once (4 B per entry) and 24 B per vertex.  Neighbour
+    color and bitmap accesses hit L2-resident arrays and are not counted."""
+    per = 36 * st["sum_w"] + 4 * st["sum_dscan"] + 4 * st["sum_next"] + 4 * m + 24 * n
+    if mode == "det":
+        return per + 4 * st["sum_scatter"]
+    return per + 4 * st["sum_d"]
 
 
 class ClockSampler:
@@ -232,6 +241,9 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    if args.tune:
+        lm, ch, bps = (int(x) for x in args.tune.split(","))
+        lib.sgr_set_tuning(light_max=lm, chunk=ch, blocks_per_sm=bps)
     desc, make = WORKLOADS[args.workload]
     g = make()
     n, m = g.n, g.m
@@ -312,7 +324,7 @@ def run_ours(args, rank, world, local):
         return
     peak, peak_src = read_peaks()
     kmean = statistics.mean(kern_ms)
-    ab = alg_bytes(st, n, m)
+    ab = alg_bytes(st, n, m, mode)
     achieved = ab / (kmean * 1e-3) / 1e9
     line = {
         "metric": METRIC_SINGLE, "value": value, "unit": "GTEPS", "n_gpus": world,
@@ -320,6 +332,7 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "n": n, "m": m, "mode": mode,
+                   "tuning": lib.sgr_get_tuning(),
                    "l2": "flushed (512 MiB write) before every step",
                    "parallelism": f"replicas x{world}"},
         "num_colors": k, "rounds": st["rounds"], "sum_d": st["sum_d"],
@@ -365,6 +378,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--timeline", default="", help="write the per-round device timeline here")
+    ap.add_argument("--tune", default="", help="light_max,chunk,blocks_per_sm (0 = default)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

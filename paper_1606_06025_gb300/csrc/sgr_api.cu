@@ -151,6 +151,7 @@ sgr_tuning current_tuning() {
 
 // Everything a coloring launch needs beyond the CSR itself.
 struct Job {
+    bool fast;
     int32_t n;
     long long m;
     const int32_t *ro;
@@ -178,7 +179,13 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     unsigned *hdone = (unsigned *)take(sp.hub_max * 4);
     unsigned *hconf = (unsigned *)take(sp.hub_max * 4);
     unsigned *hbits = (unsigned *)take(sp.hub_words * 4);
-    if (zero_bytes) *zero_bytes = off;
+    const size_t zero_fast = off;
+    const long long np = ((long long)j.n + 63) / 64 * 64;
+    unsigned *bm = (unsigned *)take((size_t)np * 8 * 4);
+    if (zero_bytes) *zero_bytes = j.fast ? zero_fast : off;
+    int32_t *lowdeg = (int32_t *)take((size_t)j.n * 4);
+    int32_t *sw = (int32_t *)take(sp.hub_max * 4);
+    unsigned *scb = (unsigned *)take(sp.hub_max * 4);
     long long *trace = (long long *)take(sizeof(long long) * sgr::kTraceCap * sgr::kTraceFields);
     int32_t *lw0 = (int32_t *)take((size_t)j.n * 4), *lw1 = (int32_t *)take((size_t)j.n * 4);
     int32_t *mw0 = (int32_t *)take((size_t)j.n * 4), *mw1 = (int32_t *)take((size_t)j.n * 4);
@@ -205,6 +212,11 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         p->hbits = hbits;
         p->hdone = hdone;
         p->hconf = hconf;
+        p->bm = bm;
+        p->np = np;
+        p->lowdeg = lowdeg;
+        p->sw = sw;
+        p->scb = scb;
         p->ctr = ctr;
         p->trace = trace;
         p->light_max = t.light_max;
@@ -221,6 +233,7 @@ void fill_stats(const Counters &h, float ms, int grid, int colors) {
     s.sum_d = (int64_t)h.sum_d;
     s.sum_dscan = (int64_t)h.sum_dscan;
     s.sum_next = (int64_t)h.sum_next;
+    s.sum_scatter = (int64_t)h.sum_scatter;
     s.num_colors = colors;
     s.rows_sorted = h.unsorted_pairs == h.boundary_pairs ? 1 : 0;
     s.grid_blocks = grid;
@@ -235,6 +248,7 @@ int run_job(DevCtx *c, Job &j, int mode, cudaStream_t st, int32_t *k_out) {
     const sgr_tuning t = current_tuning();
     const bool fast = (mode & SGR_MODE_MASK) == SGR_MODE_FAST;
     const int rule = (mode & SGR_RULE_MASK) >> 4;
+    j.fast = fast;
     size_t zero_bytes = 0;
     size_t need = layout(j, t, nullptr, nullptr, &zero_bytes);
     const size_t gid_off = need;
@@ -470,6 +484,7 @@ int sgr_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
     j.colors = colors_out;
     j.batched = true;
     j.G = G;
+    j.fast = (mode & SGR_MODE_MASK) == SGR_MODE_FAST;
     // the batch tail of the arena: gid, vbase, ebase, per-graph k (see run_job)
     const sgr_tuning t = current_tuning();
     size_t zero_bytes = 0;

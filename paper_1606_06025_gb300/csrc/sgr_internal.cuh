@@ -9,8 +9,13 @@
 //   medium lists mw[2]   vertex ids of degree in (light_max, chunk].
 //   hub lists hw[2]      hub slot ids (degree > chunk) + chunk base hcb[2].
 //   hub slots            hvert (slot -> vertex), hbase (offset of the slot's
-//                        forbidden-color bitmap in hbits), hdone / hconf
-//                        (per-round completion counter and conflict flag).
+//                        forbidden-color bitmap in hbits, fast mode), hdone /
+//                        hconf (per-round completion counter and conflict flag).
+//   bm[8][np]            det mode: bit c-1 of plane (c-1)/32 at vertex v is set
+//                        once a neighbour of v has committed color c (c <= 256).
+//   lowdeg[n]            det mode: entries below v in its (ascending) row.
+//   hub scatter list     det mode: hubs committed this round (slot + chunk
+//                        base), whose colors are scattered at the next round.
 //   Counters             list sizes, grid barrier, max
 //                        color so far, error code, statistics.
 #pragma once
@@ -45,10 +50,11 @@ struct Counters {
     int err;                        // 0 or a negative status
     unsigned long long unsorted_pairs;   // adjacent col_idx pairs with a[i] >= a[i+1]
     unsigned long long boundary_pairs;   // ... of them across row boundaries
-    unsigned long long sum_w, sum_d, sum_dscan, sum_next;
+    unsigned long long sum_w, sum_d, sum_dscan, sum_next, sum_scatter;
+    unsigned long long sc64;        // hub scatter list: (entries << 32) | total chunks
     long long rounds;
     long long t_init_ns;            // globaltimer: end of the init pass (after its barrier)
-    long long pad[3];
+    long long pad[2];
 };
 
 struct Params {
@@ -69,6 +75,11 @@ struct Params {
     unsigned int *hbits;
     unsigned int *hdone;
     unsigned int *hconf;
+    unsigned int *bm;          // det: 8 planes of np words
+    long long np;              // plane stride (>= n, multiple of 64)
+    int32_t *lowdeg;           // det
+    int32_t *sw;               // det: hub scatter list slots
+    unsigned int *scb;         // det: hub scatter list chunk bases
     Counters *ctr;
     long long *trace;
     int light_max;             // <= kLightMaxStage

@@ -5,42 +5,48 @@
 //
 //   init:    W_1 = V, binned by degree; colors = 0 (fast) or -1 (det: the
 //            round-1 FirstFit answer is 1 for every vertex, since all frozen
-//            colors are 0); strictly-ascending rows are detected.
+//            colors are 0); strictly ascending rows are detected.
 //   round r: phase A = FirstFit (Algorithm 4) over W_r,
 //            grid barrier,
 //            phase B = ConflictResolve (Algorithm 5) over W_r: keepers commit,
 //            losers are compacted into W_{r+1} (Sect. 3.1 "Atomic Operation
-//            Reduction": one atomic per CTA tile, positions from a block scan),
+//            Reduction": one atomic per CTA tile, positions from a block scan
+//            that keeps the order of the tile),
 //            grid barrier, swap W_in / W_out by parity (Algorithm 7's swap).
 //
-// The two phases share one kernel with a software grid barrier, which is the
-// paper's kernel fusion (Sect. 3.3) and its forced thread coarsening
-// (Sect. 3.2): a fixed grid of co-resident CTAs loops over the worklist.
-// Every wait is bounded by %globaltimer; on expiry the kernel records
-// SGR_ERR_TIMEOUT and returns.
+// The phases share one kernel with a software grid barrier: the paper's
+// kernel fusion (Sect. 3.3) and its forced thread coarsening (Sect. 3.2), a
+// fixed grid of co-resident CTAs looping over the worklist.  Every wait is
+// bounded by %globaltimer; on expiry the kernel records SGR_ERR_TIMEOUT and
+// returns.
 //
-// Deterministic mode keeps the tentative color of a worklist vertex as a
-// negative value in `colors`.  FirstFit only counts positive (final) colors,
-// so it sees exactly the colors frozen at the start of the round whatever
-// the interleaving; ConflictResolve compares magnitudes, so a neighbour's
-// commit (-c -> +c) during the phase does not change what it sees; losers
-// keep -c until their next FirstFit overwrites it.  This is the
-// judge-before-clear reading: a loser still counts against higher ids.
+// Deterministic mode (frozen reads, judge before clear):
+//   * A worklist vertex holds its tentative color as a negative value in
+//     `colors`; losers keep -c until their next FirstFit overwrites it.
+//   * FirstFit reads a per-vertex bitmap of the final colors of its
+//     neighbours (colors 1..256 in 8 bit planes of n words).  A vertex adds
+//     its color to every neighbour's bitmap once, when it commits; so at the
+//     start of round r the bitmap of v is exactly { F[w] : w in adj(v) } of
+//     Algorithm 4 restricted to 1..256, and the first zero bit is its
+//     first-fit color (Sect. 3.2 "Bitset Operation").  If bits 1..256 are all
+//     set, the vertex falls back to scanning its row.
+//   * ConflictResolve compares magnitudes, so a neighbour's commit (-c -> +c)
+//     during the phase does not change what it sees.  With ascending rows
+//     and the low-keeps rule it scans only the neighbours below v, nearest
+//     first, and stops at the first conflict.
+// Fast mode reads and writes colors in place while the round runs, as the
+// paper's GPU code does: FirstFit gathers the live colors of all neighbours,
+// ConflictResolve clears losers to 0 (Sect. 3.1 "Color Clearing").
 //
 // Load balance (Sect. 3.3, Merrill's thread / warp / CTA mapping): a vertex
-// of degree <= light_max is handled by one lane after its warp staged the
-// rows of 32 such vertices in shared memory, a vertex of degree
-// <= chunk by one warp, a hub by ceil(deg / chunk) warp-sized work items that
-// merge their forbidden-color bitmaps with atomicOr; the item that finishes
-// last (completion counter) resolves the vertex.
-//
-// First permissible color (Sect. 3.2 "Bitset Operation"): forbidden colors
-// are gathered into bit masks and the answer is the first zero bit (__ffsll /
-// __ffs on the complement).
+// of degree <= light_max is handled by one lane, a vertex of degree <= chunk
+// by one warp, a hub by ceil(deg / chunk) warp work items; the item that
+// finishes last for a hub (completion counter) resolves it.
 //
 // Reads of col_idx and row_offsets use the read-only path (__ldg, Sect. 3.3
-// "Read-only Data Caching") with 16-byte vector loads; colors, worklists and
-// counters change during the launch and are read through L2 (__ldcg).
+// "Read-only Data Caching") with 16-byte vector loads; everything the launch
+// itself writes (colors, bitmaps, worklists, counters) is read through L2
+// (__ldcg).
 
 #include <climits>
 #include <cstdint>
@@ -69,8 +75,8 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-// Bounded sense-by-generation grid barrier.  Returns false if this CTA must
-// stop (timeout or a recorded error).
+// Bounded grid barrier (arrival counter + generation).  Returns false if this
+// CTA must stop (timeout or a recorded error).
 __device__ bool grid_barrier(const Params &p, unsigned &gen) {
     __shared__ int s_ok;
     __syncthreads();
@@ -79,14 +85,14 @@ __device__ bool grid_barrier(const Params &p, unsigned &gen) {
         gen += 1;
         int ok = 1;
         __threadfence();
-        unsigned arrived = atomicAdd(&c->bar_count, 1u);
+        const unsigned arrived = atomicAdd(&c->bar_count, 1u);
         if (arrived == p.nblocks - 1) {
             c->bar_count = 0;
             st_release(&c->bar_gen, gen);
         } else {
-            unsigned long long t0 = globaltimer();
+            const unsigned long long t0 = globaltimer();
             while ((int)(ld_acquire(&c->bar_gen) - gen) < 0) {
-                __nanosleep(40);
+                __nanosleep(32);
                 if (globaltimer() - t0 > kWaitTimeoutNs) {
                     atomicCAS(&c->err, 0, kErrTimeout);
                     ok = 0;
@@ -105,7 +111,7 @@ template <bool kBatched>
 __device__ __forceinline__ void row_of(const Params &p, int32_t v, long long &s, long long &e,
                                        int32_t &vb) {
     if (kBatched) {
-        const int g = __ldg(p.gid + v);
+        const int g = __ldcg(p.gid + v);
         const long long eb = __ldg(p.ebase + g);
         s = eb + __ldg(p.ro + v + g);
         e = eb + __ldg(p.ro + v + g + 1);
@@ -145,14 +151,24 @@ __device__ __forceinline__ bool loses_to(const Params &p, int32_t v, int32_t w, 
 }
 
 struct Acc {
-    unsigned long long w = 0, d = 0, dscan = 0, next = 0;
+    unsigned long long w = 0, d = 0, dscan = 0, next = 0, scatter = 0;
     int kmax = 0;
 };
+
+__device__ __forceinline__ unsigned global_warp() {
+    return (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+
+__device__ __forceinline__ unsigned total_warps() { return (gridDim.x * blockDim.x) >> 5; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    return (1u << (threadIdx.x & 31)) - 1u;
+}
 
 // ------------------------------------------------------------ forbidden masks
 
 // Colors wb+1 .. wb+256 of entries [a, b) (lanes lane0, lane0+stride, ...)
-// into eight 32-bit words.
+// into eight 32-bit words; only positive colors count.
 __device__ __forceinline__ void mask256_lane(const int32_t *__restrict__ ci, long long m,
                                              const int32_t *colors, long long a, long long b,
                                              int32_t vb, int lane0, int stride, int wb,
@@ -201,8 +217,7 @@ __device__ __forceinline__ unsigned pick8(const unsigned (&mw)[8], int j) {
     return r;
 }
 
-// Whole-row first fit by one warp, windows of 256 colors (medium vertices and
-// the rare hub fallback).
+// Whole-row first fit by one warp over positive colors, windows of 256.
 __device__ __forceinline__ int warp_first_fit(const int32_t *__restrict__ ci, long long m,
                                               const int32_t *colors, long long s, long long e,
                                               int32_t vb, int lane, int32_t nv) {
@@ -215,51 +230,416 @@ __device__ __forceinline__ int warp_first_fit(const int32_t *__restrict__ ci, lo
     }
 }
 
-// ------------------------------------------------------------ block compaction
+// ------------------------------------------------------------ compaction
 
-// Each thread pushes cnt (<= kLightUnroll) items; one atomicAdd per CTA.
-__device__ __forceinline__ void block_push(int cnt, const int32_t (&items)[kLightUnroll],
+// Order-preserving block compaction of kLightUnroll flags per thread: item u
+// of thread (warp w, lane l) sits at tile position (u * kWarps + w) * 32 + l.
+// One atomicAdd per CTA tile.
+__device__ __forceinline__ void block_push(const bool (&flag)[kLightUnroll],
+                                           const int32_t (&item)[kLightUnroll],
                                            unsigned *counter, int32_t *out,
                                            unsigned long long &pushed) {
-    __shared__ unsigned s_wsum[kWarps];
+    __shared__ unsigned s_cnt[kLightUnroll][kWarps];
     __shared__ unsigned s_base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int x = cnt;
+    unsigned bal[kLightUnroll];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
+    for (int u = 0; u < kLightUnroll; ++u) {
+        bal[u] = __ballot_sync(kFull, flag[u]);
+        if (lane == 0) s_cnt[u][warp] = __popc(bal[u]);
     }
-    if (lane == 31) s_wsum[warp] = (unsigned)x;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned tot = 0;
-        for (int w = 0; w < kWarps; ++w) {
-            const unsigned c = s_wsum[w];
-            s_wsum[w] = tot;
-            tot += c;
-        }
+        for (int u = 0; u < kLightUnroll; ++u)
+            for (int w = 0; w < kWarps; ++w) {
+                const unsigned c = s_cnt[u][w];
+                s_cnt[u][w] = tot;
+                tot += c;
+            }
         s_base = tot ? atomicAdd(counter, tot) : 0u;
         pushed += tot;
     }
     __syncthreads();
-    const unsigned pos = s_base + s_wsum[warp] + (unsigned)(x - cnt);
 #pragma unroll
-    for (int k = 0; k < kLightUnroll; ++k)
-        if (k < cnt) out[pos + k] = items[k];
+    for (int u = 0; u < kLightUnroll; ++u)
+        if (flag[u]) out[s_base + s_cnt[u][warp] + __popc(bal[u] & lanemask_lt())] = item[u];
     __syncthreads();
 }
 
-// ------------------------------------------------------------ light vertices
-//
-// A warp takes 32 consecutive worklist entries (one vertex per lane), copies
-// their rows into shared memory with coalesced loads (one streaming copy when
-// the rows are contiguous, i.e. consecutive vertex ids; otherwise a flattened
-// copy where each lane finds the row that owns its position), then every lane
-// works on its own row with independent color gathers in flight.
+// index of the hub entry owning chunk q: largest i with cb[i] <= q (32-ary
+// search by the whole warp; cb is ascending and cb[0] == 0).
+__device__ __forceinline__ unsigned hub_entry(const unsigned *cb, unsigned cnt, unsigned q) {
+    const int lane = threadIdx.x & 31;
+    unsigned lo = 0, hi = cnt;
+    while (hi - lo > 1) {
+        const unsigned step = (hi - lo + 31) / 32;
+        const unsigned idx = lo + lane * step;
+        const bool ok = idx < hi && __ldcg(cb + idx) <= q;
+        const unsigned bal = __ballot_sync(kFull, ok);
+        const int last = 31 - __clz(bal);
+        lo = lo + (unsigned)last * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
 
-// Stage rows [s, s + deg) of the warp's vertices (deg <= 32 each) into sbuf;
-// returns this lane's offset.  All lanes of the warp must call it.
+// Append a hub slot with its chunk count to a (count << 32 | chunks) list.
+__device__ __forceinline__ void hub_list_push(unsigned long long *ctr64, int32_t *slots,
+                                              unsigned *cb, int32_t slot, unsigned nchunks) {
+    const unsigned long long old = atomicAdd(ctr64, (1ull << 32) | (unsigned long long)nchunks);
+    const unsigned k = (unsigned)(old >> 32);
+    slots[k] = slot;
+    cb[k] = (unsigned)old;
+}
+
+// ------------------------------------------------------------ det: FirstFit
+
+// First-fit colors of the final neighbour colors recorded in the bitmap of
+// v; 0 if colors 1..256 are all forbidden.
+__device__ __forceinline__ int bitmap_first_fit(const Params &p, int32_t v) {
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) {
+        const unsigned wv = __ldcg(p.bm + (size_t)j * p.np + v);
+        if (~wv) return j * 32 + __ffs(~wv);
+    }
+    return 0;
+}
+
+// Phase A of det mode over one list (vertex ids, or hub slots when `slots`).
+template <bool kBatched>
+__device__ void det_assign(const Params &p, const int32_t *list, unsigned cnt, bool slots) {
+    const int lane = threadIdx.x & 31;
+    const unsigned NW = total_warps();
+    for (unsigned base = global_warp() * 32; base < cnt; base += NW * 32) {
+        const unsigned idx = base + lane;
+        const bool act = idx < cnt;
+        int32_t v = 0;
+        int c = 0;
+        if (act) {
+            v = __ldcg(list + idx);
+            if (slots) v = __ldcg(p.hvert + v);
+            c = bitmap_first_fit(p, v);
+        }
+        unsigned need = __ballot_sync(kFull, act && c == 0);
+        while (need) {  // bitmap full: scan the row (colors above 256 are in use)
+            const int src = __ffs(need) - 1;
+            need &= need - 1;
+            const int32_t u = __shfl_sync(kFull, v, src);
+            long long s, e;
+            int32_t vb;
+            row_of<kBatched>(p, u, s, e, vb);
+            const int cu = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);
+            if (lane == src) c = cu;
+        }
+        if (act) __stcg(p.colors + v, -c);
+    }
+}
+
+// ------------------------------------------------------------ det: ConflictResolve
+
+// Lane-level conflict test of v (tentative c) against its own row.
+template <bool kBatched>
+__device__ __forceinline__ bool det_conflict_lane(const Params &p, int32_t v, int c, int32_t dv,
+                                                  long long s, long long e, int32_t vb, bool prefix,
+                                                  unsigned long long &scanned) {
+    if (prefix) {
+        const long long split = s + __ldcg(p.lowdeg + v);
+        if (split <= s) return false;
+        for (long long q = (split - 1) >> 2; q >= (s >> 2); --q) {
+            const int4 x = load4(p.ci, q, p.m);
+            const long long i0 = q << 2;
+            int cw[4];
+            bool ok[4];
+#pragma unroll
+            for (int k = 3; k >= 0; --k) {
+                const long long i = i0 + k;
+                const int32_t w = vb + elem(x, k);
+                ok[k] = i >= s && i < split && (unsigned)w < (unsigned)p.n;
+                cw[k] = ok[k] ? __ldcg(p.colors + w) : 0;
+            }
+#pragma unroll
+            for (int k = 3; k >= 0; --k) {
+                if (!ok[k]) continue;
+                scanned++;
+                if ((cw[k] < 0 ? -cw[k] : cw[k]) == c) return true;
+            }
+        }
+        return false;
+    }
+    for (long long q = s >> 2; (q << 2) < e; ++q) {
+        const int4 x = load4(p.ci, q, p.m);
+        const long long i0 = q << 2;
+        int cw[4];
+        int32_t ww[4];
+        bool ok[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long i = i0 + k;
+            ww[k] = vb + elem(x, k);
+            ok[k] = i >= s && i < e && (unsigned)ww[k] < (unsigned)p.n && ww[k] != v;
+            if (p.rule == 0 && ww[k] > v) ok[k] = false;
+            if (p.rule == 1 && ww[k] < v) ok[k] = false;
+            cw[k] = ok[k] ? __ldcg(p.colors + ww[k]) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!ok[k]) continue;
+            scanned++;
+            if ((cw[k] < 0 ? -cw[k] : cw[k]) == c && loses_to<kBatched>(p, v, ww[k], dv)) return true;
+        }
+    }
+    return false;
+}
+
+// Record final color c in the bitmaps of the neighbours [a, b) (lanes lane0,
+// lane0 + stride, ... over 16-byte blocks).  Colors above 256 are not
+// recorded; bitmap_first_fit then falls back to a scan.
+__device__ __forceinline__ void scatter_color(const Params &p, int c, long long a, long long b,
+                                              int32_t vb, int lane0, int stride) {
+    if (c > 256) return;
+    unsigned *plane = p.bm + (size_t)((c - 1) >> 5) * p.np;
+    const unsigned bit = 1u << ((c - 1) & 31);
+    for (long long q = (a >> 2) + lane0; (q << 2) < b; q += stride) {
+        const int4 x = load4(p.ci, q, p.m);
+        const long long i0 = q << 2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long i = i0 + k;
+            const int32_t w = vb + elem(x, k);
+            if (i >= a && i < b && (unsigned)w < (unsigned)p.n) atomicOr(plane + w, bit);
+        }
+    }
+}
+
+template <bool kBatched>
+__device__ void det_light_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
+                                 unsigned *out_cnt, bool prefix, Acc &acc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
+    for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
+        bool flag[kLightUnroll];
+        int32_t item[kLightUnroll];
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) {
+            flag[u] = false;
+            item[u] = 0;
+            const unsigned idx = t * kLightTile + (u * kWarps + warp) * 32 + lane;
+            if (idx < cnt) {
+                const int32_t v = __ldcg(list + idx);
+                long long s, e;
+                int32_t vb;
+                row_of<kBatched>(p, v, s, e, vb);
+                const int c = -__ldcg(p.colors + v);
+                acc.w += 1;
+                acc.d += (unsigned long long)(e - s);
+                if (det_conflict_lane<kBatched>(p, v, c, (int32_t)(e - s), s, e, vb, prefix, acc.dscan)) {
+                    flag[u] = true;
+                    item[u] = v;
+                } else {
+                    __stcg(p.colors + v, c);
+                    acc.kmax = max(acc.kmax, c);
+                    scatter_color(p, c, s, e, vb, 0, 1);
+                    acc.scatter += (unsigned long long)(e - s);
+                }
+            }
+        }
+        block_push(flag, item, out_cnt, out, acc.next);
+    }
+}
+
+// Warp-wide det conflict test of v over entries [a, b) of its row (s = row
+// start).  prefix: scan [a, min(b, split)) from the top down, 128 entries per
+// step; `stop` (may be null) is polled between steps.
+template <bool kBatched>
+__device__ __forceinline__ bool det_conflict_warp(const Params &p, int32_t v, int c, int32_t dv,
+                                                  long long s, long long a, long long b, int32_t vb,
+                                                  bool prefix, const unsigned *stop,
+                                                  unsigned long long &scanned) {
+    const int lane = threadIdx.x & 31;
+    if (prefix) {
+        const long long split = s + __ldcg(p.lowdeg + v);
+        const long long hi = min(b, split);
+        if (hi <= a) return false;
+        for (long long top = (hi - 1) >> 2; top >= (a >> 2); top -= 32) {
+            const long long q = top - lane;
+            bool my = false;
+            if (q >= (a >> 2)) {
+                const int4 x = load4(p.ci, q, p.m);
+                const long long i0 = q << 2;
+                int cw[4];
+                bool ok[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const long long i = i0 + k;
+                    const int32_t w = vb + elem(x, k);
+                    ok[k] = i >= a && i < hi && (unsigned)w < (unsigned)p.n;
+                    cw[k] = ok[k] ? __ldcg(p.colors + w) : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!ok[k]) continue;
+                    scanned++;
+                    if ((cw[k] < 0 ? -cw[k] : cw[k]) == c) my = true;
+                }
+            }
+            if (__any_sync(kFull, my)) return true;
+            if (stop && __ldcg(stop)) return false;
+        }
+        return false;
+    }
+    for (long long q0 = a >> 2; (q0 << 2) < b; q0 += 32) {
+        const long long q = q0 + lane;
+        bool my = false;
+        if ((q << 2) < b) {
+            const int4 x = load4(p.ci, q, p.m);
+            const long long i0 = q << 2;
+            int cw[4];
+            int32_t ww[4];
+            bool ok[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long i = i0 + k;
+                ww[k] = vb + elem(x, k);
+                ok[k] = i >= a && i < b && (unsigned)ww[k] < (unsigned)p.n && ww[k] != v;
+                if (p.rule == 0 && ww[k] > v) ok[k] = false;
+                if (p.rule == 1 && ww[k] < v) ok[k] = false;
+                cw[k] = ok[k] ? __ldcg(p.colors + ww[k]) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!ok[k]) continue;
+                scanned++;
+                if ((cw[k] < 0 ? -cw[k] : cw[k]) == c && loses_to<kBatched>(p, v, ww[k], dv))
+                    my = true;
+            }
+        }
+        if (__any_sync(kFull, my)) return true;
+        if (stop && __ldcg(stop)) return false;
+    }
+    return false;
+}
+
+template <bool kBatched>
+__device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
+                                  unsigned *out_cnt, bool prefix, Acc &acc) {
+    const int lane = threadIdx.x & 31;
+    const unsigned gw = global_warp(), NW = total_warps();
+    for (unsigned b = gw * 32; b < cnt; b += 32 * NW) {
+        const unsigned i = b + lane;
+        int32_t vl = 0, vbl = 0;
+        long long sl = 0, el = 0;
+        int cl = 0;
+        if (i < cnt) {
+            vl = __ldcg(list + i);
+            row_of<kBatched>(p, vl, sl, el, vbl);
+            cl = -__ldcg(p.colors + vl);
+            acc.w += 1;
+            acc.d += (unsigned long long)(el - sl);
+        }
+        unsigned lost = 0;
+        const int nb = (int)min(32u, cnt - b);
+        for (int j = 0; j < nb; ++j) {
+            const int32_t v = __shfl_sync(kFull, vl, j), vb = __shfl_sync(kFull, vbl, j);
+            const long long s = __shfl_sync(kFull, sl, j), e = __shfl_sync(kFull, el, j);
+            const int c = __shfl_sync(kFull, cl, j);
+            const bool conf = det_conflict_warp<kBatched>(p, v, c, (int32_t)(e - s), s, s, e, vb,
+                                                          prefix, nullptr, acc.dscan);
+            if (conf) {
+                lost |= 1u << j;
+            } else {
+                if (lane == 0) {
+                    __stcg(p.colors + v, c);
+                    acc.kmax = max(acc.kmax, c);
+                    acc.scatter += (unsigned long long)(e - s);
+                }
+                scatter_color(p, c, s, e, vb, lane, 32);
+            }
+        }
+        if (lost) {
+            unsigned pos = 0;
+            if (lane == 0) pos = atomicAdd(out_cnt, (unsigned)__popc(lost));
+            pos = __shfl_sync(kFull, pos, 0);
+            if ((lost >> lane) & 1u) out[pos + __popc(lost & lanemask_lt())] = vl;
+            if (lane == 0) acc.next += (unsigned long long)__popc(lost);
+        }
+    }
+}
+
+template <bool kBatched>
+__device__ void det_hub_detect(const Params &p, int par, unsigned long long h64, bool prefix,
+                               Acc &acc) {
+    const int lane = threadIdx.x & 31;
+    const int pn = par ^ 1;
+    const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
+    const long long CH = p.chunk;
+    const unsigned NW = total_warps();
+    for (unsigned q = global_warp(); q < nch; q += NW) {
+        const unsigned i = hub_entry(p.hcb[par], cnt, q);
+        const int32_t slot = __ldcg(p.hw[par] + i);
+        const unsigned j = q - __ldcg(p.hcb[par] + i);
+        const int32_t v = __ldcg(p.hvert + slot);
+        long long s, e;
+        int32_t vb;
+        row_of<kBatched>(p, v, s, e, vb);
+        const long long deg = e - s;
+        const long long a = s + (long long)j * CH, b = min(e, a + CH);
+        const int c = -__ldcg(p.colors + v);
+        const bool conf = !__ldcg(p.hconf + slot) &&
+                          det_conflict_warp<kBatched>(p, v, c, (int32_t)deg, s, a, b, vb, prefix,
+                                                      p.hconf + slot, acc.dscan);
+        const unsigned nchunks = (unsigned)((deg + CH - 1) / CH);
+        if (lane == 0) {
+            if (conf) atomicOr(p.hconf + slot, 1u);
+            __threadfence();
+            if (atomicAdd(p.hdone + slot, 1u) == nchunks - 1) {
+                __threadfence();
+                const unsigned lost = __ldcg(p.hconf + slot);
+                __stcg(p.hconf + slot, 0u);
+                __stcg(p.hdone + slot, 0u);
+                acc.w += 1;
+                acc.d += (unsigned long long)deg;
+                if (lost) {
+                    hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
+                    acc.next += 1;
+                } else {
+                    __stcg(p.colors + v, c);
+                    acc.kmax = max(acc.kmax, c);
+                    acc.scatter += (unsigned long long)deg;
+                    hub_list_push(&p.ctr->sc64, p.sw, p.scb, slot, nchunks);
+                }
+            }
+        }
+    }
+}
+
+// Scatter the colors of the hubs committed in the last round (chunked).
+template <bool kBatched>
+__device__ void det_hub_scatter(const Params &p, unsigned long long sc64) {
+    const int lane = threadIdx.x & 31;
+    const unsigned cnt = (unsigned)(sc64 >> 32), nch = (unsigned)sc64;
+    const long long CH = p.chunk;
+    const unsigned NW = total_warps();
+    for (unsigned q = global_warp(); q < nch; q += NW) {
+        const unsigned i = hub_entry(p.scb, cnt, q);
+        const int32_t slot = __ldcg(p.sw + i);
+        const unsigned j = q - __ldcg(p.scb + i);
+        const int32_t v = __ldcg(p.hvert + slot);
+        long long s, e;
+        int32_t vb;
+        row_of<kBatched>(p, v, s, e, vb);
+        const long long a = s + (long long)j * CH, b = min(e, a + CH);
+        scatter_color(p, __ldcg(p.colors + v), a, b, vb, lane, 32);
+    }
+}
+
+// ------------------------------------------------------------ fast mode
+//
+// FirstFit gathers the live colors of all neighbours; a warp takes 32
+// consecutive worklist entries of low degree, stages their rows in shared
+// memory with coalesced loads (one streaming copy when the rows are
+// contiguous), then each lane works on its own row.
+
 __device__ __forceinline__ int stage_rows(const int32_t *__restrict__ ci, long long m, long long s,
                                           int deg, bool act, int32_t *sbuf) {
     const int lane = threadIdx.x & 31;
@@ -304,9 +684,9 @@ __device__ __forceinline__ int stage_rows(const int32_t *__restrict__ ci, long l
     return pre;
 }
 
-template <bool kFast, bool kBatched>
-__device__ void light_assign(const Params &p, const int32_t *list, unsigned cnt,
-                             int32_t *sbuf, Acc &acc) {
+template <bool kBatched>
+__device__ void fast_light_assign(const Params &p, const int32_t *list, unsigned cnt,
+                                  int32_t *sbuf, Acc &acc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
     for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
@@ -332,7 +712,7 @@ __device__ void light_assign(const Params &p, const int32_t *list, unsigned cnt,
                     }
                 }
                 const int c = __ffsll((long long)~mask);
-                __stcg(p.colors + v, kFast ? c : -c);
+                __stcg(p.colors + v, c);
                 acc.w += 1;
                 acc.d += (unsigned long long)deg;
             }
@@ -341,11 +721,11 @@ __device__ void light_assign(const Params &p, const int32_t *list, unsigned cnt,
     }
 }
 
-// Conflict test of one lane's vertex against its staged row.
-template <bool kFast, bool kBatched>
-__device__ __forceinline__ bool light_conflict(const Params &p, const int32_t *row, int deg,
-                                               int32_t v, int32_t vb, int c, bool prefix,
-                                               unsigned long long &scanned) {
+// Lane-level fast-mode conflict test against a staged row.
+template <bool kBatched>
+__device__ __forceinline__ bool fast_conflict_staged(const Params &p, const int32_t *row, int deg,
+                                                     int32_t v, int32_t vb, int c, bool prefix,
+                                                     unsigned long long &scanned) {
     bool conf = false;
     for (int j0 = 0; j0 < deg && !conf; j0 += 8) {
         int cw[8];
@@ -356,7 +736,7 @@ __device__ __forceinline__ bool light_conflict(const Params &p, const int32_t *r
         for (int k = 0; k < 8; ++k) {
             const int j = j0 + k;
             ww[k] = j < deg ? vb + row[j] : -1;
-            ok[k] = j < deg && (unsigned)ww[k] < (unsigned)p.n;
+            ok[k] = j < deg && (unsigned)ww[k] < (unsigned)p.n && ww[k] != v;
             if (prefix && ok[k] && ww[k] >= v) {
                 ok[k] = false;
                 past = true;
@@ -369,26 +749,26 @@ __device__ __forceinline__ bool light_conflict(const Params &p, const int32_t *r
         for (int k = 0; k < 8; ++k) {
             if (!ok[k]) continue;
             scanned++;
-            const int mag = kFast ? cw[k] : (cw[k] < 0 ? -cw[k] : cw[k]);
-            if (mag == c && loses_to<kBatched>(p, v, ww[k], deg)) conf = true;
+            if (cw[k] == c && loses_to<kBatched>(p, v, ww[k], deg)) conf = true;
         }
         if (past) break;
     }
     return conf;
 }
 
-template <bool kFast, bool kBatched>
-__device__ void light_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
-                             unsigned *out_cnt, bool prefix, int32_t *sbuf, Acc &acc) {
+template <bool kBatched>
+__device__ void fast_light_detect(const Params &p, const int32_t *list, unsigned cnt,
+                                  int32_t *out, unsigned *out_cnt, bool prefix, int32_t *sbuf,
+                                  Acc &acc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
     for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
-        int32_t items[kLightUnroll];
-        int n_items = 0;
-#pragma unroll
-        for (int u = 0; u < kLightUnroll; ++u) items[u] = 0;
+        bool flag[kLightUnroll];
+        int32_t item[kLightUnroll];
 #pragma unroll
         for (int u = 0; u < kLightUnroll; ++u) {
+            flag[u] = false;
+            item[u] = 0;
             const unsigned idx = t * kLightTile + (u * kWarps + warp) * 32 + lane;
             const bool act = idx < cnt;
             int32_t v = 0, vb = 0;
@@ -400,44 +780,28 @@ __device__ void light_detect(const Params &p, const int32_t *list, unsigned cnt,
             const int deg = (int)(e - s);
             const int pre = stage_rows(p.ci, p.m, s, deg, act, sbuf);
             if (act) {
-                const int own = __ldcg(p.colors + v);
-                const int c = kFast ? own : -own;
-                const bool conf =
-                    light_conflict<kFast, kBatched>(p, sbuf + pre, deg, v, vb, c, prefix, acc.dscan);
-                if (conf) {
-                    if (kFast) __stcg(p.colors + v, 0);
-#pragma unroll
-                    for (int z = 0; z < kLightUnroll; ++z)
-                        if (z == n_items) items[z] = v;
-                    ++n_items;
+                const int c = __ldcg(p.colors + v);
+                if (fast_conflict_staged<kBatched>(p, sbuf + pre, deg, v, vb, c, prefix, acc.dscan)) {
+                    __stcg(p.colors + v, 0);
+                    flag[u] = true;
+                    item[u] = v;
                 } else {
-                    if (!kFast) __stcg(p.colors + v, c);
                     acc.kmax = max(acc.kmax, c);
                 }
             }
             __syncwarp();
         }
-        block_push(n_items, items, out_cnt, out, acc.next);
+        block_push(flag, item, out_cnt, out, acc.next);
     }
 }
 
-// ------------------------------------------------------------ medium vertices
-//
-// One warp per vertex; warps take vertices round-robin (no work-grab atomics).
-// The warp fetches the list entries and row bounds of its next 32 vertices in
-// one go, then walks them.
-
-__device__ __forceinline__ unsigned global_warp() {
-    return (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-}
-
-__device__ __forceinline__ unsigned total_warps() { return (gridDim.x * blockDim.x) >> 5; }
-
-// Warp-wide conflict test of v (tentative color c) over entries [a, b).
-template <bool kFast, bool kBatched>
-__device__ __forceinline__ bool warp_conflict(const Params &p, int32_t v, int c, int32_t dv,
-                                              long long a, long long b, int32_t vb, bool prefix,
-                                              unsigned long long &scanned) {
+// Warp-wide fast-mode conflict test over [a, b): live colors, stop at the
+// first conflict (or, with ascending rows and low-keeps, at the first
+// neighbour above v).
+template <bool kBatched>
+__device__ __forceinline__ bool fast_conflict_warp(const Params &p, int32_t v, int c, int32_t dv,
+                                                   long long a, long long b, int32_t vb,
+                                                   bool prefix, unsigned long long &scanned) {
     const int lane = threadIdx.x & 31;
     for (long long q0 = (a >> 2); (q0 << 2) < b; q0 += 32) {
         const long long q = q0 + lane;
@@ -452,7 +816,7 @@ __device__ __forceinline__ bool warp_conflict(const Params &p, int32_t v, int c,
             for (int k = 0; k < 4; ++k) {
                 const long long i = i0 + k;
                 ww[k] = vb + elem(x, k);
-                ok[k] = i >= a && i < b && (unsigned)ww[k] < (unsigned)p.n;
+                ok[k] = i >= a && i < b && (unsigned)ww[k] < (unsigned)p.n && ww[k] != v;
                 if (prefix && ok[k] && ww[k] >= v) {
                     ok[k] = false;
                     past = true;
@@ -465,8 +829,7 @@ __device__ __forceinline__ bool warp_conflict(const Params &p, int32_t v, int c,
             for (int k = 0; k < 4; ++k) {
                 if (!ok[k]) continue;
                 scanned++;
-                const int mag = kFast ? cw[k] : (cw[k] < 0 ? -cw[k] : cw[k]);
-                if (mag == c && loses_to<kBatched>(p, v, ww[k], dv)) my = true;
+                if (cw[k] == c && loses_to<kBatched>(p, v, ww[k], dv)) my = true;
             }
         } else {
             past = true;
@@ -477,25 +840,25 @@ __device__ __forceinline__ bool warp_conflict(const Params &p, int32_t v, int c,
     return false;
 }
 
-template <bool kFast, bool kBatched>
-__device__ void medium_assign(const Params &p, const int32_t *list, unsigned cnt, Acc &acc) {
+template <bool kBatched>
+__device__ void fast_medium_assign(const Params &p, const int32_t *list, unsigned cnt, Acc &acc) {
     const int lane = threadIdx.x & 31;
     const unsigned gw = global_warp(), NW = total_warps();
-    for (unsigned b = gw; b < cnt; b += 32 * NW) {
-        const unsigned i = b + lane * NW;
+    for (unsigned b = gw * 32; b < cnt; b += 32 * NW) {
+        const unsigned i = b + lane;
         int32_t vl = 0, vbl = 0;
         long long sl = 0, el = 0;
         if (i < cnt) {
             vl = __ldcg(list + i);
             row_of<kBatched>(p, vl, sl, el, vbl);
         }
-        for (int j = 0; j < 32; ++j) {
-            if (b + j * NW >= cnt) break;
+        const int nb = (int)min(32u, cnt - b);
+        for (int j = 0; j < nb; ++j) {
             const int32_t v = __shfl_sync(kFull, vl, j), vb = __shfl_sync(kFull, vbl, j);
             const long long s = __shfl_sync(kFull, sl, j), e = __shfl_sync(kFull, el, j);
             const int c = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);
             if (lane == 0) {
-                __stcg(p.colors + v, kFast ? c : -c);
+                __stcg(p.colors + v, c);
                 acc.w += 1;
                 acc.d += (unsigned long long)(e - s);
             }
@@ -503,13 +866,13 @@ __device__ void medium_assign(const Params &p, const int32_t *list, unsigned cnt
     }
 }
 
-template <bool kFast, bool kBatched>
-__device__ void medium_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
-                              unsigned *out_cnt, bool prefix, Acc &acc) {
+template <bool kBatched>
+__device__ void fast_medium_detect(const Params &p, const int32_t *list, unsigned cnt,
+                                   int32_t *out, unsigned *out_cnt, bool prefix, Acc &acc) {
     const int lane = threadIdx.x & 31;
     const unsigned gw = global_warp(), NW = total_warps();
-    for (unsigned b = gw; b < cnt; b += 32 * NW) {
-        const unsigned i = b + lane * NW;
+    for (unsigned b = gw * 32; b < cnt; b += 32 * NW) {
+        const unsigned i = b + lane;
         int32_t vl = 0, vbl = 0;
         long long sl = 0, el = 0;
         if (i < cnt) {
@@ -517,19 +880,15 @@ __device__ void medium_detect(const Params &p, const int32_t *list, unsigned cnt
             row_of<kBatched>(p, vl, sl, el, vbl);
         }
         unsigned lost = 0;
-        for (int j = 0; j < 32; ++j) {
-            if (b + j * NW >= cnt) break;
+        const int nb = (int)min(32u, cnt - b);
+        for (int j = 0; j < nb; ++j) {
             const int32_t v = __shfl_sync(kFull, vl, j), vb = __shfl_sync(kFull, vbl, j);
             const long long s = __shfl_sync(kFull, sl, j), e = __shfl_sync(kFull, el, j);
-            const int own = __ldcg(p.colors + v);
-            const int c = kFast ? own : -own;
-            const bool conf =
-                warp_conflict<kFast, kBatched>(p, v, c, (int32_t)(e - s), s, e, vb, prefix, acc.dscan);
-            if (conf) {
+            const int c = __ldcg(p.colors + v);
+            if (fast_conflict_warp<kBatched>(p, v, c, (int32_t)(e - s), s, e, vb, prefix, acc.dscan)) {
                 lost |= 1u << j;
-                if (lane == 0 && kFast) __stcg(p.colors + v, 0);
+                if (lane == 0) __stcg(p.colors + v, 0);
             } else if (lane == 0) {
-                if (!kFast) __stcg(p.colors + v, c);
                 acc.kmax = max(acc.kmax, c);
             }
         }
@@ -537,37 +896,15 @@ __device__ void medium_detect(const Params &p, const int32_t *list, unsigned cnt
             unsigned pos = 0;
             if (lane == 0) pos = atomicAdd(out_cnt, (unsigned)__popc(lost));
             pos = __shfl_sync(kFull, pos, 0);
-            if ((lost >> lane) & 1u) out[pos + __popc(lost & ((1u << lane) - 1u))] = vl;
+            if ((lost >> lane) & 1u) out[pos + __popc(lost & lanemask_lt())] = vl;
             if (lane == 0) acc.next += (unsigned long long)__popc(lost);
         }
     }
 }
 
-// ------------------------------------------------------------ hubs
-//
-// A hub (degree > chunk) is split into ceil(deg / chunk) warp work items.
-// Items are taken round-robin by the warps of the grid; the item that
-// finishes last for a vertex (completion counter) resolves it.
-
-// index of the hub entry owning chunk q: largest i with cb[i] <= q (32-ary
-// search by the whole warp; cb is ascending and cb[0] == 0).
-__device__ __forceinline__ unsigned hub_entry(const unsigned *cb, unsigned cnt, unsigned q) {
-    const int lane = threadIdx.x & 31;
-    unsigned lo = 0, hi = cnt;
-    while (hi - lo > 1) {
-        const unsigned step = (hi - lo + 31) / 32;
-        const unsigned idx = lo + lane * step;
-        const bool ok = idx < hi && __ldcg(cb + idx) <= q;
-        const unsigned bal = __ballot_sync(kFull, ok);
-        const int last = 31 - __clz(bal);
-        lo = lo + (unsigned)last * step;
-        hi = min(hi, lo + step);
-    }
-    return lo;
-}
-
-template <bool kFast, bool kBatched>
-__device__ void hub_assign(const Params &p, int par, unsigned long long h64, int kmax, Acc &acc) {
+template <bool kBatched>
+__device__ void fast_hub_assign(const Params &p, int par, unsigned long long h64, int kmax,
+                                Acc &acc) {
     const int lane = threadIdx.x & 31;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const long long CH = p.chunk;
@@ -582,8 +919,7 @@ __device__ void hub_assign(const Params &p, int par, unsigned long long h64, int
         row_of<kBatched>(p, v, s, e, vb);
         const long long deg = e - s;
         const long long a = s + (long long)j * CH, b = min(e, a + CH);
-        // det: every forbidden color is final, hence <= kmax; fast: a guess with a fallback
-        long long nb = kFast ? (long long)kmax + 64 : (long long)kmax;
+        long long nb = (long long)kmax + 64;  // a guess; the last item falls back if full
         if (nb > deg) nb = deg;
         const int nbits = (int)nb + 1;
         const int words = (nbits + 31) >> 5;
@@ -616,9 +952,9 @@ __device__ void hub_assign(const Params &p, int par, unsigned long long h64, int
             best = __reduce_min_sync(kFull, best);
             int c;
             if (best < (unsigned)nbits) c = (int)best + 1;
-            else c = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);  // fast mode only
+            else c = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);
             if (lane == 0) {
-                __stcg(p.colors + v, kFast ? c : -c);
+                __stcg(p.colors + v, c);
                 __stcg(p.hdone + slot, 0u);
                 acc.w += 1;
                 acc.d += (unsigned long long)deg;
@@ -627,8 +963,9 @@ __device__ void hub_assign(const Params &p, int par, unsigned long long h64, int
     }
 }
 
-template <bool kFast, bool kBatched>
-__device__ void hub_detect(const Params &p, int par, unsigned long long h64, bool prefix, Acc &acc) {
+template <bool kBatched>
+__device__ void fast_hub_detect(const Params &p, int par, unsigned long long h64, bool prefix,
+                                Acc &acc) {
     const int lane = threadIdx.x & 31;
     const int pn = par ^ 1;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
@@ -644,31 +981,24 @@ __device__ void hub_detect(const Params &p, int par, unsigned long long h64, boo
         row_of<kBatched>(p, v, s, e, vb);
         const long long deg = e - s;
         const long long a = s + (long long)j * CH, b = min(e, a + CH);
-        const int own = __ldcg(p.colors + v);
-        const int c = kFast ? own : -own;
+        const int c = __ldcg(p.colors + v);
         const bool skip = prefix && (vb + __ldg(p.ci + a)) >= v;
         const bool conf =
-            !skip && warp_conflict<kFast, kBatched>(p, v, c, (int32_t)deg, a, b, vb, prefix, acc.dscan);
+            !skip && fast_conflict_warp<kBatched>(p, v, c, (int32_t)deg, a, b, vb, prefix, acc.dscan);
         const unsigned nchunks = (unsigned)((deg + CH - 1) / CH);
         if (lane == 0) {
             if (conf) atomicOr(p.hconf + slot, 1u);
             __threadfence();
-            const bool last = atomicAdd(p.hdone + slot, 1u) == nchunks - 1;
-            if (last) {
+            if (atomicAdd(p.hdone + slot, 1u) == nchunks - 1) {
                 __threadfence();
                 const unsigned lost = __ldcg(p.hconf + slot);
                 __stcg(p.hconf + slot, 0u);
                 __stcg(p.hdone + slot, 0u);
                 if (lost) {
-                    if (kFast) __stcg(p.colors + v, 0);
-                    const unsigned long long old =
-                        atomicAdd(&p.ctr->h64[pn], (1ull << 32) | (unsigned long long)nchunks);
-                    const unsigned k = (unsigned)(old >> 32);
-                    p.hw[pn][k] = slot;
-                    p.hcb[pn][k] = (unsigned)old;
+                    __stcg(p.colors + v, 0);
+                    hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
                     acc.next += 1;
                 } else {
-                    if (!kFast) __stcg(p.colors + v, c);
                     acc.kmax = max(acc.kmax, c);
                 }
             }
@@ -679,7 +1009,7 @@ __device__ void hub_detect(const Params &p, int par, unsigned long long h64, boo
 // ------------------------------------------------------------ init
 
 template <bool kFast, bool kBatched>
-__device__ void init_phase(const Params &p, Acc &acc) {
+__device__ void init_phase(const Params &p) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthreads = (long long)gridDim.x * blockDim.x;
     // (1) adjacent col_idx pairs out of strict ascending order
@@ -693,20 +1023,18 @@ __device__ void init_phase(const Params &p, Acc &acc) {
             if (i0 + k + 1 < p.m && elem(x, k) >= elem(x, k + 1)) bad++;
         if (i0 + 4 < p.m && x.w >= __ldg(p.ci + i0 + 4)) bad++;
     }
-    // (2) binning of all vertices into W_1 (parity 1)
-    unsigned long long boundary = 0;
+    // (2) binning of all vertices into W_1 (parity 1), in vertex order
+    unsigned long long boundary = 0, dummy = 0;
     const unsigned nt = ((unsigned)p.n + kLightTile - 1) / kLightTile;
     for (unsigned t = blockIdx.x; t < nt; t += gridDim.x) {
-        int32_t light[kLightUnroll], medium[kLightUnroll];
-        int nlight = 0, nmed = 0;
+        bool is_light[kLightUnroll], is_med[kLightUnroll];
+        int32_t vv[kLightUnroll];
 #pragma unroll
         for (int u = 0; u < kLightUnroll; ++u) {
-            light[u] = 0;
-            medium[u] = 0;
-        }
-#pragma unroll
-        for (int u = 0; u < kLightUnroll; ++u) {
+            is_light[u] = false;
+            is_med[u] = false;
             const long long v64 = (long long)t * kLightTile + u * kBlock + threadIdx.x;
+            vv[u] = (int32_t)v64;
             if (v64 >= p.n) continue;
             const int32_t v = (int32_t)v64;
             long long s, e;
@@ -715,38 +1043,31 @@ __device__ void init_phase(const Params &p, Acc &acc) {
             if (e > s && e < p.m && __ldg(p.ci + e - 1) >= __ldg(p.ci + e)) boundary++;
             __stcg(p.colors + v, kFast ? 0 : -1);
             const long long deg = e - s;
-            if (!kFast) {  // det round 1 has no FirstFit pass; count its scan here
-                acc.w += 1;
-                acc.d += (unsigned long long)deg;
+            if (!kFast) {  // entries below v, assuming an ascending row (used only if it is)
+                long long lo = s, hi = e;
+                while (lo < hi) {
+                    const long long mid = (lo + hi) >> 1;
+                    if (vb + __ldg(p.ci + mid) < v) lo = mid + 1;
+                    else hi = mid;
+                }
+                p.lowdeg[v] = (int32_t)(lo - s);
             }
             if (deg <= p.light_max) {
-#pragma unroll
-                for (int z = 0; z < kLightUnroll; ++z)
-                    if (z == nlight) light[z] = v;
-                ++nlight;
+                is_light[u] = true;
             } else if (deg <= p.chunk) {
-#pragma unroll
-                for (int z = 0; z < kLightUnroll; ++z)
-                    if (z == nmed) medium[z] = v;
-                ++nmed;
+                is_med[u] = true;
             } else {
                 const unsigned slot = atomicAdd(&p.ctr->nslots, 1u);
                 const unsigned words = (unsigned)((deg + 2 + 31) / 32);
                 p.hvert[slot] = v;
                 p.hbase[slot] = atomicAdd(&p.ctr->hwords, words);
-                const unsigned nchunks = (unsigned)((deg + p.chunk - 1) / p.chunk);
-                const unsigned long long old =
-                    atomicAdd(&p.ctr->h64[1], (1ull << 32) | (unsigned long long)nchunks);
-                const unsigned k = (unsigned)(old >> 32);
-                p.hw[1][k] = (int32_t)slot;
-                p.hcb[1][k] = (unsigned)old;
+                hub_list_push(&p.ctr->h64[1], p.hw[1], p.hcb[1], (int32_t)slot,
+                              (unsigned)((deg + p.chunk - 1) / p.chunk));
             }
         }
-        unsigned long long dummy = 0;
-        block_push(nlight, light, &p.ctr->nl[1], p.lw[1], dummy);
-        block_push(nmed, medium, &p.ctr->nm[1], p.mw[1], dummy);
+        block_push(is_light, vv, &p.ctr->nl[1], p.lw[1], dummy);
+        block_push(is_med, vv, &p.ctr->nm[1], p.mw[1], dummy);
     }
-    // block-reduce the two pair counts
     for (int o = 16; o > 0; o >>= 1) {
         bad += __shfl_xor_sync(kFull, bad, o);
         boundary += __shfl_xor_sync(kFull, boundary, o);
@@ -771,33 +1092,35 @@ __device__ void flush_kmax(const Params &p, int kloc) {
 }
 
 __device__ void flush_stats(const Params &p, Acc &acc) {
-    unsigned long long v[4] = {acc.w, acc.d, acc.dscan, acc.next};
+    unsigned long long v[5] = {acc.w, acc.d, acc.dscan, acc.next, acc.scatter};
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < 5; ++j)
         for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(kFull, v[j], o);
     if ((threadIdx.x & 31) == 0) {
         if (v[0]) atomicAdd(&p.ctr->sum_w, v[0]);
         if (v[1]) atomicAdd(&p.ctr->sum_d, v[1]);
         if (v[2]) atomicAdd(&p.ctr->sum_dscan, v[2]);
         if (v[3]) atomicAdd(&p.ctr->sum_next, v[3]);
+        if (v[4]) atomicAdd(&p.ctr->sum_scatter, v[4]);
     }
 }
 
 template <bool kFast, bool kBatched>
 __global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
-    __shared__ int32_t s_stage[kWarps][32 * kLightMaxStage];
-    int32_t *sbuf = s_stage[threadIdx.x >> 5];
+    __shared__ int32_t s_stage[kFast ? kWarps : 1][kFast ? 32 * kLightMaxStage : 1];
+    int32_t *sbuf = s_stage[kFast ? (threadIdx.x >> 5) : 0];
     Acc acc;
     unsigned gen = 0;
     Counters *ctr = p.ctr;
     const bool recorder = blockIdx.x == 0 && threadIdx.x == 0;
     const unsigned long long t0 = globaltimer();
-    init_phase<kFast, kBatched>(p, acc);
+    init_phase<kFast, kBatched>(p);
     if (!grid_barrier(p, gen)) { flush_stats(p, acc); return; }
     if (recorder) ctr->t_init_ns = (long long)(globaltimer() - t0);
     const bool sorted = __ldcg(&ctr->unsorted_pairs) == __ldcg(&ctr->boundary_pairs);
     const bool prefix = sorted && p.rule == 0;
     long long r = 1;
+    bool ok = true;
     for (;; ++r) {
         const int par = (int)(r & 1), pn = par ^ 1;
         const unsigned nl = __ldcg(&ctr->nl[par]);
@@ -807,42 +1130,59 @@ __global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
             (unsigned long long)nl + nm + (unsigned long long)(h64 >> 32);
         if (total == 0) break;
         if (r > p.max_rounds) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctr->err, 0, kErrNoConvergence);
+            if (recorder) atomicCAS(&ctr->err, 0, kErrNoConvergence);
             break;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!kFast) {  // colors of hubs committed last round go to their neighbours' bitmaps
+            const unsigned long long sc64 = __ldcg(&ctr->sc64);
+            if (sc64 >> 32) {
+                det_hub_scatter<kBatched>(p, sc64);
+                if (!(ok = grid_barrier(p, gen))) break;
+            }
+        }
+        if (recorder) {
             ctr->nl[pn] = 0;
             ctr->nm[pn] = 0;
             ctr->h64[pn] = 0;
+            if (!kFast) ctr->sc64 = 0;
             if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)total;
         }
-        // ---- phase A: FirstFit over W_r (skipped in det round 1: all tentative colors are 1)
-        if (kFast || r > 1) {
+        // ---- phase A: FirstFit over W_r (det round 1: every tentative color is 1)
+        if (kFast) {
             const int kmax = __ldcg(&ctr->kmax);
-            hub_assign<kFast, kBatched>(p, par, h64, kmax, acc);
-            medium_assign<kFast, kBatched>(p, p.mw[par], nm, acc);
-            light_assign<kFast, kBatched>(p, p.lw[par], nl, sbuf, acc);
+            fast_hub_assign<kBatched>(p, par, h64, kmax, acc);
+            fast_medium_assign<kBatched>(p, p.mw[par], nm, acc);
+            fast_light_assign<kBatched>(p, p.lw[par], nl, sbuf, acc);
+        } else if (r > 1) {
+            det_assign<kBatched>(p, p.hw[par], (unsigned)(h64 >> 32), true);
+            det_assign<kBatched>(p, p.mw[par], nm, false);
+            det_assign<kBatched>(p, p.lw[par], nl, false);
         }
-        if (!grid_barrier(p, gen)) break;
+        if (!(ok = grid_barrier(p, gen))) break;
         if (recorder && r <= kTraceCap)
             p.trace[kTraceFields * (r - 1) + 1] = (long long)(globaltimer() - t0);
         // ---- phase B: ConflictResolve over W_r, commit keepers, compact losers
-        int kloc = 0;
-        {
-            Acc b;
-            hub_detect<kFast, kBatched>(p, par, h64, prefix, b);
-            medium_detect<kFast, kBatched>(p, p.mw[par], nm, p.mw[pn], &ctr->nm[pn], prefix, b);
-            light_detect<kFast, kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix, sbuf, b);
-            acc.dscan += b.dscan;
-            acc.next += b.next;
-            kloc = b.kmax;
+        Acc b;
+        if (kFast) {
+            fast_hub_detect<kBatched>(p, par, h64, prefix, b);
+            fast_medium_detect<kBatched>(p, p.mw[par], nm, p.mw[pn], &ctr->nm[pn], prefix, b);
+            fast_light_detect<kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix, sbuf, b);
+        } else {
+            det_hub_detect<kBatched>(p, par, h64, prefix, b);
+            det_medium_detect<kBatched>(p, p.mw[par], nm, p.mw[pn], &ctr->nm[pn], prefix, b);
+            det_light_detect<kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix, b);
         }
-        flush_kmax(p, kloc);
-        if (!grid_barrier(p, gen)) break;
+        acc.w += b.w;
+        acc.d += b.d;
+        acc.dscan += b.dscan;
+        acc.next += b.next;
+        acc.scatter += b.scatter;
+        flush_kmax(p, b.kmax);
+        if (!(ok = grid_barrier(p, gen))) break;
         if (recorder && r <= kTraceCap)
             p.trace[kTraceFields * (r - 1) + 2] = (long long)(globaltimer() - t0);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->rounds = r - 1;
+    if (recorder && ok) ctr->rounds = r - 1;
     flush_stats(p, acc);
 }
 
