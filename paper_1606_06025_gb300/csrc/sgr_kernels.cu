@@ -233,28 +233,28 @@ __device__ __forceinline__ int warp_first_fit(const int32_t *__restrict__ ci, lo
 // ------------------------------------------------------------ compaction
 
 // Order-preserving block compaction of kLightUnroll flags per thread: item u
-// of thread (warp w, lane l) sits at tile position (u * kWarps + w) * 32 + l.
-// One atomicAdd per CTA tile.
+// of thread (warp w, lane l) sits at tile position (w * kLightUnroll + u) * 32
+// + l.  One atomicAdd per CTA tile.
 __device__ __forceinline__ void block_push(const bool (&flag)[kLightUnroll],
                                            const int32_t (&item)[kLightUnroll],
                                            unsigned *counter, int32_t *out,
                                            unsigned long long &pushed) {
-    __shared__ unsigned s_cnt[kLightUnroll][kWarps];
+    __shared__ unsigned s_cnt[kWarps][kLightUnroll];
     __shared__ unsigned s_base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned bal[kLightUnroll];
 #pragma unroll
     for (int u = 0; u < kLightUnroll; ++u) {
         bal[u] = __ballot_sync(kFull, flag[u]);
-        if (lane == 0) s_cnt[u][warp] = __popc(bal[u]);
+        if (lane == 0) s_cnt[warp][u] = __popc(bal[u]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned tot = 0;
-        for (int u = 0; u < kLightUnroll; ++u)
-            for (int w = 0; w < kWarps; ++w) {
-                const unsigned c = s_cnt[u][w];
-                s_cnt[u][w] = tot;
+        for (int w = 0; w < kWarps; ++w)
+            for (int u = 0; u < kLightUnroll; ++u) {
+                const unsigned c = s_cnt[w][u];
+                s_cnt[w][u] = tot;
                 tot += c;
             }
         s_base = tot ? atomicAdd(counter, tot) : 0u;
@@ -263,8 +263,27 @@ __device__ __forceinline__ void block_push(const bool (&flag)[kLightUnroll],
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < kLightUnroll; ++u)
-        if (flag[u]) out[s_base + s_cnt[u][warp] + __popc(bal[u] & lanemask_lt())] = item[u];
+        if (flag[u]) out[s_base + s_cnt[warp][u] + __popc(bal[u] & lanemask_lt())] = item[u];
     __syncthreads();
+}
+
+// Warp-level order-preserving push of one flag per lane.
+__device__ __forceinline__ void warp_push(bool flag, int32_t item, unsigned *counter,
+                                          int32_t *out, unsigned long long &pushed) {
+    const unsigned bal = __ballot_sync(kFull, flag);
+    if (!bal) return;
+    unsigned pos = 0;
+    if ((threadIdx.x & 31) == 0) {
+        pos = atomicAdd(counter, (unsigned)__popc(bal));
+        pushed += (unsigned long long)__popc(bal);
+    }
+    pos = __shfl_sync(kFull, pos, 0);
+    if (flag) out[pos + __popc(bal & lanemask_lt())] = item;
+}
+
+// Position of (tile t, warp w, sub-tile u, lane l) in a light list.
+__device__ __forceinline__ unsigned tile_index(unsigned t, int u) {
+    return t * kLightTile + ((threadIdx.x >> 5) * kLightUnroll + u) * 32 + (threadIdx.x & 31);
 }
 
 // index of the hub entry owning chunk q: largest i with cb[i] <= q (32-ary
@@ -295,58 +314,78 @@ __device__ __forceinline__ void hub_list_push(unsigned long long *ctr64, int32_t
 
 // ------------------------------------------------------------ det: FirstFit
 
-// First-fit colors of the final neighbour colors recorded in the bitmap of
-// v; 0 if colors 1..256 are all forbidden.
-__device__ __forceinline__ int bitmap_first_fit(const Params &p, int32_t v) {
-#pragma unroll 1
-    for (int j = 0; j < 8; ++j) {
-        const unsigned wv = __ldcg(p.bm + (size_t)j * p.np + v);
-        if (~wv) return j * 32 + __ffs(~wv);
-    }
-    return 0;
-}
-
 // Phase A of det mode over one list (vertex ids, or hub slots when `slots`).
+// Each warp takes 128 consecutive entries, four per lane, with all loads of
+// a stage in flight together.
 template <bool kBatched>
 __device__ void det_assign(const Params &p, const int32_t *list, unsigned cnt, bool slots) {
+    constexpr int U = 4;
     const int lane = threadIdx.x & 31;
     const unsigned NW = total_warps();
-    for (unsigned base = global_warp() * 32; base < cnt; base += NW * 32) {
-        const unsigned idx = base + lane;
-        const bool act = idx < cnt;
-        int32_t v = 0;
-        int c = 0;
-        if (act) {
-            v = __ldcg(list + idx);
-            if (slots) v = __ldcg(p.hvert + v);
-            c = bitmap_first_fit(p, v);
+    for (unsigned base = global_warp() * 32 * U; base < cnt; base += NW * 32 * U) {
+        int32_t v[U];
+        int c[U];
+        bool act[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned idx = base + u * 32 + lane;
+            act[u] = idx < cnt;
+            v[u] = act[u] ? __ldcg(list + idx) : 0;
         }
-        unsigned need = __ballot_sync(kFull, act && c == 0);
-        while (need) {  // bitmap full: scan the row (colors above 256 are in use)
-            const int src = __ffs(need) - 1;
-            need &= need - 1;
-            const int32_t u = __shfl_sync(kFull, v, src);
-            long long s, e;
-            int32_t vb;
-            row_of<kBatched>(p, u, s, e, vb);
-            const int cu = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);
-            if (lane == src) c = cu;
+        if (slots) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (act[u]) v[u] = __ldcg(p.hvert + v[u]);
         }
-        if (act) __stcg(p.colors + v, -c);
+        unsigned w0[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) w0[u] = act[u] ? __ldcg(p.bm + v[u]) : 0u;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            c[u] = 0;
+            if (act[u]) {
+                if (~w0[u]) {
+                    c[u] = __ffs(~w0[u]);
+                } else {  // colors 1..32 all forbidden: look at the higher planes
+                    for (int j = 1; j < 8 && c[u] == 0; ++j) {
+                        const unsigned wv = __ldcg(p.bm + (size_t)j * p.np + v[u]);
+                        if (~wv) c[u] = j * 32 + __ffs(~wv);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            unsigned need = __ballot_sync(kFull, act[u] && c[u] == 0);
+            while (need) {  // bitmap full: scan the row (colors above 256 are in use)
+                const int src = __ffs(need) - 1;
+                need &= need - 1;
+                const int32_t x = __shfl_sync(kFull, v[u], src);
+                long long s, e;
+                int32_t vb;
+                row_of<kBatched>(p, x, s, e, vb);
+                const int cx = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);
+                if (lane == src) c[u] = cx;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (act[u]) __stcg(p.colors + v[u], -c[u]);
     }
 }
 
 // ------------------------------------------------------------ det: ConflictResolve
 
-// Lane-level conflict test of v (tentative c) against its own row.
+// Lane-level conflict test of v (tentative c) against entries of its row.
+// With hi >= 0: entries [s, hi) are all below v (ascending row, low-keeps
+// rule) and are scanned from the top down.  With hi < 0: entries [s, e) are
+// scanned in order under the loser rule.  Stops at the first conflict.
 template <bool kBatched>
 __device__ __forceinline__ bool det_conflict_lane(const Params &p, int32_t v, int c, int32_t dv,
-                                                  long long s, long long e, int32_t vb, bool prefix,
-                                                  unsigned long long &scanned) {
-    if (prefix) {
-        const long long split = s + __ldcg(p.lowdeg + v);
-        if (split <= s) return false;
-        for (long long q = (split - 1) >> 2; q >= (s >> 2); --q) {
+                                                  long long s, long long e, int32_t vb, bool,
+                                                  unsigned long long &scanned, long long hi) {
+    if (hi >= 0) {
+        for (long long q = (e - 1) >> 2; hi > s && q >= (s >> 2); --q) {
             const int4 x = load4(p.ci, q, p.m);
             const long long i0 = q << 2;
             int cw[4];
@@ -355,7 +394,7 @@ __device__ __forceinline__ bool det_conflict_lane(const Params &p, int32_t v, in
             for (int k = 3; k >= 0; --k) {
                 const long long i = i0 + k;
                 const int32_t w = vb + elem(x, k);
-                ok[k] = i >= s && i < split && (unsigned)w < (unsigned)p.n;
+                ok[k] = i >= s && i < e && i < hi && (unsigned)w < (unsigned)p.n;
                 cw[k] = ok[k] ? __ldcg(p.colors + w) : 0;
             }
 #pragma unroll
@@ -412,37 +451,150 @@ __device__ __forceinline__ void scatter_color(const Params &p, int c, long long 
     }
 }
 
+// Scatter for a committed light vertex (degree <= 32): the row spans at most
+// nine 16-byte blocks; three are loaded at a time before their updates.
+__device__ __forceinline__ void scatter_light(const Params &p, int c, long long s, long long e,
+                                              int32_t vb) {
+    if (c > 256 || e <= s) return;
+    unsigned *plane = p.bm + (size_t)((c - 1) >> 5) * p.np;
+    const unsigned bit = 1u << ((c - 1) & 31);
+    const long long q1 = (e + 3) >> 2;
+    for (long long q0 = s >> 2; q0 < q1; q0 += 3) {
+        int4 x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[k] = q0 + k < q1 ? load4(p.ci, q0 + k, p.m) : make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long i = ((q0 + k) << 2) + j;
+                const int32_t w = vb + elem(x[k], j);
+                if (i >= s && i < e && (unsigned)w < (unsigned)p.n) atomicOr(plane + w, bit);
+            }
+    }
+}
+
+// Resolve U light worklist vertices per lane (list positions idx[u]): the
+// independent loads of all U vertices are issued stage by stage.  Losers come
+// back in flag/item; keepers are committed and scattered here.
+template <bool kBatched, int U>
+__device__ __forceinline__ void det_light_resolve(const Params &p, const int32_t *list,
+                                                  unsigned cnt, const unsigned (&idx)[U],
+                                                  bool prefix, bool (&flag)[U],
+                                                  int32_t (&item)[U], Acc &acc) {
+    int32_t v[U], vb[U], c[U], ld[U];
+    long long s[U], e[U];
+    bool act[U], conf[U], open[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        act[u] = idx[u] < cnt;
+        v[u] = act[u] ? __ldcg(list + idx[u]) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        s[u] = e[u] = 0;
+        vb[u] = 0;
+        c[u] = 0;
+        ld[u] = 0;
+        if (act[u]) {
+            row_of<kBatched>(p, v[u], s[u], e[u], vb[u]);
+            c[u] = -__ldcg(p.colors + v[u]);
+            if (prefix) ld[u] = __ldcg(p.lowdeg + v[u]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        conf[u] = false;
+        open[u] = act[u];
+        if (act[u]) {
+            acc.w += 1;
+            acc.d += (unsigned long long)(e[u] - s[u]);
+        }
+    }
+    if (prefix) {
+        // first probe: the 16-byte block that holds the nearest lower neighbour
+        long long q[U], split[U];
+        int4 x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            split[u] = s[u] + ld[u];
+            if (split[u] <= s[u]) open[u] = false;
+            q[u] = (split[u] - 1) >> 2;
+            x[u] = open[u] ? load4(p.ci, q[u], p.m) : make_int4(0, 0, 0, 0);
+        }
+        int cw[U][4];
+        bool ok[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long i = (q[u] << 2) + k;
+                const int32_t w = vb[u] + elem(x[u], k);
+                ok[u][k] = open[u] && i >= s[u] && i < split[u] && (unsigned)w < (unsigned)p.n;
+                cw[u][k] = ok[u][k] ? __ldcg(p.colors + w) : 0;
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (ok[u][k]) {
+                    acc.dscan++;
+                    if ((cw[u][k] < 0 ? -cw[u][k] : cw[u][k]) == c[u]) conf[u] = true;
+                }
+            // rest of the lower prefix (rare: keepers and far conflicts)
+            if (open[u] && !conf[u] && q[u] > (s[u] >> 2))
+                conf[u] = det_conflict_lane<kBatched>(p, v[u], c[u], (int32_t)(e[u] - s[u]), s[u],
+                                                      q[u] << 2, vb[u], false, acc.dscan, split[u]);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (act[u])
+                conf[u] = det_conflict_lane<kBatched>(p, v[u], c[u], (int32_t)(e[u] - s[u]), s[u],
+                                                      e[u], vb[u], false, acc.dscan, -1);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        flag[u] = act[u] && conf[u];
+        item[u] = v[u];
+        if (act[u] && !conf[u]) {
+            __stcg(p.colors + v[u], c[u]);
+            acc.kmax = max(acc.kmax, c[u]);
+            acc.scatter += (unsigned long long)(e[u] - s[u]);
+            scatter_light(p, c[u], s[u], e[u], vb[u]);
+        }
+    }
+}
+
 template <bool kBatched>
 __device__ void det_light_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
                                  unsigned *out_cnt, bool prefix, Acc &acc) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (cnt < 2u * gridDim.x * kLightTile) {
+        // small worklist: 32 entries per warp, spread over every warp of the grid
+        const unsigned NW = total_warps();
+        for (unsigned base = global_warp() * 32; base < cnt; base += NW * 32) {
+            const unsigned idx[1] = {base + (threadIdx.x & 31)};
+            bool flag[1];
+            int32_t item[1];
+            det_light_resolve<kBatched, 1>(p, list, cnt, idx, prefix, flag, item, acc);
+            warp_push(flag[0], item[0], out_cnt, out, acc.next);
+        }
+        return;
+    }
     const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
     for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
         bool flag[kLightUnroll];
         int32_t item[kLightUnroll];
 #pragma unroll
-        for (int u = 0; u < kLightUnroll; ++u) {
-            flag[u] = false;
-            item[u] = 0;
-            const unsigned idx = t * kLightTile + (u * kWarps + warp) * 32 + lane;
-            if (idx < cnt) {
-                const int32_t v = __ldcg(list + idx);
-                long long s, e;
-                int32_t vb;
-                row_of<kBatched>(p, v, s, e, vb);
-                const int c = -__ldcg(p.colors + v);
-                acc.w += 1;
-                acc.d += (unsigned long long)(e - s);
-                if (det_conflict_lane<kBatched>(p, v, c, (int32_t)(e - s), s, e, vb, prefix, acc.dscan)) {
-                    flag[u] = true;
-                    item[u] = v;
-                } else {
-                    __stcg(p.colors + v, c);
-                    acc.kmax = max(acc.kmax, c);
-                    scatter_color(p, c, s, e, vb, 0, 1);
-                    acc.scatter += (unsigned long long)(e - s);
-                }
-            }
+        for (int h = 0; h < kLightUnroll; h += 2) {
+            const unsigned idx[2] = {tile_index(t, h), tile_index(t, h + 1)};
+            bool f2[2];
+            int32_t i2[2];
+            det_light_resolve<kBatched, 2>(p, list, cnt, idx, prefix, f2, i2, acc);
+            flag[h] = f2[0];
+            flag[h + 1] = f2[1];
+            item[h] = i2[0];
+            item[h + 1] = i2[1];
         }
         block_push(flag, item, out_cnt, out, acc.next);
     }
@@ -520,17 +672,26 @@ __device__ __forceinline__ bool det_conflict_warp(const Params &p, int32_t v, in
     return false;
 }
 
+// Batch of worklist entries a warp takes at a time: spread a short list over
+// all warps, up to 32 entries (one per lane) for long lists.
+__device__ __forceinline__ unsigned warp_batch(unsigned cnt) {
+    const unsigned NW = total_warps();
+    const unsigned b = (cnt + NW - 1) / NW;
+    return b < 1 ? 1 : (b > 32 ? 32 : b);
+}
+
 template <bool kBatched>
 __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
                                   unsigned *out_cnt, bool prefix, Acc &acc) {
     const int lane = threadIdx.x & 31;
-    const unsigned gw = global_warp(), NW = total_warps();
-    for (unsigned b = gw * 32; b < cnt; b += 32 * NW) {
+    const unsigned NW = total_warps(), B = warp_batch(cnt);
+    for (unsigned b = global_warp() * B; b < cnt; b += NW * B) {
         const unsigned i = b + lane;
+        const int nb = (int)min(B, cnt - b);
         int32_t vl = 0, vbl = 0;
         long long sl = 0, el = 0;
         int cl = 0;
-        if (i < cnt) {
+        if (lane < nb) {
             vl = __ldcg(list + i);
             row_of<kBatched>(p, vl, sl, el, vbl);
             cl = -__ldcg(p.colors + vl);
@@ -538,7 +699,6 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
             acc.d += (unsigned long long)(el - sl);
         }
         unsigned lost = 0;
-        const int nb = (int)min(32u, cnt - b);
         for (int j = 0; j < nb; ++j) {
             const int32_t v = __shfl_sync(kFull, vl, j), vb = __shfl_sync(kFull, vbl, j);
             const long long s = __shfl_sync(kFull, sl, j), e = __shfl_sync(kFull, el, j);
@@ -687,11 +847,10 @@ __device__ __forceinline__ int stage_rows(const int32_t *__restrict__ ci, long l
 template <bool kBatched>
 __device__ void fast_light_assign(const Params &p, const int32_t *list, unsigned cnt,
                                   int32_t *sbuf, Acc &acc) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
     for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
         for (int u = 0; u < kLightUnroll; ++u) {
-            const unsigned idx = t * kLightTile + (u * kWarps + warp) * 32 + lane;
+            const unsigned idx = tile_index(t, u);
             const bool act = idx < cnt;
             int32_t v = 0, vb = 0;
             long long s = 0, e = 0;
@@ -760,7 +919,6 @@ template <bool kBatched>
 __device__ void fast_light_detect(const Params &p, const int32_t *list, unsigned cnt,
                                   int32_t *out, unsigned *out_cnt, bool prefix, int32_t *sbuf,
                                   Acc &acc) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
     for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
         bool flag[kLightUnroll];
@@ -769,7 +927,7 @@ __device__ void fast_light_detect(const Params &p, const int32_t *list, unsigned
         for (int u = 0; u < kLightUnroll; ++u) {
             flag[u] = false;
             item[u] = 0;
-            const unsigned idx = t * kLightTile + (u * kWarps + warp) * 32 + lane;
+            const unsigned idx = tile_index(t, u);
             const bool act = idx < cnt;
             int32_t v = 0, vb = 0;
             long long s = 0, e = 0;
@@ -843,16 +1001,16 @@ __device__ __forceinline__ bool fast_conflict_warp(const Params &p, int32_t v, i
 template <bool kBatched>
 __device__ void fast_medium_assign(const Params &p, const int32_t *list, unsigned cnt, Acc &acc) {
     const int lane = threadIdx.x & 31;
-    const unsigned gw = global_warp(), NW = total_warps();
-    for (unsigned b = gw * 32; b < cnt; b += 32 * NW) {
+    const unsigned NW = total_warps(), B = warp_batch(cnt);
+    for (unsigned b = global_warp() * B; b < cnt; b += NW * B) {
         const unsigned i = b + lane;
+        const int nb = (int)min(B, cnt - b);
         int32_t vl = 0, vbl = 0;
         long long sl = 0, el = 0;
-        if (i < cnt) {
+        if (lane < nb) {
             vl = __ldcg(list + i);
             row_of<kBatched>(p, vl, sl, el, vbl);
         }
-        const int nb = (int)min(32u, cnt - b);
         for (int j = 0; j < nb; ++j) {
             const int32_t v = __shfl_sync(kFull, vl, j), vb = __shfl_sync(kFull, vbl, j);
             const long long s = __shfl_sync(kFull, sl, j), e = __shfl_sync(kFull, el, j);
@@ -870,17 +1028,17 @@ template <bool kBatched>
 __device__ void fast_medium_detect(const Params &p, const int32_t *list, unsigned cnt,
                                    int32_t *out, unsigned *out_cnt, bool prefix, Acc &acc) {
     const int lane = threadIdx.x & 31;
-    const unsigned gw = global_warp(), NW = total_warps();
-    for (unsigned b = gw * 32; b < cnt; b += 32 * NW) {
+    const unsigned NW = total_warps(), B = warp_batch(cnt);
+    for (unsigned b = global_warp() * B; b < cnt; b += NW * B) {
         const unsigned i = b + lane;
+        const int nb = (int)min(B, cnt - b);
         int32_t vl = 0, vbl = 0;
         long long sl = 0, el = 0;
-        if (i < cnt) {
+        if (lane < nb) {
             vl = __ldcg(list + i);
             row_of<kBatched>(p, vl, sl, el, vbl);
         }
         unsigned lost = 0;
-        const int nb = (int)min(32u, cnt - b);
         for (int j = 0; j < nb; ++j) {
             const int32_t v = __shfl_sync(kFull, vl, j), vb = __shfl_sync(kFull, vbl, j);
             const long long s = __shfl_sync(kFull, sl, j), e = __shfl_sync(kFull, el, j);
@@ -1033,7 +1191,7 @@ __device__ void init_phase(const Params &p) {
         for (int u = 0; u < kLightUnroll; ++u) {
             is_light[u] = false;
             is_med[u] = false;
-            const long long v64 = (long long)t * kLightTile + u * kBlock + threadIdx.x;
+            const long long v64 = (long long)tile_index(t, u);
             vv[u] = (int32_t)v64;
             if (v64 >= p.n) continue;
             const int32_t v = (int32_t)v64;
