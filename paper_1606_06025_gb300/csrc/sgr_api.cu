@@ -184,6 +184,7 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     unsigned *bm = (unsigned *)take((size_t)np * 8 * 4);
     if (zero_bytes) *zero_bytes = j.fast ? zero_fast : off;
     int32_t *lowdeg = (int32_t *)take((size_t)j.n * 4);
+    int32_t *witness = (int32_t *)take((size_t)j.n * 4);
     int32_t *sw = (int32_t *)take(sp.hub_max * 4);
     unsigned *scb = (unsigned *)take(sp.hub_max * 4);
     long long *trace = (long long *)take(sizeof(long long) * sgr::kTraceCap * sgr::kTraceFields);
@@ -215,6 +216,7 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         p->bm = bm;
         p->np = np;
         p->lowdeg = lowdeg;
+        p->witness = witness;
         p->sw = sw;
         p->scb = scb;
         p->ctr = ctr;

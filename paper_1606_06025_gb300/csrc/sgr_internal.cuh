@@ -14,6 +14,7 @@
 //   bm[8][np]            det mode: bit c-1 of plane (c-1)/32 at vertex v is set
 //                        once a neighbour of v has committed color c (c <= 256).
 //   lowdeg[n]            det mode: entries below v in its (ascending) row.
+//   witness[n]           det mode: the neighbour that beat v last time, or -1.
 //   hub scatter list     det mode: hubs committed this round (slot + chunk
 //                        base), whose colors are scattered at the next round.
 //   Counters             list sizes, grid barrier, max
@@ -29,6 +30,7 @@ constexpr int kBlock = 256;                      // threads per CTA
 constexpr int kWarps = kBlock / 32;
 constexpr int kLightUnroll = 4;                  // 32-vertex sub-tiles per warp and light tile
 constexpr int kLightTile = kBlock * kLightUnroll;
+constexpr int kMinBlocks = 3;                    // CTAs per SM the register budget targets
 constexpr int kLightMaxStage = 32;               // largest light degree (staged rows per lane)
 constexpr int kTraceCap = 1 << 16;               // rounds recorded in the timeline
 constexpr int kTraceFields = 3;                  // |W_r|, ns at end of phase A, ns at end of phase B
@@ -52,9 +54,10 @@ struct Counters {
     unsigned long long boundary_pairs;   // ... of them across row boundaries
     unsigned long long sum_w, sum_d, sum_dscan, sum_next, sum_scatter;
     unsigned long long sc64;        // hub scatter list: (entries << 32) | total chunks
+    unsigned long long dcur;        // det: degree sum of the current worklist
     long long rounds;
     long long t_init_ns;            // globaltimer: end of the init pass (after its barrier)
-    long long pad[2];
+    long long pad[1];
 };
 
 struct Params {
@@ -78,6 +81,7 @@ struct Params {
     unsigned int *bm;          // det: 8 planes of np words
     long long np;              // plane stride (>= n, multiple of 64)
     int32_t *lowdeg;           // det
+    int32_t *witness;          // det: the neighbour that last beat v, or -1
     int32_t *sw;               // det: hub scatter list slots
     unsigned int *scb;         // det: hub scatter list chunk bases
     Counters *ctr;

@@ -152,6 +152,7 @@ __device__ __forceinline__ bool loses_to(const Params &p, int32_t v, int32_t w, 
 
 struct Acc {
     unsigned long long w = 0, d = 0, dscan = 0, next = 0, scatter = 0;
+    unsigned long long kdeg = 0;  // det: degree sum of this phase's keepers
     int kmax = 0;
 };
 
@@ -375,36 +376,45 @@ __device__ void det_assign(const Params &p, const int32_t *list, unsigned cnt, b
 }
 
 // ------------------------------------------------------------ det: ConflictResolve
+//
+// v (tentative color c) loses iff a neighbour w that wins against it under
+// the rule holds the same color magnitude.  A matching magnitude can only be
+// a same-round worklist vertex: every final color of a neighbour was avoided
+// by v's FirstFit.  So the neighbour that beat v in an earlier round (its
+// witness) settles a repeat loss with one read; otherwise v scans its row.
 
-// Lane-level conflict test of v (tentative c) against entries of its row.
-// With hi >= 0: entries [s, hi) are all below v (ascending row, low-keeps
-// rule) and are scanned from the top down.  With hi < 0: entries [s, e) are
-// scanned in order under the loser rule.  Stops at the first conflict.
+__device__ __forceinline__ int mag(int x) { return x < 0 ? -x : x; }
+
+// Lane-level scan of v's row for a conflict; returns the conflicting
+// neighbour or -1.  hi >= 0: entries [s, hi) are all below v (ascending row,
+// low-keeps rule) and are scanned from the top down; hi < 0: entries [s, e)
+// are scanned in order under the loser rule.
 template <bool kBatched>
-__device__ __forceinline__ bool det_conflict_lane(const Params &p, int32_t v, int c, int32_t dv,
-                                                  long long s, long long e, int32_t vb, bool,
-                                                  unsigned long long &scanned, long long hi) {
+__device__ __forceinline__ int32_t det_scan_lane(const Params &p, int32_t v, int c, int32_t dv,
+                                                 long long s, long long e, int32_t vb,
+                                                 long long hi, unsigned long long &scanned) {
     if (hi >= 0) {
-        for (long long q = (e - 1) >> 2; hi > s && q >= (s >> 2); --q) {
+        for (long long q = (hi - 1) >> 2; hi > s && q >= (s >> 2); --q) {
             const int4 x = load4(p.ci, q, p.m);
             const long long i0 = q << 2;
             int cw[4];
+            int32_t ww[4];
             bool ok[4];
 #pragma unroll
             for (int k = 3; k >= 0; --k) {
                 const long long i = i0 + k;
-                const int32_t w = vb + elem(x, k);
-                ok[k] = i >= s && i < e && i < hi && (unsigned)w < (unsigned)p.n;
-                cw[k] = ok[k] ? __ldcg(p.colors + w) : 0;
+                ww[k] = vb + elem(x, k);
+                ok[k] = i >= s && i < hi && (unsigned)ww[k] < (unsigned)p.n;
+                cw[k] = ok[k] ? __ldcg(p.colors + ww[k]) : 0;
             }
 #pragma unroll
             for (int k = 3; k >= 0; --k) {
                 if (!ok[k]) continue;
                 scanned++;
-                if ((cw[k] < 0 ? -cw[k] : cw[k]) == c) return true;
+                if (mag(cw[k]) == c) return ww[k];
             }
         }
-        return false;
+        return -1;
     }
     for (long long q = s >> 2; (q << 2) < e; ++q) {
         const int4 x = load4(p.ci, q, p.m);
@@ -425,15 +435,15 @@ __device__ __forceinline__ bool det_conflict_lane(const Params &p, int32_t v, in
         for (int k = 0; k < 4; ++k) {
             if (!ok[k]) continue;
             scanned++;
-            if ((cw[k] < 0 ? -cw[k] : cw[k]) == c && loses_to<kBatched>(p, v, ww[k], dv)) return true;
+            if (mag(cw[k]) == c && loses_to<kBatched>(p, v, ww[k], dv)) return ww[k];
         }
     }
-    return false;
+    return -1;
 }
 
 // Record final color c in the bitmaps of the neighbours [a, b) (lanes lane0,
 // lane0 + stride, ... over 16-byte blocks).  Colors above 256 are not
-// recorded; bitmap_first_fit then falls back to a scan.
+// recorded; FirstFit then falls back to a scan.
 __device__ __forceinline__ void scatter_color(const Params &p, int c, long long a, long long b,
                                               int32_t vb, int lane0, int stride) {
     if (c > 256) return;
@@ -474,17 +484,19 @@ __device__ __forceinline__ void scatter_light(const Params &p, int c, long long 
     }
 }
 
-// Resolve U light worklist vertices per lane (list positions idx[u]): the
-// independent loads of all U vertices are issued stage by stage.  Losers come
-// back in flag/item; keepers are committed and scattered here.
+// Resolve U light worklist vertices per lane (list positions idx[u]), the
+// independent loads of all U vertices issued stage by stage: entry, then
+// witness and own color, then the witness's color.  Vertices the witness does
+// not settle probe the 16-byte block of their nearest lower neighbour, then
+// scan the rest of the row if needed.  Losers come back in flag/item;
+// keepers are committed and scattered here.
 template <bool kBatched, int U>
 __device__ __forceinline__ void det_light_resolve(const Params &p, const int32_t *list,
                                                   unsigned cnt, const unsigned (&idx)[U],
                                                   bool prefix, bool (&flag)[U],
                                                   int32_t (&item)[U], Acc &acc) {
-    int32_t v[U], vb[U], c[U], ld[U];
-    long long s[U], e[U];
-    bool act[U], conf[U], open[U];
+    int32_t v[U], wit[U], c[U];
+    bool act[U], conf[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         act[u] = idx[u] < cnt;
@@ -492,35 +504,36 @@ __device__ __forceinline__ void det_light_resolve(const Params &p, const int32_t
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        s[u] = e[u] = 0;
-        vb[u] = 0;
-        c[u] = 0;
-        ld[u] = 0;
-        if (act[u]) {
-            row_of<kBatched>(p, v[u], s[u], e[u], vb[u]);
-            c[u] = -__ldcg(p.colors + v[u]);
-            if (prefix) ld[u] = __ldcg(p.lowdeg + v[u]);
-        }
+        wit[u] = act[u] ? __ldcg(p.witness + v[u]) : -1;
+        c[u] = act[u] ? -__ldcg(p.colors + v[u]) : 0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        conf[u] = false;
-        open[u] = act[u];
-        if (act[u]) {
-            acc.w += 1;
-            acc.d += (unsigned long long)(e[u] - s[u]);
+        const int cw = wit[u] >= 0 ? __ldcg(p.colors + wit[u]) : 0;
+        conf[u] = wit[u] >= 0 && mag(cw) == c[u];
+    }
+    // slow path: vertices the witness does not settle
+    bool need[U];
+    long long s[U], e[U], hi[U];
+    int32_t vb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        need[u] = act[u] && !conf[u];
+        s[u] = e[u] = 0;
+        vb[u] = 0;
+        hi[u] = -1;
+        if (need[u]) {
+            row_of<kBatched>(p, v[u], s[u], e[u], vb[u]);
+            if (prefix) hi[u] = s[u] + __ldcg(p.lowdeg + v[u]);
         }
     }
-    if (prefix) {
-        // first probe: the 16-byte block that holds the nearest lower neighbour
-        long long q[U], split[U];
+    if (prefix) {  // first probe: the 16-byte block of the nearest lower neighbour
         int4 x[U];
+        long long q[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            split[u] = s[u] + ld[u];
-            if (split[u] <= s[u]) open[u] = false;
-            q[u] = (split[u] - 1) >> 2;
-            x[u] = open[u] ? load4(p.ci, q[u], p.m) : make_int4(0, 0, 0, 0);
+            q[u] = (hi[u] - 1) >> 2;
+            x[u] = need[u] && hi[u] > s[u] ? load4(p.ci, q[u], p.m) : make_int4(0, 0, 0, 0);
         }
         int cw[U][4];
         bool ok[U][4];
@@ -530,28 +543,37 @@ __device__ __forceinline__ void det_light_resolve(const Params &p, const int32_t
             for (int k = 0; k < 4; ++k) {
                 const long long i = (q[u] << 2) + k;
                 const int32_t w = vb[u] + elem(x[u], k);
-                ok[u][k] = open[u] && i >= s[u] && i < split[u] && (unsigned)w < (unsigned)p.n;
+                ok[u][k] = need[u] && i >= s[u] && i < hi[u] && (unsigned)w < (unsigned)p.n;
                 cw[u][k] = ok[u][k] ? __ldcg(p.colors + w) : 0;
             }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+            int32_t found = -1;
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 3; k >= 0; --k)
                 if (ok[u][k]) {
                     acc.dscan++;
-                    if ((cw[u][k] < 0 ? -cw[u][k] : cw[u][k]) == c[u]) conf[u] = true;
+                    if (found < 0 && mag(cw[u][k]) == c[u]) found = vb[u] + elem(x[u], k);
                 }
-            // rest of the lower prefix (rare: keepers and far conflicts)
-            if (open[u] && !conf[u] && q[u] > (s[u] >> 2))
-                conf[u] = det_conflict_lane<kBatched>(p, v[u], c[u], (int32_t)(e[u] - s[u]), s[u],
-                                                      q[u] << 2, vb[u], false, acc.dscan, split[u]);
+            if (need[u] && found < 0 && q[u] > (s[u] >> 2))  // rest of the lower prefix
+                found = det_scan_lane<kBatched>(p, v[u], c[u], (int32_t)(e[u] - s[u]), s[u], e[u],
+                                                vb[u], q[u] << 2, acc.dscan);
+            if (found >= 0) {
+                conf[u] = true;
+                __stcg(p.witness + v[u], found);
+            }
         }
     } else {
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (act[u])
-                conf[u] = det_conflict_lane<kBatched>(p, v[u], c[u], (int32_t)(e[u] - s[u]), s[u],
-                                                      e[u], vb[u], false, acc.dscan, -1);
+            if (need[u]) {
+                const int32_t found = det_scan_lane<kBatched>(p, v[u], c[u], (int32_t)(e[u] - s[u]),
+                                                              s[u], e[u], vb[u], -1, acc.dscan);
+                if (found >= 0) {
+                    conf[u] = true;
+                    __stcg(p.witness + v[u], found);
+                }
+            }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -560,6 +582,7 @@ __device__ __forceinline__ void det_light_resolve(const Params &p, const int32_t
         if (act[u] && !conf[u]) {
             __stcg(p.colors + v[u], c[u]);
             acc.kmax = max(acc.kmax, c[u]);
+            acc.kdeg += (unsigned long long)(e[u] - s[u]);
             acc.scatter += (unsigned long long)(e[u] - s[u]);
             scatter_light(p, c[u], s[u], e[u], vb[u]);
         }
@@ -570,7 +593,7 @@ template <bool kBatched>
 __device__ void det_light_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
                                  unsigned *out_cnt, bool prefix, Acc &acc) {
     if (cnt < 2u * gridDim.x * kLightTile) {
-        // small worklist: 32 entries per warp, spread over every warp of the grid
+        // short worklist: 32 entries per warp, spread over every warp of the grid
         const unsigned NW = total_warps();
         for (unsigned base = global_warp() * 32; base < cnt; base += NW * 32) {
             const unsigned idx[1] = {base + (threadIdx.x & 31)};
@@ -585,37 +608,31 @@ __device__ void det_light_detect(const Params &p, const int32_t *list, unsigned 
     for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
         bool flag[kLightUnroll];
         int32_t item[kLightUnroll];
+        unsigned idx[kLightUnroll];
 #pragma unroll
-        for (int h = 0; h < kLightUnroll; h += 2) {
-            const unsigned idx[2] = {tile_index(t, h), tile_index(t, h + 1)};
-            bool f2[2];
-            int32_t i2[2];
-            det_light_resolve<kBatched, 2>(p, list, cnt, idx, prefix, f2, i2, acc);
-            flag[h] = f2[0];
-            flag[h + 1] = f2[1];
-            item[h] = i2[0];
-            item[h + 1] = i2[1];
-        }
+        for (int u = 0; u < kLightUnroll; ++u) idx[u] = tile_index(t, u);
+        det_light_resolve<kBatched, kLightUnroll>(p, list, cnt, idx, prefix, flag, item, acc);
         block_push(flag, item, out_cnt, out, acc.next);
     }
 }
 
-// Warp-wide det conflict test of v over entries [a, b) of its row (s = row
-// start).  prefix: scan [a, min(b, split)) from the top down, 128 entries per
-// step; `stop` (may be null) is polled between steps.
+// Warp-wide det scan of entries [a, b) of v's row (s = row start); returns
+// the conflicting neighbour or -1.  prefix: entries below v, [a, min(b,
+// split)), 128 per step from the top down; `stop` (may be null) is polled
+// between steps.
 template <bool kBatched>
-__device__ __forceinline__ bool det_conflict_warp(const Params &p, int32_t v, int c, int32_t dv,
-                                                  long long s, long long a, long long b, int32_t vb,
-                                                  bool prefix, const unsigned *stop,
-                                                  unsigned long long &scanned) {
+__device__ __forceinline__ int32_t det_scan_warp(const Params &p, int32_t v, int c, int32_t dv,
+                                                 long long s, long long a, long long b, int32_t vb,
+                                                 bool prefix, const unsigned *stop,
+                                                 unsigned long long &scanned) {
     const int lane = threadIdx.x & 31;
     if (prefix) {
         const long long split = s + __ldcg(p.lowdeg + v);
         const long long hi = min(b, split);
-        if (hi <= a) return false;
+        if (hi <= a) return -1;
         for (long long top = (hi - 1) >> 2; top >= (a >> 2); top -= 32) {
             const long long q = top - lane;
-            bool my = false;
+            int32_t my = -1;
             if (q >= (a >> 2)) {
                 const int4 x = load4(p.ci, q, p.m);
                 const long long i0 = q << 2;
@@ -632,17 +649,18 @@ __device__ __forceinline__ bool det_conflict_warp(const Params &p, int32_t v, in
                 for (int k = 0; k < 4; ++k) {
                     if (!ok[k]) continue;
                     scanned++;
-                    if ((cw[k] < 0 ? -cw[k] : cw[k]) == c) my = true;
+                    if (mag(cw[k]) == c) my = vb + elem(x, k);
                 }
             }
-            if (__any_sync(kFull, my)) return true;
-            if (stop && __ldcg(stop)) return false;
+            const unsigned bal = __ballot_sync(kFull, my >= 0);
+            if (bal) return __shfl_sync(kFull, my, __ffs(bal) - 1);
+            if (stop && __ldcg(stop)) return -1;
         }
-        return false;
+        return -1;
     }
     for (long long q0 = a >> 2; (q0 << 2) < b; q0 += 32) {
         const long long q = q0 + lane;
-        bool my = false;
+        int32_t my = -1;
         if ((q << 2) < b) {
             const int4 x = load4(p.ci, q, p.m);
             const long long i0 = q << 2;
@@ -662,14 +680,14 @@ __device__ __forceinline__ bool det_conflict_warp(const Params &p, int32_t v, in
             for (int k = 0; k < 4; ++k) {
                 if (!ok[k]) continue;
                 scanned++;
-                if ((cw[k] < 0 ? -cw[k] : cw[k]) == c && loses_to<kBatched>(p, v, ww[k], dv))
-                    my = true;
+                if (mag(cw[k]) == c && loses_to<kBatched>(p, v, ww[k], dv)) my = ww[k];
             }
         }
-        if (__any_sync(kFull, my)) return true;
-        if (stop && __ldcg(stop)) return false;
+        const unsigned bal = __ballot_sync(kFull, my >= 0);
+        if (bal) return __shfl_sync(kFull, my, __ffs(bal) - 1);
+        if (stop && __ldcg(stop)) return -1;
     }
-    return false;
+    return -1;
 }
 
 // Batch of worklist entries a warp takes at a time: spread a short list over
@@ -688,29 +706,33 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
     for (unsigned b = global_warp() * B; b < cnt; b += NW * B) {
         const unsigned i = b + lane;
         const int nb = (int)min(B, cnt - b);
-        int32_t vl = 0, vbl = 0;
+        int32_t vl = 0, vbl = 0, wl = -1;
         long long sl = 0, el = 0;
         int cl = 0;
+        bool settled = false;
         if (lane < nb) {
             vl = __ldcg(list + i);
-            row_of<kBatched>(p, vl, sl, el, vbl);
+            wl = __ldcg(p.witness + vl);
             cl = -__ldcg(p.colors + vl);
-            acc.w += 1;
-            acc.d += (unsigned long long)(el - sl);
+            row_of<kBatched>(p, vl, sl, el, vbl);
+            if (wl >= 0) settled = mag(__ldcg(p.colors + wl)) == cl;
         }
-        unsigned lost = 0;
+        unsigned lost = __ballot_sync(kFull, settled);
         for (int j = 0; j < nb; ++j) {
+            if ((lost >> j) & 1u) continue;
             const int32_t v = __shfl_sync(kFull, vl, j), vb = __shfl_sync(kFull, vbl, j);
             const long long s = __shfl_sync(kFull, sl, j), e = __shfl_sync(kFull, el, j);
             const int c = __shfl_sync(kFull, cl, j);
-            const bool conf = det_conflict_warp<kBatched>(p, v, c, (int32_t)(e - s), s, s, e, vb,
+            const int32_t found = det_scan_warp<kBatched>(p, v, c, (int32_t)(e - s), s, s, e, vb,
                                                           prefix, nullptr, acc.dscan);
-            if (conf) {
+            if (found >= 0) {
                 lost |= 1u << j;
+                if (lane == 0) __stcg(p.witness + v, found);
             } else {
                 if (lane == 0) {
                     __stcg(p.colors + v, c);
                     acc.kmax = max(acc.kmax, c);
+                    acc.kdeg += (unsigned long long)(e - s);
                     acc.scatter += (unsigned long long)(e - s);
                 }
                 scatter_color(p, c, s, e, vb, lane, 32);
@@ -745,9 +767,19 @@ __device__ void det_hub_detect(const Params &p, int par, unsigned long long h64,
         const long long deg = e - s;
         const long long a = s + (long long)j * CH, b = min(e, a + CH);
         const int c = -__ldcg(p.colors + v);
-        const bool conf = !__ldcg(p.hconf + slot) &&
-                          det_conflict_warp<kBatched>(p, v, c, (int32_t)deg, s, a, b, vb, prefix,
-                                                      p.hconf + slot, acc.dscan);
+        bool conf = false;
+        if (j == 0) {  // the first item tries the witness
+            const int32_t w = __ldcg(p.witness + v);
+            conf = w >= 0 && mag(__ldcg(p.colors + w)) == c;
+        }
+        if (!conf && !__ldcg(p.hconf + slot)) {
+            const int32_t found = det_scan_warp<kBatched>(p, v, c, (int32_t)deg, s, a, b, vb, prefix,
+                                                          p.hconf + slot, acc.dscan);
+            if (found >= 0) {
+                conf = true;
+                if (lane == 0) __stcg(p.witness + v, found);
+            }
+        }
         const unsigned nchunks = (unsigned)((deg + CH - 1) / CH);
         if (lane == 0) {
             if (conf) atomicOr(p.hconf + slot, 1u);
@@ -757,14 +789,13 @@ __device__ void det_hub_detect(const Params &p, int par, unsigned long long h64,
                 const unsigned lost = __ldcg(p.hconf + slot);
                 __stcg(p.hconf + slot, 0u);
                 __stcg(p.hdone + slot, 0u);
-                acc.w += 1;
-                acc.d += (unsigned long long)deg;
                 if (lost) {
                     hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
                     acc.next += 1;
                 } else {
                     __stcg(p.colors + v, c);
                     acc.kmax = max(acc.kmax, c);
+                    acc.kdeg += (unsigned long long)deg;
                     acc.scatter += (unsigned long long)deg;
                     hub_list_push(&p.ctr->sc64, p.sw, p.scb, slot, nchunks);
                 }
@@ -1200,6 +1231,7 @@ __device__ void init_phase(const Params &p) {
             row_of<kBatched>(p, v, s, e, vb);
             if (e > s && e < p.m && __ldg(p.ci + e - 1) >= __ldg(p.ci + e)) boundary++;
             __stcg(p.colors + v, kFast ? 0 : -1);
+            if (!kFast) p.witness[v] = -1;
             const long long deg = e - s;
             if (!kFast) {  // entries below v, assuming an ascending row (used only if it is)
                 long long lo = s, hi = e;
@@ -1236,16 +1268,30 @@ __device__ void init_phase(const Params &p) {
     }
 }
 
-__device__ void flush_kmax(const Params &p, int kloc) {
+// End of phase B: the CTA's largest committed color and (det) the degree sum
+// of its keepers, which leave the worklist.
+__device__ void flush_phase(const Params &p, int kloc, unsigned long long kdeg) {
     __shared__ int s_k[kWarps];
+    __shared__ unsigned long long s_d[kWarps];
     int k = kloc;
-    for (int o = 16; o > 0; o >>= 1) k = max(k, __shfl_xor_sync(kFull, k, o));
-    if ((threadIdx.x & 31) == 0) s_k[threadIdx.x >> 5] = k;
+    for (int o = 16; o > 0; o >>= 1) {
+        k = max(k, __shfl_xor_sync(kFull, k, o));
+        kdeg += __shfl_xor_sync(kFull, kdeg, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_k[threadIdx.x >> 5] = k;
+        s_d[threadIdx.x >> 5] = kdeg;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         int b = 0;
-        for (int w = 0; w < kWarps; ++w) b = max(b, s_k[w]);
+        unsigned long long d = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            b = max(b, s_k[w]);
+            d += s_d[w];
+        }
         if (b > 0 && b > *(volatile int *)&p.ctr->kmax) atomicMax(&p.ctr->kmax, b);
+        if (d) atomicAdd(&p.ctr->dcur, 0ull - d);
     }
 }
 
@@ -1264,7 +1310,7 @@ __device__ void flush_stats(const Params &p, Acc &acc) {
 }
 
 template <bool kFast, bool kBatched>
-__global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
+__global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Params p) {
     __shared__ int32_t s_stage[kFast ? kWarps : 1][kFast ? 32 * kLightMaxStage : 1];
     int32_t *sbuf = s_stage[kFast ? (threadIdx.x >> 5) : 0];
     Acc acc;
@@ -1272,6 +1318,7 @@ __global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
     Counters *ctr = p.ctr;
     const bool recorder = blockIdx.x == 0 && threadIdx.x == 0;
     const unsigned long long t0 = globaltimer();
+    if (recorder && !kFast) ctr->dcur = (unsigned long long)p.m;
     init_phase<kFast, kBatched>(p);
     if (!grid_barrier(p, gen)) { flush_stats(p, acc); return; }
     if (recorder) ctr->t_init_ns = (long long)(globaltimer() - t0);
@@ -1302,7 +1349,11 @@ __global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
             ctr->nl[pn] = 0;
             ctr->nm[pn] = 0;
             ctr->h64[pn] = 0;
-            if (!kFast) ctr->sc64 = 0;
+            if (!kFast) {
+                ctr->sc64 = 0;
+                ctr->sum_w += total;                       // |W_r|
+                ctr->sum_d += __ldcg(&ctr->dcur);          // D_r: degrees of W_r
+            }
             if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)total;
         }
         // ---- phase A: FirstFit over W_r (det round 1: every tentative color is 1)
@@ -1335,7 +1386,7 @@ __global__ void __launch_bounds__(kBlock) sgr_color_kernel(const Params p) {
         acc.dscan += b.dscan;
         acc.next += b.next;
         acc.scatter += b.scatter;
-        flush_kmax(p, b.kmax);
+        flush_phase(p, b.kmax, b.kdeg);
         if (!(ok = grid_barrier(p, gen))) break;
         if (recorder && r <= kTraceCap)
             p.trace[kTraceFields * (r - 1) + 2] = (long long)(globaltimer() - t0);
