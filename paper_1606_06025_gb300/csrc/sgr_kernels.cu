@@ -461,35 +461,113 @@ __device__ __forceinline__ void scatter_color(const Params &p, int c, long long 
     }
 }
 
-// Scatter for a committed light vertex (degree <= 32): the row spans at most
-// nine 16-byte blocks; three are loaded at a time before their updates.
-__device__ __forceinline__ void scatter_light(const Params &p, int c, long long s, long long e,
-                                              int32_t vb) {
-    if (c > 256 || e <= s) return;
-    unsigned *plane = p.bm + (size_t)((c - 1) >> 5) * p.np;
-    const unsigned bit = 1u << ((c - 1) & 31);
-    const long long q1 = (e + 3) >> 2;
-    for (long long q0 = s >> 2; q0 < q1; q0 += 3) {
-        int4 x[3];
+// Warp-cooperative pass over one "segment" per lane: lane j owns entries
+// [s_j, s_j + len_j) of col_idx (len_j may be 0).  The segments are laid end
+// to end and the warp walks them 32 entries at a time; each lane finds the
+// segment that owns its position with a binary search over the segment starts
+// (shuffles).  Calls f(owner, entry index, neighbour id, step hit mask) per
+// position; returns per-owner results through the callback's side effects.
+//
+// Conflict search: for each owner j that is active, returns the conflicting
+// neighbour (or -1) of vertex v_j with tentative color c_j.
+template <bool kBatched>
+__device__ __forceinline__ int32_t warp_flat_conflict(const Params &p, bool slow, int32_t v,
+                                                      int c, int32_t dv, long long s, int len,
+                                                      int32_t vb, bool prefix,
+                                                      unsigned long long &scanned) {
+    const int lane = threadIdx.x & 31;
+    int incl = len;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) x[k] = q0 + k < q1 ? load4(p.ci, q0 + k, p.m) : make_int4(0, 0, 0, 0);
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int pre = incl - len;
+    const int total = __shfl_sync(kFull, incl, 31);
+    int32_t found = -1;
+    for (int p0 = 0; p0 < total; p0 += 32) {
+        const int pos = p0 + lane;
+        int lo = 0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const long long i = ((q0 + k) << 2) + j;
-                const int32_t w = vb + elem(x[k], j);
-                if (i >= s && i < e && (unsigned)w < (unsigned)p.n) atomicOr(plane + w, bit);
+        for (int step = 16; step > 0; step >>= 1) {
+            const int cand = lo + step;
+            if (__shfl_sync(kFull, pre, cand) <= pos) lo = cand;
+        }
+        const long long so = __shfl_sync(kFull, s, lo);
+        const int po = __shfl_sync(kFull, pre, lo);
+        const int32_t vo = __shfl_sync(kFull, v, lo), vbo = __shfl_sync(kFull, vb, lo);
+        const int co = __shfl_sync(kFull, c, lo), dvo = __shfl_sync(kFull, dv, lo);
+        bool hit = false;
+        int32_t w = -1;
+        if (pos < total) {
+            w = vbo + __ldg(p.ci + so + (pos - po));
+            bool ok = (unsigned)w < (unsigned)p.n && w != vo;
+            if (!prefix) {
+                if (p.rule == 0 && w > vo) ok = false;
+                if (p.rule == 1 && w < vo) ok = false;
             }
+            if (ok) {
+                scanned++;
+                const int cw = __ldcg(p.colors + w);
+                hit = mag(cw) == co && (prefix || loses_to<kBatched>(p, vo, w, dvo));
+            }
+        }
+        const unsigned hb = __ballot_sync(kFull, hit);
+        // this lane's segment within the step: positions [pre, pre + len) - p0
+        const int a0 = max(pre - p0, 0), a1 = min(pre + len - p0, 32);
+        unsigned mine = 0;
+        if (slow && a1 > a0) {
+            const unsigned hiMask = a1 >= 32 ? kFull : ((1u << a1) - 1u);
+            const unsigned loMask = (1u << a0) - 1u;
+            mine = hb & hiMask & ~loMask;
+        }
+        const int src = mine ? 31 - __clz(mine) : lane;  // highest entry: nearest lower neighbour
+        const int32_t wsrc = __shfl_sync(kFull, w, src);
+        if (mine && found < 0) found = wsrc;
+    }
+    return found;
+}
+
+// Warp-cooperative scatter: lane j (if keep) records color c_j in the bitmaps
+// of its whole row [s_j, e_j).
+__device__ __forceinline__ void warp_flat_scatter(const Params &p, bool keep, int c, long long s,
+                                                  long long e, int32_t vb) {
+    const int lane = threadIdx.x & 31;
+    const int len = keep && c <= 256 ? (int)(e - s) : 0;
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int pre = incl - len;
+    const int total = __shfl_sync(kFull, incl, 31);
+    for (int p0 = 0; p0 < total; p0 += 32) {
+        const int pos = p0 + lane;
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int cand = lo + step;
+            if (__shfl_sync(kFull, pre, cand) <= pos) lo = cand;
+        }
+        const long long so = __shfl_sync(kFull, s, lo);
+        const int po = __shfl_sync(kFull, pre, lo);
+        const int32_t vbo = __shfl_sync(kFull, vb, lo);
+        const int co = __shfl_sync(kFull, c, lo);
+        if (pos < total) {
+            const int32_t w = vbo + __ldg(p.ci + so + (pos - po));
+            if ((unsigned)w < (unsigned)p.n)
+                atomicOr(p.bm + (size_t)((co - 1) >> 5) * p.np + w, 1u << ((co - 1) & 31));
+        }
     }
 }
 
-// Resolve U light worklist vertices per lane (list positions idx[u]), the
-// independent loads of all U vertices issued stage by stage: entry, then
-// witness and own color, then the witness's color.  Vertices the witness does
-// not settle probe the 16-byte block of their nearest lower neighbour, then
-// scan the rest of the row if needed.  Losers come back in flag/item;
-// keepers are committed and scattered here.
+// Resolve U light worklist vertices per lane (list positions idx[u]).  Stage
+// by stage for all U vertices: entry, then witness and own color, then the
+// witness's color.  The vertices the witness does not settle are resolved by
+// the whole warp together (flattened scans of their lower neighbours), and
+// the keepers' rows are scattered the same way.  Losers come back in
+// flag/item.
 template <bool kBatched, int U>
 __device__ __forceinline__ void det_light_resolve(const Params &p, const int32_t *list,
                                                   unsigned cnt, const unsigned (&idx)[U],
@@ -512,80 +590,33 @@ __device__ __forceinline__ void det_light_resolve(const Params &p, const int32_t
         const int cw = wit[u] >= 0 ? __ldcg(p.colors + wit[u]) : 0;
         conf[u] = wit[u] >= 0 && mag(cw) == c[u];
     }
-    // slow path: vertices the witness does not settle
-    bool need[U];
-    long long s[U], e[U], hi[U];
-    int32_t vb[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        need[u] = act[u] && !conf[u];
-        s[u] = e[u] = 0;
-        vb[u] = 0;
-        hi[u] = -1;
-        if (need[u]) {
-            row_of<kBatched>(p, v[u], s[u], e[u], vb[u]);
-            if (prefix) hi[u] = s[u] + __ldcg(p.lowdeg + v[u]);
-        }
-    }
-    if (prefix) {  // first probe: the 16-byte block of the nearest lower neighbour
-        int4 x[U];
-        long long q[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            q[u] = (hi[u] - 1) >> 2;
-            x[u] = need[u] && hi[u] > s[u] ? load4(p.ci, q[u], p.m) : make_int4(0, 0, 0, 0);
-        }
-        int cw[U][4];
-        bool ok[U][4];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const long long i = (q[u] << 2) + k;
-                const int32_t w = vb[u] + elem(x[u], k);
-                ok[u][k] = need[u] && i >= s[u] && i < hi[u] && (unsigned)w < (unsigned)p.n;
-                cw[u][k] = ok[u][k] ? __ldcg(p.colors + w) : 0;
-            }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            int32_t found = -1;
-#pragma unroll
-            for (int k = 3; k >= 0; --k)
-                if (ok[u][k]) {
-                    acc.dscan++;
-                    if (found < 0 && mag(cw[u][k]) == c[u]) found = vb[u] + elem(x[u], k);
-                }
-            if (need[u] && found < 0 && q[u] > (s[u] >> 2))  // rest of the lower prefix
-                found = det_scan_lane<kBatched>(p, v[u], c[u], (int32_t)(e[u] - s[u]), s[u], e[u],
-                                                vb[u], q[u] << 2, acc.dscan);
-            if (found >= 0) {
-                conf[u] = true;
-                __stcg(p.witness + v[u], found);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (need[u]) {
-                const int32_t found = det_scan_lane<kBatched>(p, v[u], c[u], (int32_t)(e[u] - s[u]),
-                                                              s[u], e[u], vb[u], -1, acc.dscan);
-                if (found >= 0) {
-                    conf[u] = true;
-                    __stcg(p.witness + v[u], found);
-                }
-            }
-    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         flag[u] = act[u] && conf[u];
         item[u] = v[u];
-        if (act[u] && !conf[u]) {
+        const bool slow = act[u] && !conf[u];
+        if (!__any_sync(kFull, slow)) continue;
+        long long s = 0, e = 0;
+        int32_t vb = 0;
+        int len = 0;
+        if (slow) {
+            row_of<kBatched>(p, v[u], s, e, vb);
+            len = prefix ? __ldcg(p.lowdeg + v[u]) : (int)(e - s);
+        }
+        const int32_t found = warp_flat_conflict<kBatched>(p, slow, v[u], c[u], (int32_t)(e - s), s,
+                                                           len, vb, prefix, acc.dscan);
+        const bool keep = slow && found < 0;
+        if (slow && found >= 0) {
+            flag[u] = true;
+            __stcg(p.witness + v[u], found);
+        }
+        if (keep) {
             __stcg(p.colors + v[u], c[u]);
             acc.kmax = max(acc.kmax, c[u]);
-            acc.kdeg += (unsigned long long)(e[u] - s[u]);
-            acc.scatter += (unsigned long long)(e[u] - s[u]);
-            scatter_light(p, c[u], s[u], e[u], vb[u]);
+            acc.kdeg += (unsigned long long)(e - s);
+            acc.scatter += (unsigned long long)(e - s);
         }
+        if (__any_sync(kFull, keep)) warp_flat_scatter(p, keep, c[u], s, e, vb);
     }
 }
 
