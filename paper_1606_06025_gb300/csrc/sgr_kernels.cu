@@ -562,24 +562,76 @@ __device__ __forceinline__ void warp_flat_scatter(const Params &p, bool keep, in
     }
 }
 
-// Resolve U light worklist vertices per lane (list positions idx[u]).  Stage
-// by stage for all U vertices: entry, then witness and own color, then the
-// witness's color.  The vertices the witness does not settle are resolved by
-// the whole warp together (flattened scans of their lower neighbours), and
-// the keepers' rows are scattered the same way.  Losers come back in
-// flag/item.
+// Resolve the slow vertices held one per lane (slow: the witness did not
+// settle it): the warp scans their lower neighbours together, losers get a
+// new witness, keepers commit and scatter their color.  Returns true for a
+// loser.
+template <bool kBatched>
+__device__ __forceinline__ bool det_resolve_slow(const Params &p, bool slow, int32_t v, int c,
+                                                 bool prefix, Acc &acc) {
+    long long s = 0, e = 0;
+    int32_t vb = 0;
+    int len = 0;
+    if (slow) {
+        row_of<kBatched>(p, v, s, e, vb);
+        len = prefix ? __ldcg(p.lowdeg + v) : (int)(e - s);
+    }
+    const int32_t found = warp_flat_conflict<kBatched>(p, slow, v, c, (int32_t)(e - s), s, len, vb,
+                                                       prefix, acc.dscan);
+    const bool keep = slow && found < 0;
+    if (slow && found >= 0) __stcg(p.witness + v, found);
+    if (keep) {
+        __stcg(p.colors + v, c);
+        acc.kmax = max(acc.kmax, c);
+        acc.kdeg += (unsigned long long)(e - s);
+        acc.scatter += (unsigned long long)(e - s);
+    }
+    if (__any_sync(kFull, keep)) warp_flat_scatter(p, keep, c, s, e, vb);
+    return slow && found >= 0;
+}
+
+// Fast path for U light worklist vertices per lane (list positions idx[u]),
+// stage by stage for all U: entry, then witness and own color, then the
+// witness's color.  In round 1 with ascending rows and the low-keeps rule
+// every tentative color is 1, so v loses iff it has a lower neighbour, and
+// its nearest lower neighbour becomes its witness.  flag: settled loser;
+// slow: not settled here (v and c returned for the slow path).
 template <bool kBatched, int U>
-__device__ __forceinline__ void det_light_resolve(const Params &p, const int32_t *list,
-                                                  unsigned cnt, const unsigned (&idx)[U],
-                                                  bool prefix, bool (&flag)[U],
-                                                  int32_t (&item)[U], Acc &acc) {
-    int32_t v[U], wit[U], c[U];
-    bool act[U], conf[U];
+__device__ __forceinline__ void det_light_fast(const Params &p, const int32_t *list, unsigned cnt,
+                                               const unsigned (&idx)[U], bool prefix, bool round1,
+                                               bool (&flag)[U], bool (&slow)[U],
+                                               int32_t (&v)[U], int32_t (&c)[U]) {
+    bool act[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         act[u] = idx[u] < cnt;
         v[u] = act[u] ? __ldcg(list + idx[u]) : 0;
     }
+    if (round1 && prefix) {
+        int ld[U];
+        long long s[U];
+        int32_t vb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ld[u] = 0;
+            s[u] = 0;
+            vb[u] = 0;
+            c[u] = 1;
+            if (act[u]) {
+                long long e;
+                row_of<kBatched>(p, v[u], s[u], e, vb[u]);
+                ld[u] = __ldcg(p.lowdeg + v[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            flag[u] = act[u] && ld[u] > 0;
+            slow[u] = act[u] && ld[u] == 0;
+            if (flag[u]) __stcg(p.witness + v[u], vb[u] + __ldg(p.ci + s[u] + ld[u] - 1));
+        }
+        return;
+    }
+    int32_t wit[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         wit[u] = act[u] ? __ldcg(p.witness + v[u]) : -1;
@@ -588,62 +640,75 @@ __device__ __forceinline__ void det_light_resolve(const Params &p, const int32_t
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int cw = wit[u] >= 0 ? __ldcg(p.colors + wit[u]) : 0;
-        conf[u] = wit[u] >= 0 && mag(cw) == c[u];
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        flag[u] = act[u] && conf[u];
-        item[u] = v[u];
-        const bool slow = act[u] && !conf[u];
-        if (!__any_sync(kFull, slow)) continue;
-        long long s = 0, e = 0;
-        int32_t vb = 0;
-        int len = 0;
-        if (slow) {
-            row_of<kBatched>(p, v[u], s, e, vb);
-            len = prefix ? __ldcg(p.lowdeg + v[u]) : (int)(e - s);
-        }
-        const int32_t found = warp_flat_conflict<kBatched>(p, slow, v[u], c[u], (int32_t)(e - s), s,
-                                                           len, vb, prefix, acc.dscan);
-        const bool keep = slow && found < 0;
-        if (slow && found >= 0) {
-            flag[u] = true;
-            __stcg(p.witness + v[u], found);
-        }
-        if (keep) {
-            __stcg(p.colors + v[u], c[u]);
-            acc.kmax = max(acc.kmax, c[u]);
-            acc.kdeg += (unsigned long long)(e - s);
-            acc.scatter += (unsigned long long)(e - s);
-        }
-        if (__any_sync(kFull, keep)) warp_flat_scatter(p, keep, c[u], s, e, vb);
+        flag[u] = act[u] && wit[u] >= 0 && mag(cw) == c[u];
+        slow[u] = act[u] && !flag[u];
     }
 }
 
 template <bool kBatched>
 __device__ void det_light_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
-                                 unsigned *out_cnt, bool prefix, Acc &acc) {
+                                 unsigned *out_cnt, bool prefix, bool round1, Acc &acc) {
     if (cnt < 2u * gridDim.x * kLightTile) {
         // short worklist: 32 entries per warp, spread over every warp of the grid
         const unsigned NW = total_warps();
         for (unsigned base = global_warp() * 32; base < cnt; base += NW * 32) {
             const unsigned idx[1] = {base + (threadIdx.x & 31)};
-            bool flag[1];
-            int32_t item[1];
-            det_light_resolve<kBatched, 1>(p, list, cnt, idx, prefix, flag, item, acc);
-            warp_push(flag[0], item[0], out_cnt, out, acc.next);
+            bool flag[1], slow[1];
+            int32_t v[1], c[1];
+            det_light_fast<kBatched, 1>(p, list, cnt, idx, prefix, round1, flag, slow, v, c);
+            bool lost = flag[0];
+            if (__any_sync(kFull, slow[0]))
+                lost = det_resolve_slow<kBatched>(p, slow[0], v[0], c[0], prefix, acc) || lost;
+            warp_push(lost, v[0], out_cnt, out, acc.next);
         }
         return;
     }
+    // long worklist: CTA tiles; the vertices the witness does not settle are
+    // queued in shared memory and resolved by all warps of the CTA together.
+    __shared__ int32_t s_sv[kSlowCap], s_sc[kSlowCap];
+    __shared__ unsigned s_sn;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_sn = 0;
+    __syncthreads();
     const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
-    for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
-        bool flag[kLightUnroll];
-        int32_t item[kLightUnroll];
-        unsigned idx[kLightUnroll];
+    for (unsigned t = blockIdx.x;; t += gridDim.x) {
+        const bool more = t < tiles;
+        if (more) {
+            bool flag[kLightUnroll], slow[kLightUnroll];
+            int32_t v[kLightUnroll], c[kLightUnroll];
+            unsigned idx[kLightUnroll];
 #pragma unroll
-        for (int u = 0; u < kLightUnroll; ++u) idx[u] = tile_index(t, u);
-        det_light_resolve<kBatched, kLightUnroll>(p, list, cnt, idx, prefix, flag, item, acc);
-        block_push(flag, item, out_cnt, out, acc.next);
+            for (int u = 0; u < kLightUnroll; ++u) idx[u] = tile_index(t, u);
+            det_light_fast<kBatched, kLightUnroll>(p, list, cnt, idx, prefix, round1, flag, slow, v, c);
+#pragma unroll
+            for (int u = 0; u < kLightUnroll; ++u) {
+                const unsigned bal = __ballot_sync(kFull, slow[u]);
+                if (!bal) continue;
+                unsigned pos = 0;
+                if (lane == 0) pos = atomicAdd(&s_sn, (unsigned)__popc(bal));
+                pos = __shfl_sync(kFull, pos, 0) + __popc(bal & lanemask_lt());
+                if (slow[u]) {
+                    s_sv[pos] = v[u];
+                    s_sc[pos] = c[u];
+                }
+            }
+            block_push(flag, v, out_cnt, out, acc.next);
+        }
+        __syncthreads();
+        const unsigned nslow = s_sn;
+        if (nslow > kSlowCap - kLightTile || (!more && nslow > 0)) {  // drain the queue
+            for (unsigned g = warp * 32; g < nslow; g += kWarps * 32) {
+                const bool sl = g + lane < nslow;
+                const int32_t v = sl ? s_sv[g + lane] : 0;
+                const int c = sl ? s_sc[g + lane] : 0;
+                const bool lost = det_resolve_slow<kBatched>(p, sl, v, c, prefix, acc);
+                warp_push(lost, v, out_cnt, out, acc.next);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_sn = 0;
+            __syncthreads();
+        }
+        if (!more) break;
     }
 }
 
@@ -1410,7 +1475,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
         } else {
             det_hub_detect<kBatched>(p, par, h64, prefix, b);
             det_medium_detect<kBatched>(p, p.mw[par], nm, p.mw[pn], &ctr->nm[pn], prefix, b);
-            det_light_detect<kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix, b);
+            det_light_detect<kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix, r == 1, b);
         }
         acc.w += b.w;
         acc.d += b.d;
