@@ -296,10 +296,10 @@ def run_ours(args, rank, world, local):
     ci_h = torch.from_numpy(g.col_idx).pin_memory().numpy()
     col_h = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
     if args.timeline and rank == 0:
-        tw, ta, tb, tinit = lib.sgr_last_trace()
+        tl = lib.sgr_last_trace()
         with open(args.timeline, "w") as f:
-            json.dump({"workload": args.workload, "mode": mode, "init_ns": tinit,
-                       "w": tw.tolist(), "end_a_ns": ta.tolist(), "end_b_ns": tb.tolist()}, f)
+            json.dump({"workload": args.workload, "mode": mode, "init_ns": tl["init_ns"],
+                       **{k: v.tolist() for k, v in tl.items() if k != "init_ns"}}, f)
     e2e_ms = []
     for i in range(0 if args.no_e2e else args.warmup + args.steps):
         flush.fill_(1)

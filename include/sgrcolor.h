@@ -168,10 +168,11 @@ int sgr_last_stats(sgr_stats *out);
 
 /*
  * Device timeline of the last coloring launch on the current device: for
- * round r (0-based, at most cap_rounds and 65536 rounds) out[3r] = |W_r|,
- * out[3r+1] / out[3r+2] = nanoseconds from kernel start to the end of the
+ * round r (0-based, at most cap_rounds and 65536 rounds) out[4r] = |W_r|,
+ * out[4r+1] / out[4r+2] = nanoseconds from kernel start to the end of the
  * FirstFit / ConflictResolve phase (read from %globaltimer by CTA 0 after each
- * grid barrier).  *init_ns (HOST, may be NULL) receives the end of the
+ * grid barrier), out[4r+3] = worklist vertices whose ConflictResolve had to
+ * scan their row in that round (deterministic mode; 0 in fast mode).  *init_ns (HOST, may be NULL) receives the end of the
  * initial binning pass.  Returns the number of rounds written (>= 0) or a
  * negative status.  Valid until the next call on the device.  out is HOST.
  */

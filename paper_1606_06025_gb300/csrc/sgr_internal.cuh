@@ -34,7 +34,7 @@ constexpr int kSlowCap = 2 * kLightTile;          // det: queued slow vertices p
 constexpr int kMinBlocks = 3;                    // CTAs per SM the register budget targets
 constexpr int kLightMaxStage = 32;               // largest light degree (staged rows per lane)
 constexpr int kTraceCap = 1 << 16;               // rounds recorded in the timeline
-constexpr int kTraceFields = 3;                  // |W_r|, ns at end of phase A, ns at end of phase B
+constexpr int kTraceFields = 4;                  // |W_r|, ns at end of phase A / phase B, rescans
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;  // bounded device waits
 
 // status codes mirrored from sgrcolor.h (device code cannot include it twice)
@@ -56,9 +56,9 @@ struct Counters {
     unsigned long long sum_w, sum_d, sum_dscan, sum_next, sum_scatter;
     unsigned long long sc64;        // hub scatter list: (entries << 32) | total chunks
     unsigned long long dcur;        // det: degree sum of the current worklist
+    unsigned long long nslow;       // det: worklist vertices that rescanned their row this round
     long long rounds;
     long long t_init_ns;            // globaltimer: end of the init pass (after its barrier)
-    long long pad[1];
 };
 
 struct Params {

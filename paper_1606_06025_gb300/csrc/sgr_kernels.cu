@@ -153,6 +153,7 @@ __device__ __forceinline__ bool loses_to(const Params &p, int32_t v, int32_t w, 
 struct Acc {
     unsigned long long w = 0, d = 0, dscan = 0, next = 0, scatter = 0;
     unsigned long long kdeg = 0;  // det: degree sum of this phase's keepers
+    unsigned long long slow = 0;  // det: vertices that rescanned their row
     int kmax = 0;
 };
 
@@ -573,6 +574,7 @@ __device__ __forceinline__ bool det_resolve_slow(const Params &p, bool slow, int
     int32_t vb = 0;
     int len = 0;
     if (slow) {
+        acc.slow++;
         row_of<kBatched>(p, v, s, e, vb);
         len = prefix ? __ldcg(p.lowdeg + v) : (int)(e - s);
     }
@@ -1366,28 +1368,33 @@ __device__ void init_phase(const Params &p) {
 
 // End of phase B: the CTA's largest committed color and (det) the degree sum
 // of its keepers, which leave the worklist.
-__device__ void flush_phase(const Params &p, int kloc, unsigned long long kdeg) {
+__device__ void flush_phase(const Params &p, int kloc, unsigned long long kdeg,
+                            unsigned long long nslow) {
     __shared__ int s_k[kWarps];
-    __shared__ unsigned long long s_d[kWarps];
+    __shared__ unsigned long long s_d[kWarps], s_s[kWarps];
     int k = kloc;
     for (int o = 16; o > 0; o >>= 1) {
         k = max(k, __shfl_xor_sync(kFull, k, o));
         kdeg += __shfl_xor_sync(kFull, kdeg, o);
+        nslow += __shfl_xor_sync(kFull, nslow, o);
     }
     if ((threadIdx.x & 31) == 0) {
         s_k[threadIdx.x >> 5] = k;
         s_d[threadIdx.x >> 5] = kdeg;
+        s_s[threadIdx.x >> 5] = nslow;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         int b = 0;
-        unsigned long long d = 0;
+        unsigned long long d = 0, sl = 0;
         for (int w = 0; w < kWarps; ++w) {
             b = max(b, s_k[w]);
             d += s_d[w];
+            sl += s_s[w];
         }
         if (b > 0 && b > *(volatile int *)&p.ctr->kmax) atomicMax(&p.ctr->kmax, b);
         if (d) atomicAdd(&p.ctr->dcur, 0ull - d);
+        if (sl) atomicAdd(&p.ctr->nslow, sl);
     }
 }
 
@@ -1482,10 +1489,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
         acc.dscan += b.dscan;
         acc.next += b.next;
         acc.scatter += b.scatter;
-        flush_phase(p, b.kmax, b.kdeg);
+        flush_phase(p, b.kmax, b.kdeg, b.slow);
         if (!(ok = grid_barrier(p, gen))) break;
-        if (recorder && r <= kTraceCap)
+        if (recorder && r <= kTraceCap) {
             p.trace[kTraceFields * (r - 1) + 2] = (long long)(globaltimer() - t0);
+            p.trace[kTraceFields * (r - 1) + 3] = (long long)__ldcg(&ctr->nslow);
+            ctr->nslow = 0;
+        }
     }
     if (recorder && ok) ctr->rounds = r - 1;
     flush_stats(p, acc);

@@ -179,16 +179,18 @@ def sgr_last_stats() -> dict:
 
 
 def sgr_last_trace(cap_rounds: int = 1 << 16):
-    """Per-round timeline of the last launch: (W sizes, ns at end of phase A,
-    ns at end of phase B, ns at end of the init pass) as numpy arrays."""
+    """Per-round timeline of the last launch: dict of numpy arrays (w: |W_r|,
+    end_a_ns / end_b_ns: ns at the end of each phase, rescans: vertices that
+    scanned their row) and init_ns."""
     import numpy as np
-    buf = np.zeros(3 * cap_rounds, dtype=np.int64)
+    buf = np.zeros(4 * cap_rounds, dtype=np.int64)
     init = ctypes.c_int64(0)
     r = _lib.sgr_last_trace(buf.ctypes.data, cap_rounds, ctypes.byref(init))
     if r < 0:
         raise SgrError(r, "sgr_last_trace")
-    t = buf[:3 * r].reshape(r, 3)
-    return t[:, 0].copy(), t[:, 1].copy(), t[:, 2].copy(), int(init.value)
+    t = buf[:4 * r].reshape(r, 4)
+    return {"w": t[:, 0].copy(), "end_a_ns": t[:, 1].copy(), "end_b_ns": t[:, 2].copy(),
+            "rescans": t[:, 3].copy(), "init_ns": int(init.value)}
 
 
 def sgr_get_tuning() -> dict:
