@@ -462,134 +462,85 @@ __device__ __forceinline__ void scatter_color(const Params &p, int c, long long 
     }
 }
 
-// Warp-cooperative pass over one "segment" per lane: lane j owns entries
-// [s_j, s_j + len_j) of col_idx (len_j may be 0).  The segments are laid end
-// to end and the warp walks them 32 entries at a time; each lane finds the
-// segment that owns its position with a binary search over the segment starts
-// (shuffles).  Calls f(owner, entry index, neighbour id, step hit mask) per
-// position; returns per-owner results through the callback's side effects.
-//
-// Conflict search: for each owner j that is active, returns the conflicting
-// neighbour (or -1) of vertex v_j with tentative color c_j.
-template <bool kBatched>
-__device__ __forceinline__ int32_t warp_flat_conflict(const Params &p, bool slow, int32_t v,
-                                                      int c, int32_t dv, long long s, int len,
-                                                      int32_t vb, bool prefix,
-                                                      unsigned long long &scanned) {
-    const int lane = threadIdx.x & 31;
-    int incl = len;
+// Backward scan of entries [s, hi) of v's ascending row (all below v), three
+// 16-byte blocks at a time with every load of a batch in flight before the
+// checks; returns the nearest neighbour holding magnitude c, or -1.
+__device__ __forceinline__ int32_t scan_below(const Params &p, int c, long long s, long long hi,
+                                              int32_t vb, unsigned long long &scanned) {
+    for (long long qt = (hi - 1) >> 2; hi > s && qt >= (s >> 2); qt -= 3) {
+        int4 x[3];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int pre = incl - len;
-    const int total = __shfl_sync(kFull, incl, 31);
-    int32_t found = -1;
-    for (int p0 = 0; p0 < total; p0 += 32) {
-        const int pos = p0 + lane;
-        int lo = 0;
+        for (int k = 0; k < 3; ++k)
+            x[k] = qt - k >= (s >> 2) ? load4(p.ci, qt - k, p.m) : make_int4(0, 0, 0, 0);
+        int cw[3][4];
+        bool ok[3][4];
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int cand = lo + step;
-            if (__shfl_sync(kFull, pre, cand) <= pos) lo = cand;
-        }
-        const long long so = __shfl_sync(kFull, s, lo);
-        const int po = __shfl_sync(kFull, pre, lo);
-        const int32_t vo = __shfl_sync(kFull, v, lo), vbo = __shfl_sync(kFull, vb, lo);
-        const int co = __shfl_sync(kFull, c, lo), dvo = __shfl_sync(kFull, dv, lo);
-        bool hit = false;
-        int32_t w = -1;
-        if (pos < total) {
-            w = vbo + __ldg(p.ci + so + (pos - po));
-            bool ok = (unsigned)w < (unsigned)p.n && w != vo;
-            if (!prefix) {
-                if (p.rule == 0 && w > vo) ok = false;
-                if (p.rule == 1 && w < vo) ok = false;
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long i = ((qt - k) << 2) + j;
+                const int32_t w = vb + elem(x[k], j);
+                ok[k][j] = qt - k >= (s >> 2) && i >= s && i < hi && (unsigned)w < (unsigned)p.n;
+                cw[k][j] = ok[k][j] ? __ldcg(p.colors + w) : 0;
             }
-            if (ok) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 3; j >= 0; --j) {
+                if (!ok[k][j]) continue;
                 scanned++;
-                const int cw = __ldcg(p.colors + w);
-                hit = mag(cw) == co && (prefix || loses_to<kBatched>(p, vo, w, dvo));
+                if (mag(cw[k][j]) == c) return vb + elem(x[k], j);
             }
-        }
-        const unsigned hb = __ballot_sync(kFull, hit);
-        // this lane's segment within the step: positions [pre, pre + len) - p0
-        const int a0 = max(pre - p0, 0), a1 = min(pre + len - p0, 32);
-        unsigned mine = 0;
-        if (slow && a1 > a0) {
-            const unsigned hiMask = a1 >= 32 ? kFull : ((1u << a1) - 1u);
-            const unsigned loMask = (1u << a0) - 1u;
-            mine = hb & hiMask & ~loMask;
-        }
-        const int src = mine ? 31 - __clz(mine) : lane;  // highest entry: nearest lower neighbour
-        const int32_t wsrc = __shfl_sync(kFull, w, src);
-        if (mine && found < 0) found = wsrc;
     }
-    return found;
+    return -1;
 }
 
-// Warp-cooperative scatter: lane j (if keep) records color c_j in the bitmaps
-// of its whole row [s_j, e_j).
-__device__ __forceinline__ void warp_flat_scatter(const Params &p, bool keep, int c, long long s,
-                                                  long long e, int32_t vb) {
-    const int lane = threadIdx.x & 31;
-    const int len = keep && c <= 256 ? (int)(e - s) : 0;
-    int incl = len;
+// Record color c in the bitmaps of the neighbours [s, e) (one lane; three
+// 16-byte blocks loaded per batch).
+__device__ __forceinline__ void scatter_lane(const Params &p, int c, long long s, long long e,
+                                             int32_t vb) {
+    if (c > 256 || e <= s) return;
+    unsigned *plane = p.bm + (size_t)((c - 1) >> 5) * p.np;
+    const unsigned bit = 1u << ((c - 1) & 31);
+    const long long q1 = (e + 3) >> 2;
+    for (long long q0 = s >> 2; q0 < q1; q0 += 3) {
+        int4 x[3];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int pre = incl - len;
-    const int total = __shfl_sync(kFull, incl, 31);
-    for (int p0 = 0; p0 < total; p0 += 32) {
-        const int pos = p0 + lane;
-        int lo = 0;
+        for (int k = 0; k < 3; ++k) x[k] = q0 + k < q1 ? load4(p.ci, q0 + k, p.m) : make_int4(0, 0, 0, 0);
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int cand = lo + step;
-            if (__shfl_sync(kFull, pre, cand) <= pos) lo = cand;
-        }
-        const long long so = __shfl_sync(kFull, s, lo);
-        const int po = __shfl_sync(kFull, pre, lo);
-        const int32_t vbo = __shfl_sync(kFull, vb, lo);
-        const int co = __shfl_sync(kFull, c, lo);
-        if (pos < total) {
-            const int32_t w = vbo + __ldg(p.ci + so + (pos - po));
-            if ((unsigned)w < (unsigned)p.n)
-                atomicOr(p.bm + (size_t)((co - 1) >> 5) * p.np + w, 1u << ((co - 1) & 31));
-        }
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long i = ((q0 + k) << 2) + j;
+                const int32_t w = vb + elem(x[k], j);
+                if (i >= s && i < e && (unsigned)w < (unsigned)p.n) atomicOr(plane + w, bit);
+            }
     }
 }
 
-// Resolve the slow vertices held one per lane (slow: the witness did not
-// settle it): the warp scans their lower neighbours together, losers get a
-// new witness, keepers commit and scatter their color.  Returns true for a
-// loser.
+// Resolve a vertex the witness did not settle (one lane): scan its row,
+// record a new witness or commit and scatter.  Returns true for a loser.
 template <bool kBatched>
 __device__ __forceinline__ bool det_resolve_slow(const Params &p, bool slow, int32_t v, int c,
                                                  bool prefix, Acc &acc) {
-    long long s = 0, e = 0;
-    int32_t vb = 0;
-    int len = 0;
-    if (slow) {
-        acc.slow++;
-        row_of<kBatched>(p, v, s, e, vb);
-        len = prefix ? __ldcg(p.lowdeg + v) : (int)(e - s);
+    if (!slow) return false;
+    acc.slow++;
+    long long s, e;
+    int32_t vb;
+    row_of<kBatched>(p, v, s, e, vb);
+    const int32_t found =
+        prefix ? scan_below(p, c, s, s + __ldcg(p.lowdeg + v), vb, acc.dscan)
+               : det_scan_lane<kBatched>(p, v, c, (int32_t)(e - s), s, e, vb, -1, acc.dscan);
+    if (found >= 0) {
+        __stcg(p.witness + v, found);
+        return true;
     }
-    const int32_t found = warp_flat_conflict<kBatched>(p, slow, v, c, (int32_t)(e - s), s, len, vb,
-                                                       prefix, acc.dscan);
-    const bool keep = slow && found < 0;
-    if (slow && found >= 0) __stcg(p.witness + v, found);
-    if (keep) {
-        __stcg(p.colors + v, c);
-        acc.kmax = max(acc.kmax, c);
-        acc.kdeg += (unsigned long long)(e - s);
-        acc.scatter += (unsigned long long)(e - s);
-    }
-    if (__any_sync(kFull, keep)) warp_flat_scatter(p, keep, c, s, e, vb);
-    return slow && found >= 0;
+    __stcg(p.colors + v, c);
+    acc.kmax = max(acc.kmax, c);
+    acc.kdeg += (unsigned long long)(e - s);
+    acc.scatter += (unsigned long long)(e - s);
+    scatter_lane(p, c, s, e, vb);
+    return false;
 }
 
 // Fast path for U light worklist vertices per lane (list positions idx[u]),
