@@ -127,6 +127,32 @@ int sgr_color(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
               int32_t *colors_out, int32_t *num_colors, int mode, sgr_stream_t stream);
 
 /*
+ * sgr_color without any allocation by the library.  The paper has no
+ * counterpart: this entry point exists for callers that must not let a
+ * library allocate device memory -- an application that gives this code a
+ * fixed share of the GPU and routes every allocation through its own pool, or
+ * a latency-sensitive loop in which cudaMalloc / cudaFree would synchronise
+ * the device and stall other streams.
+ *   Arguments, layout, modes and results are those of sgr_color (device
+ *   buffers owned by the caller, colors 1..k, k on the host).
+ *   Scratch: a fixed 16 MiB array inside the library's device image, held by
+ *   every GPU that loads the library until the process exits (enough for
+ *   graphs of about 200,000 vertices and a few million entries).  A graph
+ *   whose scratch does not fit is refused with SGR_ERR_INVALID_ARG before any
+ *   device work.
+ *   The first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents; each call
+ *   clears what must start at zero.  Calls whose GPU work overlaps would race
+ *   on the array; within one process calls on a device are serialised and
+ *   each returns after its work is complete.
+ *   The call makes no cudaMalloc, cudaFree or other allocating call.
+ *   sgr_last_stats reports device_ms = 0 for it.
+ */
+int sgr_color_noalloc(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
+                      int32_t *colors_out, int32_t *num_colors, int mode, sgr_stream_t stream);
+
+/*
  * Same as sgr_color with HOST buffers: copies the CSR to library-owned device
  * memory on `stream`, colors it and copies the colors back.  Pinned host
  * memory makes the copies faster but is not required.

@@ -566,3 +566,99 @@ int sgr_validate_csr(int32_t n, const int32_t *row_offsets, const int32_t *col_i
 
 }  // extern "C"
 
+
+// ---------------------------------------------------------------------------
+// Coloring without any allocation by the library (no counterpart in the
+// paper).
+//
+// Some callers must not let a library allocate device memory: an application
+// that gives a plugin a fixed share of the GPU and routes every allocation
+// through its own pool, or a latency-sensitive loop in which a cudaMalloc or
+// cudaFree would synchronise the device and stall work on other streams.  For
+// them sgr_color_noalloc runs the same coloring kernel with its scratch in
+// g_noalloc_scratch, a fixed-size array that is part of this library's device
+// image: every GPU that loads the library holds it until the process exits.
+// The caller still owns and passes the graph and the colors buffer.
+//
+// In host code the name g_noalloc_scratch only stands for the array; its
+// device address comes from cudaGetSymbolAddress, taken once per device (with
+// that device current) by the first sgr_color_noalloc call on the device.
+// Every call shares the one array and leaves the last call's contents in it;
+// the call clears what must start at zero.  Two calls whose GPU work
+// overlapped would race on it; within one process the calls on a device are
+// serialised and each returns only after its work is done.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu[kNoAllocMaxDevices];
+char *g_noalloc_ptr[kNoAllocMaxDevices];
+
+}  // namespace
+
+extern "C" int sgr_color_noalloc(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
+                                 int32_t *colors_out, int32_t *num_colors, int mode,
+                                 sgr_stream_t stream) {
+    std::memset(&t_stats, 0, sizeof(t_stats));
+    if (n < 0 || !num_colors || !valid_mode(mode)) return SGR_ERR_INVALID_ARG;
+    if (n == 0) {
+        *num_colors = 0;
+        return SGR_OK;
+    }
+    if (!row_offsets || !col_idx || !colors_out) return SGR_ERR_INVALID_ARG;
+    if (!is_device_ptr(row_offsets) || !is_device_ptr(colors_out)) return SGR_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return SGR_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu[dev]);
+    if (!g_noalloc_ptr[dev]) {  // set-up, once per device, with that device current
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return SGR_ERR_CUDA;
+        g_noalloc_ptr[dev] = (char *)ptr;
+    }
+    char *base = g_noalloc_ptr[dev];
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t ends[2] = {0, 0};  // pageable: the copies complete before the synchronisation returns
+    cudaError_t e = cudaMemcpyAsync(&ends[0], row_offsets, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], row_offsets + n, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return map_cuda(e);
+    const int32_t m = ends[1];
+    if (ends[0] != 0 || m < 0) return SGR_ERR_INVALID_GRAPH;
+    if (m > 0 && (((uintptr_t)col_idx & 15) != 0 || !is_device_ptr(col_idx))) return SGR_ERR_INVALID_ARG;
+    const sgr_tuning t = current_tuning();
+    const bool fast = (mode & SGR_MODE_MASK) == SGR_MODE_FAST;
+    Job j;
+    std::memset(&j, 0, sizeof(j));
+    j.fast = fast;
+    j.n = n;
+    j.m = m;
+    j.ro = row_offsets;
+    j.ci = col_idx;
+    j.colors = colors_out;
+    size_t zero_bytes = 0;
+    if (layout(j, t, nullptr, nullptr, &zero_bytes) > kNoAllocScratchBytes)
+        return SGR_ERR_INVALID_ARG;  // the graph needs more scratch than the fixed array holds
+    Params p;
+    layout(j, t, base, &p, nullptr);
+    p.rule = (mode & SGR_RULE_MASK) >> 4;
+    p.max_rounds = (long long)n + 1;
+    int per_sm = 0, sms = 0;
+    if (sgr::occupancy_blocks_per_sm(fast, false, &per_sm) != 0) return SGR_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SGR_ERR_CUDA;
+    if (t.blocks_per_sm > 0) per_sm = std::min(per_sm, t.blocks_per_sm);
+    if (per_sm < 1) return SGR_ERR_CUDA;
+    const int grid = per_sm * sms;
+    p.nblocks = (unsigned)grid;
+    if ((e = cudaMemsetAsync(base, 0, zero_bytes, st)) != cudaSuccess) return map_cuda(e);
+    if ((e = sgr::launch_color(p, fast, false, grid, st)) != cudaSuccess) return map_cuda(e);
+    Counters h;
+    if ((e = cudaMemcpyAsync(&h, p.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);
+    fill_stats(h, 0.f, grid, h.kmax);
+    if (h.err != 0) return h.err;
+    *num_colors = h.kmax;
+    return SGR_OK;
+}

@@ -36,7 +36,7 @@ RULES = {"low_keeps": SGR_RULE_LOW_KEEPS, "low_loses": SGR_RULE_LOW_LOSES,
          "degree": SGR_RULE_DEGREE}
 
 # every symbol include/sgrcolor.h declares (checked by the tests)
-EXPORTS = ["sgr_color", "sgr_color_host", "sgr_color_batch", "sgr_validate_csr",
+EXPORTS = ["sgr_color", "sgr_color_noalloc", "sgr_color_host", "sgr_color_batch", "sgr_validate_csr",
            "sgr_last_stats", "sgr_last_trace", "sgr_get_tuning", "sgr_set_tuning", "sgr_release_scratch",
            "sgr_status_string", "sgr_version"]
 
@@ -71,6 +71,7 @@ def _load():
     pi32 = ctypes.POINTER(ctypes.c_int32)
     lib.sgr_color.argtypes = [i32, vp, vp, vp, pi32, ctypes.c_int, vp]
     lib.sgr_color_host.argtypes = [i32, vp, vp, vp, pi32, ctypes.c_int, vp]
+    lib.sgr_color_noalloc.argtypes = [i32, vp, vp, vp, pi32, ctypes.c_int, vp]
     lib.sgr_color_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
     lib.sgr_validate_csr.argtypes = [i32, vp, vp, pi32, vp]
     lib.sgr_last_stats.argtypes = [ctypes.POINTER(Stats)]
@@ -143,6 +144,16 @@ def sgr_color(n, row_offsets, col_idx, colors_out, mode=0, stream=None) -> int:
     k = ctypes.c_int32(0)
     _check(_lib.sgr_color(int(n), _addr(row_offsets), _addr(col_idx), _addr(colors_out),
                           ctypes.byref(k), _mode(mode), _stream(stream)), "sgr_color")
+    return int(k.value)
+
+
+def sgr_color_noalloc(n, row_offsets, col_idx, colors_out, mode=0, stream=None) -> int:
+    """sgr_color for callers that must not let the library allocate device
+    memory: scratch comes from a fixed 16 MiB array in the library's device
+    image.  Graphs too large for it raise SgrError(SGR_ERR_INVALID_ARG)."""
+    k = ctypes.c_int32(0)
+    _check(_lib.sgr_color_noalloc(int(n), _addr(row_offsets), _addr(col_idx), _addr(colors_out),
+                                  ctypes.byref(k), _mode(mode), _stream(stream)), "sgr_color_noalloc")
     return int(k.value)
 
 
