@@ -50,6 +50,13 @@ WORKLOADS = {
     "stencil128": ("3-D 27-point stencil 128^3, natural order (profiling size)",
                    lambda: gg.stencil27(128)),
 }
+BATCH_WORKLOADS = {
+    "batch512": ("512 graphs, n log-uniform in [1k, 200k]: 1/3 uniform (avg degree 4-32), 1/3 R-MAT "
+                 "(ef 16, a,b,c,d = 0.57,0.19,0.19,0.05), 1/3 2-D 9-point / 3-D 27-point stencils, seed 0",
+                 lambda: gg.batch_mix(512, 1000, 200000, 0)),
+    "batch64": ("64 graphs of the same mix, n log-uniform in [1k, 50k], seed 1 (quick check)",
+                lambda: gg.batch_mix(64, 1000, 50000, 1)),
+}
 
 
 def dist_env():
@@ -367,13 +374,113 @@ def run_ours(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args, rank, world, local):
+    """Batched workload: graphs/s of one sgr_color_batch call over the whole mix,
+    against the same graphs colored by one sgr_color call each (the plain path)."""
+    import torch
+
+    from paper_1606_06025_gb300 import sgrcolor as lib
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    desc, make = BATCH_WORKLOADS[args.workload]
+    b = make()
+    if world > 1:  # shard the graphs by rank: no exchange on the data path
+        b = gg.pack(b.graphs[rank::world])
+    n, m, G = int(b.vtx_off[-1]), int(b.edge_off[-1]), b.G
+    ro = torch.from_numpy(b.row_offsets).to(dev)
+    ci = torch.from_numpy(b.col_idx).to(dev)
+    colors = torch.empty(n, dtype=torch.int32, device=dev)
+    kk = np.zeros(G, dtype=np.int32)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    mode = args.mode
+
+    def step():
+        lib.sgr_color_batch(G, b.vtx_off, b.edge_off, ro, ci, colors, kk, mode, stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    st = lib.sgr_last_stats()
+    total = sum(ms)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    value = G * world * args.steps / (total * 1e-3)
+    # the plain path: one sgr_color per graph, same graphs, same device buffers
+    seq_ms = []
+    offs = [(int(b.vtx_off[i]), int(b.vtx_off[i + 1]), int(b.edge_off[i]), int(b.edge_off[i + 1]))
+            for i in range(G)]
+    dev_graphs = []
+    for i, (v0, v1, e0_, e1_) in enumerate(offs):
+        r = torch.from_numpy(b.graphs[i].row_offsets).to(dev)
+        c = torch.from_numpy(b.graphs[i].col_idx).to(dev) if e1_ > e0_ else torch.zeros(
+            4, dtype=torch.int32, device=dev)
+        dev_graphs.append((v1 - v0, r, c))
+    out = torch.empty(max(x[0] for x in dev_graphs) + 1, dtype=torch.int32, device=dev)
+    for rep in range(2):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for nn, r, c in dev_graphs:
+            lib.sgr_color(nn, r, c, out, mode, stream)
+        e1.record(stream)
+        e1.synchronize()
+        if rep == 1:
+            seq_ms.append(e0.elapsed_time(e1))
+    seq_value = G / (seq_ms[0] * 1e-3)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {
+        "metric": "batched graphs/s", "value": value, "unit": "graphs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "graphs": G, "n": n, "m": m,
+                   "mode": mode, "l2": "flushed (512 MiB write) before every step",
+                   "parallelism": f"graphs sharded by rank x{world}"},
+        "rounds": st["rounds"], "sum_d": st["sum_d"], "kernel_ms": st["device_ms"],
+        "sequential_graphs_per_s": seq_value, "speedup_vs_sequential": value / seq_value,
+        "clocks": clocks, "gpu_launches": args.steps * 3,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS), default="rmat20")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + list(BATCH_WORKLOADS),
+                    default="rmat20")
     ap.add_argument("--mode", choices=["det", "fast"], default="det")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -383,6 +490,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload in BATCH_WORKLOADS:
+        run_batch(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

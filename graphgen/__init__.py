@@ -130,15 +130,13 @@ def uniform(n: int, avg_degree: float, seed: int = 0) -> CSR:
 
 def rmat(scale: int, edge_factor: int = 16, abc=(0.57, 0.19, 0.19), seed: int = 0,
          n: int | None = None) -> CSR:
-    """R-MAT graph on 2^scale ids with edge_factor * 2^scale draws, ids permuted
-    by the seed.  With ``n`` below 2^scale only ids < n are kept and the draw
-    count is raised so that about edge_factor * n pairs survive."""
+    """R-MAT graph with edge_factor * n draws on ids [0, n), n = 2^scale by
+    default; an edge with an endpoint >= n is drawn again.  Ids are permuted
+    by the seed."""
     N = 1 << scale
     if n is None:
         n = N
-        draws = edge_factor * N
-    else:
-        draws = int(math.ceil(edge_factor * N * (N / n)))
+    draws = edge_factor * n
     a, b, c = abc
     return _take(_load().gg_rmat(scale, n, draws, a, b, c, seed),
                  f"rmat_s{scale}_n{n}_ef{edge_factor}_s{seed}",

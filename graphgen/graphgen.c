@@ -74,9 +74,44 @@ typedef struct {
     int32_t *ci; /* m */
 } gg_graph;
 
-static int cmp_i32(const void *a, const void *b) {
-    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
-    return (x > y) - (x < y);
+/* In-place ascending sort of int32 (quicksort with median-of-three pivots,
+ * recursing on the smaller side, insertion sort below 24 elements). */
+static void sort_i32(int32_t *a, int64_t n) {
+    while (n > 24) {
+        int64_t mid = n / 2;
+        int32_t x = a[0], y = a[mid], z = a[n - 1];
+        int32_t piv = (x < y) ? ((y < z) ? y : ((x < z) ? z : x)) : ((x < z) ? x : ((y < z) ? z : y));
+        int64_t i = 0, j = n - 1;
+        while (i <= j) {
+            while (a[i] < piv) i++;
+            while (a[j] > piv) j--;
+            if (i <= j) {
+                int32_t t = a[i];
+                a[i] = a[j];
+                a[j] = t;
+                i++;
+                j--;
+            }
+        }
+        /* [0, j] <= piv <= [i, n) */
+        if (j + 1 < n - i) {
+            sort_i32(a, j + 1);
+            a += i;
+            n -= i;
+        } else {
+            sort_i32(a + i, n - i);
+            n = j + 1;
+        }
+    }
+    for (int64_t i = 1; i < n; ++i) {
+        int32_t v = a[i];
+        int64_t k = i - 1;
+        while (k >= 0 && a[k] > v) {
+            a[k + 1] = a[k];
+            k--;
+        }
+        a[k + 1] = v;
+    }
 }
 
 /* Build a symmetric CSR from `cnt` undirected pairs (u[i], v[i]).  Self-loops
@@ -112,7 +147,7 @@ static gg_graph *gg_from_pairs(int32_t n, int64_t cnt, const int32_t *u, const i
     ro[0] = 0;
     for (int32_t i = 0; i < n; ++i) {
         int64_t a = pos[i], b = pos[i + 1];
-        if (b - a > 1) qsort(tmp + a, (size_t)(b - a), sizeof(int32_t), cmp_i32);
+        if (b - a > 1) sort_i32(tmp + a, b - a);
         int64_t start = w;
         for (int64_t k = a; k < b; ++k) {
             if (k > a && tmp[k] == tmp[k - 1]) continue;
@@ -173,12 +208,13 @@ void *gg_uniform(int32_t n, int64_t pairs, uint64_t seed) {
     return g;
 }
 
-/* R-MAT (Chakrabarti, Zhan and Faloutsos, SDM 2004): each of `draws` edges
- * descends `scale` levels of the adjacency matrix, picking a quadrant with
- * probabilities (a, b, c, 1-a-b-c).  No noise is added.  Vertex ids are then
- * relabelled by a seeded Fisher-Yates permutation of [0, 2^scale); only edges
- * whose relabelled endpoints are both below n are kept (n = 2^scale keeps
- * all), so graphs of any size can be drawn from the same distribution. */
+/* R-MAT (Chakrabarti, Zhan and Faloutsos, SDM 2004): each edge descends
+ * `scale` levels of the 2^scale x 2^scale adjacency matrix, picking a quadrant
+ * with probabilities (a, b, c, 1-a-b-c) given to 16-bit precision (four
+ * levels per 64-bit draw).  No noise is added.  An edge with an endpoint at or
+ * above n is drawn again, so `draws` edges land in [0, n)^2 (n = 2^scale keeps
+ * all of them).  Vertex ids are then relabelled by a seeded Fisher-Yates
+ * permutation of [0, n). */
 void *gg_rmat(int32_t scale, int32_t n, int64_t draws, double a, double b, double c,
               uint64_t seed) {
     if (scale < 1 || scale > 30) return NULL;
@@ -186,46 +222,47 @@ void *gg_rmat(int32_t scale, int32_t n, int64_t draws, double a, double b, doubl
     if (n <= 0 || n > N || draws < 0) return NULL;
     gg_rng r;
     gg_seed(&r, seed);
-    const double two53 = 9007199254740992.0;
-    const uint64_t ta = (uint64_t)(a * two53);
-    const uint64_t tb = (uint64_t)((a + b) * two53);
-    const uint64_t tc = (uint64_t)((a + b + c) * two53);
+    const uint32_t ta = (uint32_t)(a * 65536.0);
+    const uint32_t tb = (uint32_t)((a + b) * 65536.0);
+    const uint32_t tc = (uint32_t)((a + b + c) * 65536.0);
     int32_t *u = (int32_t *)malloc((size_t)(draws > 0 ? draws : 1) * sizeof(int32_t));
     int32_t *v = (int32_t *)malloc((size_t)(draws > 0 ? draws : 1) * sizeof(int32_t));
-    int32_t *perm = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    int32_t *perm = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     if (!u || !v || !perm) { free(u); free(v); free(perm); return NULL; }
-    for (int64_t i = 0; i < draws; ++i) {
+    uint64_t bits = 0;
+    int left = 0;
+    for (int64_t i = 0; i < draws;) {
         int64_t x = 0, y = 0;
         for (int l = 0; l < scale; ++l) {
-            uint64_t q = gg_next(&r) >> 11;
-            int bx, by;
-            if (q < ta) { bx = 0; by = 0; }
-            else if (q < tb) { bx = 0; by = 1; }
-            else if (q < tc) { bx = 1; by = 0; }
-            else { bx = 1; by = 1; }
+            if (left == 0) {
+                bits = gg_next(&r);
+                left = 4;
+            }
+            const uint32_t q = (uint32_t)(bits & 0xFFFFu);
+            bits >>= 16;
+            left--;
+            const int bx = q >= tb, by = (q >= ta && q < tb) || q >= tc;
             x = (x << 1) | bx;
             y = (y << 1) | by;
         }
+        if (x >= n || y >= n) continue; /* redraw */
         u[i] = (int32_t)x;
         v[i] = (int32_t)y;
+        i++;
     }
-    for (int64_t i = 0; i < N; ++i) perm[i] = (int32_t)i;
-    for (int64_t i = N - 1; i > 0; --i) {
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+    for (int64_t i = n - 1; i > 0; --i) {
         int64_t j = (int64_t)gg_below(&r, (uint64_t)(i + 1));
         int32_t t = perm[i];
         perm[i] = perm[j];
         perm[j] = t;
     }
-    int64_t kept = 0;
     for (int64_t i = 0; i < draws; ++i) {
-        int32_t pu = perm[u[i]], pv = perm[v[i]];
-        if (pu >= n || pv >= n) continue;
-        u[kept] = pu;
-        v[kept] = pv;
-        kept++;
+        u[i] = perm[u[i]];
+        v[i] = perm[v[i]];
     }
     free(perm);
-    gg_graph *g = gg_from_pairs(n, kept, u, v);
+    gg_graph *g = gg_from_pairs(n, draws, u, v);
     free(u);
     free(v);
     return g;
