@@ -179,6 +179,69 @@ int sgr_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
                     int32_t *num_colors, int mode, sgr_stream_t stream);
 
 /*
+ * Coloring server (continuous batching).  Deterministic mode only; the rule
+ * bits of `mode` apply.  Requests of any size arrive at any time; a scheduler
+ * thread keeps each admitted graph (its CSR, colors and worklist entries)
+ * resident on the device, advances the rounds of all resident graphs together
+ * in one persistent launch, retires finished graphs and admits waiting ones
+ * as room frees up under the HBM budget.  Every result equals sgr_color on
+ * the same graph in the same mode (the graphs are disjoint, the loser rules
+ * only compare ids within a graph).  The paper has no server; this is a
+ * systems addition around its Algorithm 7.
+ */
+typedef struct sgr_server sgr_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes;  /* device memory the server allocates at creation (0: 1 GiB):
+                                  about 30% for per-vertex state, the rest for col_idx */
+    int32_t max_inflight;      /* graphs resident at once (0: 1024) */
+    int32_t mode;              /* SGR_MODE_DETERMINISTIC | SGR_RULE_* */
+    int32_t device;            /* CUDA device ordinal */
+    int32_t rounds_per_launch; /* rounds advanced per launch (0: 8 while requests wait, else 64) */
+} sgr_server_config;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t pending;           /* waiting for admission */
+    int64_t resident;          /* admitted, not yet finished */
+    int64_t launches;          /* persistent launches so far */
+    int64_t rounds;            /* rounds advanced so far */
+    int64_t hbm_bytes;         /* device memory held */
+    int64_t vertex_capacity;   /* vertices that can be resident at once */
+    int64_t entry_capacity;    /* col_idx entries that can be resident at once */
+    double p50_ms, p99_ms, mean_ms;  /* submit-to-finish latency of completed requests */
+    double graphs_per_s;       /* completed / (last completion - first submission) */
+} sgr_server_counters;
+
+/* Create a server on cfg->device; allocates its whole budget up front.
+ * SGR_ERR_INVALID_ARG for fast mode, unknown bits or a budget under ~2 MiB;
+ * SGR_ERR_OUT_OF_MEMORY if the budget cannot be allocated. */
+int sgr_server_create(const sgr_server_config *cfg, sgr_server **out);
+
+/* Queue one graph (HOST CSR, same contract as sgr_color; rows need not be
+ * sorted).  The CSR is copied; the caller may free it on return.  Checks
+ * offsets, id range and self-loops (SGR_ERR_INVALID_GRAPH); a graph larger
+ * than the server's capacity gives SGR_ERR_OUT_OF_MEMORY.  *req_id receives a
+ * fresh id.  Thread-safe. */
+int sgr_server_submit(sgr_server *s, int32_t n, const int32_t *row_offsets_host,
+                      const int32_t *col_idx_host, uint64_t *req_id);
+
+/* Wait up to timeout_ms (0: do not wait, < 0: wait indefinitely) for a request.
+ * SGR_PENDING if not finished yet; SGR_OK with colors_host (HOST, n int32,
+ * may be NULL) and *num_colors filled, after which the id is forgotten;
+ * SGR_ERR_NOT_FOUND for an unknown or already collected id; or the request's
+ * error.  Thread-safe. */
+int sgr_server_poll(sgr_server *s, uint64_t req_id, int32_t *colors_host, int32_t *num_colors,
+                    int timeout_ms);
+
+/* Counters and latency percentiles so far.  Returns SGR_OK or the error that
+ * stopped the server. */
+int sgr_server_stats(sgr_server *s, sgr_server_counters *out);
+
+/* Stop the scheduler, free device memory and drop uncollected requests. */
+int sgr_server_destroy(sgr_server *s);
+
+/*
  * Check the input contract on the device: row_offsets[0] == 0,
  * non-decreasing offsets, ids in [0, n), no self-loops, no duplicate entry in
  * a row, and symmetry (w in adj(v) iff v in adj(w)).  Returns SGR_OK or

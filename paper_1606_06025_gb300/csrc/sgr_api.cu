@@ -161,6 +161,7 @@ struct Job {
     int G;
     const long long *vbase_dev;
     const long long *ebase_dev;
+    const long long *robase_dev;
     int32_t *gid_dev;  // filled by the caller for batched jobs
 };
 
@@ -201,6 +202,7 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         p->gid = j.gid_dev;
         p->vbase = j.vbase_dev;
         p->ebase = j.ebase_dev;
+        p->robase = j.robase_dev;
         p->m = j.m;
         p->n = j.n;
         p->colors = j.colors;
@@ -254,7 +256,7 @@ int run_job(DevCtx *c, Job &j, int mode, cudaStream_t st, int32_t *k_out) {
     size_t zero_bytes = 0;
     size_t need = layout(j, t, nullptr, nullptr, &zero_bytes);
     const size_t gid_off = need;
-    if (j.batched) need = align_up(need + (size_t)j.n * 4) + align_up((size_t)(j.G + 1) * 8) * 2 +
+    if (j.batched) need = align_up(need + (size_t)j.n * 4) + align_up((size_t)(j.G + 1) * 8) * 3 +
                           align_up((size_t)j.G * 4);
     cudaError_t e = c->scratch.ensure(need);
     if (e != cudaSuccess) return map_cuda(e);
@@ -295,6 +297,26 @@ int run_job(DevCtx *c, Job &j, int mode, cudaStream_t st, int32_t *k_out) {
 }
 
 }  // namespace
+
+namespace sgr {
+
+sgr_tuning tuning_snapshot() { return current_tuning(); }
+
+// Cooperative persistent launches of this process on one device are
+// serialised: two of them in flight could each wait in a grid barrier for
+// CTAs that cannot become resident.
+std::mutex &device_launch_mutex(int device) {
+    DevCtx *c = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_ctx_mu);
+        if ((int)g_ctx.size() <= device) g_ctx.resize(device + 1, nullptr);
+        if (!g_ctx[device]) g_ctx[device] = new DevCtx();
+        c = g_ctx[device];
+    }
+    return c->mu;
+}
+
+}  // namespace sgr
 
 extern "C" {
 
@@ -476,7 +498,7 @@ int sgr_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
     if (rc != SGR_OK) return rc;
     std::lock_guard<std::mutex> lk(c->mu);
     cudaStream_t st = (cudaStream_t)stream;
-    if ((rc = ensure_host_small(c, 2 * (size_t)(G + 1) + (size_t)G)) != SGR_OK) return rc;
+    if ((rc = ensure_host_small(c, 3 * (size_t)(G + 1) + (size_t)G)) != SGR_OK) return rc;
     Job j;
     std::memset(&j, 0, sizeof(j));
     j.n = (int32_t)n;
@@ -491,28 +513,34 @@ int sgr_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
     const sgr_tuning t = current_tuning();
     size_t zero_bytes = 0;
     const size_t base_need = layout(j, t, nullptr, nullptr, &zero_bytes);
-    const size_t need = align_up(base_need + (size_t)n * 4) + align_up((size_t)(G + 1) * 8) * 2 +
+    const size_t need = align_up(base_need + (size_t)n * 4) + align_up((size_t)(G + 1) * 8) * 3 +
                         align_up((size_t)G * 4);
     cudaError_t e = c->scratch.ensure(need);
     if (e != cudaSuccess) return map_cuda(e);
     char *tail = c->scratch.ptr + align_up(base_need + (size_t)n * 4);
     long long *vb_d = (long long *)tail;
     long long *eb_d = (long long *)(tail + align_up((size_t)(G + 1) * 8));
-    int32_t *k_d = (int32_t *)(tail + 2 * align_up((size_t)(G + 1) * 8));
+    long long *rb_d = (long long *)(tail + 2 * align_up((size_t)(G + 1) * 8));
+    int32_t *k_d = (int32_t *)(tail + 3 * align_up((size_t)(G + 1) * 8));
     std::memcpy(c->host_small, vtx_off, (size_t)(G + 1) * 8);
     std::memcpy(c->host_small + (G + 1), edge_off, (size_t)(G + 1) * 8);
+    for (int g = 0; g <= G; ++g) c->host_small[2 * (G + 1) + g] = vtx_off[g] + g;
     if ((e = cudaMemcpyAsync(vb_d, c->host_small, (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return map_cuda(e);
     if ((e = cudaMemcpyAsync(eb_d, c->host_small + (G + 1), (size_t)(G + 1) * 8, cudaMemcpyHostToDevice,
                              st)) != cudaSuccess)
         return map_cuda(e);
+    if ((e = cudaMemcpyAsync(rb_d, c->host_small + 2 * (G + 1), (size_t)(G + 1) * 8,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return map_cuda(e);
     j.vbase_dev = vb_d;
     j.ebase_dev = eb_d;
+    j.robase_dev = rb_d;
     int32_t kall = 0;
     rc = run_job(c, j, mode, st, &kall);
     if (rc != SGR_OK) return rc;
     if ((e = sgr::launch_segmented_max(colors_out, vb_d, G, k_d, st)) != cudaSuccess) return map_cuda(e);
-    int32_t *kh = (int32_t *)(c->host_small + 2 * (G + 1));
+    int32_t *kh = (int32_t *)(c->host_small + 3 * (G + 1));
     if ((e = cudaMemcpyAsync(kh, k_d, (size_t)G * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return map_cuda(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);

@@ -21,8 +21,12 @@
 //                        color so far, error code, statistics.
 #pragma once
 
-#include <cstdint>
 #include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "sgrcolor.h"
 
 namespace sgr {
 
@@ -37,9 +41,8 @@ constexpr int kTraceCap = 1 << 16;               // rounds recorded in the timel
 constexpr int kTraceFields = 4;                  // |W_r|, ns at end of phase A / phase B, rescans
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;  // bounded device waits
 
-// status codes mirrored from sgrcolor.h (device code cannot include it twice)
-constexpr int kErrNoConvergence = -5;
-constexpr int kErrTimeout = -6;
+constexpr int kErrNoConvergence = SGR_ERR_NO_CONVERGENCE;
+constexpr int kErrTimeout = SGR_ERR_TIMEOUT;
 
 struct Counters {
     unsigned int nl[2];             // light list sizes by round parity
@@ -58,6 +61,7 @@ struct Counters {
     unsigned long long dcur;        // det: degree sum of the current worklist
     unsigned long long nslow;       // det: worklist vertices that rescanned their row this round
     long long rounds;
+    long long round;                // resumable launches: the next round to run
     long long t_init_ns;            // globaltimer: end of the init pass (after its barrier)
 };
 
@@ -67,6 +71,7 @@ struct Params {
     const int32_t *gid;        // batched: vertex -> graph id
     const long long *vbase;    // batched: graph -> first global vertex
     const long long *ebase;    // batched: graph -> first global entry
+    const long long *robase;   // batched: graph -> index of its first row offset in ro
     long long m;               // total col_idx entries
     int32_t n;                 // total vertices
     int32_t *colors;
@@ -92,6 +97,9 @@ struct Params {
     int rule;                  // 0 low keeps, 1 low loses, 2 degree
     long long max_rounds;
     unsigned int nblocks;
+    int resume;                // 1: skip init and continue from Counters::round
+    int resume_sorted;         // resume: every resident graph has ascending rows
+    long long rounds_per_launch;  // resume: rounds to advance before returning
 };
 
 // Scratch sizes for a graph of n vertices / m entries under a chunk size.
@@ -110,9 +118,17 @@ inline ScratchPlan plan_scratch(long long n, long long m, int chunk) {
     return p;
 }
 
+// Host-side shared state (implemented in sgr_api.cu).
+sgr_tuning tuning_snapshot();
+std::mutex &device_launch_mutex(int device);
+
 // Launches (implemented in sgr_kernels.cu).
 int occupancy_blocks_per_sm(bool fast, bool batched, int *out);
 cudaError_t launch_color(const Params &p, bool fast, bool batched, int grid, cudaStream_t s);
+cudaError_t launch_admit(const Params &p, int g, long long vb, int32_t n, int par, int grid,
+                         cudaStream_t s);
+cudaError_t launch_slot_status(const int32_t *colors, const long long *vbase, const int32_t *nv,
+                               int G, int32_t *rem, int32_t *kmax, cudaStream_t s);
 cudaError_t launch_fill_gid(int32_t *gid, const long long *vbase_dev, int G, int32_t n,
                             cudaStream_t s);
 cudaError_t launch_segmented_max(const int32_t *colors, const long long *vbase_dev, int G,

@@ -112,10 +112,11 @@ __device__ __forceinline__ void row_of(const Params &p, int32_t v, long long &s,
                                        int32_t &vb) {
     if (kBatched) {
         const int g = __ldcg(p.gid + v);
-        const long long eb = __ldg(p.ebase + g);
-        s = eb + __ldg(p.ro + v + g);
-        e = eb + __ldg(p.ro + v + g + 1);
-        vb = (int32_t)__ldg(p.vbase + g);
+        const long long eb = __ldg(p.ebase + g), vbase = __ldg(p.vbase + g);
+        const long long rb = __ldg(p.robase + g) + (v - vbase);
+        s = eb + __ldg(p.ro + rb);
+        e = eb + __ldg(p.ro + rb + 1);
+        vb = (int32_t)vbase;
     } else {
         s = __ldg(p.ro + v);
         e = __ldg(p.ro + v + 1);
@@ -1372,22 +1373,34 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
     Counters *ctr = p.ctr;
     const bool recorder = blockIdx.x == 0 && threadIdx.x == 0;
     const unsigned long long t0 = globaltimer();
-    if (recorder && !kFast) ctr->dcur = (unsigned long long)p.m;
-    init_phase<kFast, kBatched>(p);
-    if (!grid_barrier(p, gen)) { flush_stats(p, acc); return; }
-    if (recorder) ctr->t_init_ns = (long long)(globaltimer() - t0);
-    const bool sorted = __ldcg(&ctr->unsorted_pairs) == __ldcg(&ctr->boundary_pairs);
+    bool sorted;
+    long long r;
+    if (!p.resume) {
+        if (recorder && !kFast) ctr->dcur = (unsigned long long)p.m;
+        init_phase<kFast, kBatched>(p);
+        if (!grid_barrier(p, gen)) { flush_stats(p, acc); return; }
+        if (recorder) ctr->t_init_ns = (long long)(globaltimer() - t0);
+        sorted = __ldcg(&ctr->unsorted_pairs) == __ldcg(&ctr->boundary_pairs);
+        r = 1;
+    } else {  // continue the rounds of an earlier launch (graphs admitted in between)
+        sorted = p.resume_sorted != 0;
+        r = __ldcg(&ctr->round);
+    }
     const bool prefix = sorted && p.rule == 0;
-    long long r = 1;
+    const long long r_end = p.resume ? r + p.rounds_per_launch : LLONG_MAX;
     bool ok = true;
     for (;; ++r) {
+        if (r == r_end) break;
         const int par = (int)(r & 1), pn = par ^ 1;
         const unsigned nl = __ldcg(&ctr->nl[par]);
         const unsigned nm = __ldcg(&ctr->nm[par]);
         const unsigned long long h64 = __ldcg(&ctr->h64[par]);
         const unsigned long long total =
             (unsigned long long)nl + nm + (unsigned long long)(h64 >> 32);
-        if (total == 0) break;
+        if (total == 0) {
+            if (recorder && !kFast) ctr->sc64 = 0;  // nobody is left to read those bitmaps
+            break;
+        }
         if (r > p.max_rounds) {
             if (recorder) atomicCAS(&ctr->err, 0, kErrNoConvergence);
             break;
@@ -1416,7 +1429,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             fast_hub_assign<kBatched>(p, par, h64, kmax, acc);
             fast_medium_assign<kBatched>(p, p.mw[par], nm, acc);
             fast_light_assign<kBatched>(p, p.lw[par], nl, sbuf, acc);
-        } else if (r > 1) {
+        } else if (r > 1 || p.resume) {
             det_assign<kBatched>(p, p.hw[par], (unsigned)(h64 >> 32), true);
             det_assign<kBatched>(p, p.mw[par], nm, false);
             det_assign<kBatched>(p, p.lw[par], nl, false);
@@ -1433,7 +1446,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
         } else {
             det_hub_detect<kBatched>(p, par, h64, prefix, b);
             det_medium_detect<kBatched>(p, p.mw[par], nm, p.mw[pn], &ctr->nm[pn], prefix, b);
-            det_light_detect<kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix, r == 1, b);
+            det_light_detect<kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix,
+                                       r == 1 && !p.resume, b);
         }
         acc.w += b.w;
         acc.d += b.d;
@@ -1448,7 +1462,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             ctr->nslow = 0;
         }
     }
-    if (recorder && ok) ctr->rounds = r - 1;
+    if (recorder && ok) {
+        ctr->rounds = r - 1;
+        ctr->round = r;
+    }
     flush_stats(p, acc);
 }
 
@@ -1476,6 +1493,95 @@ __global__ void segmented_max_kernel(const int32_t *colors, const long long *vba
         int b2 = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b2 = max(b2, s_k[w]);
         out[g] = b2;
+    }
+}
+
+// ------------------------------------------------------------ server helpers
+
+// Admit graph slot g (global vertices [vb, vb + n), det mode) into the
+// resident state between two resumable launches: reset its per-vertex state,
+// compute lower-neighbour counts, and append its vertices, binned by degree,
+// to the worklists of parity `par` (the next round's W_in).  Hubs use their
+// vertex id as slot.
+__global__ void __launch_bounds__(kBlock) admit_kernel(const Params p, int g, long long vb,
+                                                       int32_t n, int par) {
+    unsigned long long dsum = 0, dummy = 0;
+    const unsigned nt = ((unsigned)n + kLightTile - 1) / kLightTile;
+    for (unsigned t = blockIdx.x; t < nt; t += gridDim.x) {
+        bool is_light[kLightUnroll], is_med[kLightUnroll];
+        int32_t vv[kLightUnroll];
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) {
+            is_light[u] = false;
+            is_med[u] = false;
+            const long long i = (long long)tile_index(t, u);
+            vv[u] = (int32_t)(vb + i);
+            if (i >= n) continue;
+            const int32_t v = (int32_t)(vb + i);
+            const_cast<int32_t *>(p.gid)[v] = g;
+            __stcg(p.colors + v, -1);
+            p.witness[v] = -1;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) p.bm[(size_t)j * p.np + v] = 0u;
+            const long long eb = p.ebase[g];
+            const long long s = eb + __ldg(p.ro + p.robase[g] + i);
+            const long long e = eb + __ldg(p.ro + p.robase[g] + i + 1);
+            long long lo = s, hi = e;
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (vb + __ldg(p.ci + mid) < v) lo = mid + 1;
+                else hi = mid;
+            }
+            p.lowdeg[v] = (int32_t)(lo - s);
+            const long long deg = e - s;
+            dsum += (unsigned long long)deg;
+            if (deg <= p.light_max) {
+                is_light[u] = true;
+            } else if (deg <= p.chunk) {
+                is_med[u] = true;
+            } else {
+                p.hvert[v] = v;
+                hub_list_push(&p.ctr->h64[par], p.hw[par], p.hcb[par], v,
+                              (unsigned)((deg + p.chunk - 1) / p.chunk));
+            }
+        }
+        block_push(is_light, vv, &p.ctr->nl[par], p.lw[par], dummy);
+        block_push(is_med, vv, &p.ctr->nm[par], p.mw[par], dummy);
+    }
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+    if ((threadIdx.x & 31) == 0 && dsum) atomicAdd(&p.ctr->dcur, dsum);
+}
+
+// Per resident graph slot: vertices not yet final and the largest color.
+__global__ void slot_status_kernel(const int32_t *colors, const long long *vbase,
+                                   const int32_t *nv, int G, int32_t *rem, int32_t *kmax) {
+    const int g = blockIdx.x;
+    if (g >= G) return;
+    const long long a = vbase[g], b = a + nv[g];
+    int open = 0, k = 0;
+    for (long long v = a + threadIdx.x; v < b; v += blockDim.x) {
+        const int c = __ldcg(colors + v);
+        open += c <= 0;
+        k = max(k, c);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        open += __shfl_xor_sync(kFull, open, o);
+        k = max(k, __shfl_xor_sync(kFull, k, o));
+    }
+    __shared__ int s_o[kWarps], s_k[kWarps];
+    if ((threadIdx.x & 31) == 0) {
+        s_o[threadIdx.x >> 5] = open;
+        s_k[threadIdx.x >> 5] = k;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int o2 = 0, k2 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            o2 += s_o[w];
+            k2 = max(k2, s_k[w]);
+        }
+        rem[g] = o2;
+        kmax[g] = k2;
     }
 }
 
@@ -1565,6 +1671,20 @@ cudaError_t launch_color(const Params &p, bool fast, bool batched, int grid, cud
     else fn = batched ? (const void *)sgr_color_kernel<false, true>
                       : (const void *)sgr_color_kernel<false, false>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
+}
+
+cudaError_t launch_admit(const Params &p, int g, long long vb, int32_t n, int par, int grid,
+                         cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    admit_kernel<<<grid, kBlock, 0, s>>>(p, g, vb, n, par);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slot_status(const int32_t *colors, const long long *vbase, const int32_t *nv,
+                               int G, int32_t *rem, int32_t *kmax, cudaStream_t s) {
+    if (G <= 0) return cudaSuccess;
+    slot_status_kernel<<<G, kBlock, 0, s>>>(colors, vbase, nv, G, rem, kmax);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fill_gid(int32_t *gid, const long long *vbase_dev, int G, int32_t n,

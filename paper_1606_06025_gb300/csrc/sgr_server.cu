@@ -1,0 +1,549 @@
+// sgr_server.cu -- a continuous-batching coloring server (deterministic mode).
+//
+// Requests (host CSR graphs) arrive at any time through sgr_server_submit.
+// A scheduler thread keeps every admitted graph resident on the device: its
+// CSR in two arenas (row offsets, column ids), its per-vertex state (colors,
+// forbidden-color bitmaps, worklist entries) in a global vertex space where
+// it owns a contiguous range.  The rounds of all resident graphs advance
+// together: each launch of the resumable persistent kernel runs R rounds of
+// Algorithm 7 over the union of their worklists (graphs are disjoint, so each
+// still gets exactly its own coloring), then returns.  Between launches the
+// scheduler retires graphs whose vertices are all final (device-side status
+// pass, then a copy of their colors to the host) and admits queued requests
+// whose vertex and entry ranges fit in the free space of the arenas, which are
+// sized from the HBM budget at creation.  A new graph joins the running rounds
+// at its own round 1 while the others are further along.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "sgr_internal.cuh"
+#include "sgrcolor.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+int map_err(cudaError_t e) {
+    if (e == cudaSuccess) return SGR_OK;
+    if (e == cudaErrorMemoryAllocation) return SGR_ERR_OUT_OF_MEMORY;
+    return SGR_ERR_CUDA;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// First-fit allocator of ranges in [0, cap).
+struct RangeAlloc {
+    std::map<long long, long long> free_;  // start -> length
+    long long cap = 0, used = 0;
+    void init(long long c) {
+        cap = c;
+        used = 0;
+        free_.clear();
+        if (c > 0) free_[0] = c;
+    }
+    long long alloc(long long len) {
+        if (len <= 0) return 0;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < len) continue;
+            const long long off = it->first, rest = it->second - len;
+            free_.erase(it);
+            if (rest) free_[off + len] = rest;
+            used += len;
+            return off;
+        }
+        return -1;
+    }
+    void release(long long off, long long len) {
+        if (len <= 0) return;
+        used -= len;
+        auto it = free_.emplace(off, len).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct Request {
+    uint64_t id = 0;
+    int32_t n = 0;
+    long long m = 0;
+    std::vector<int32_t> ro, ci;
+    Clock::time_point t_submit, t_done;
+    int status = SGR_PENDING;
+    std::vector<int32_t> colors;
+    int32_t k = 0;
+    int slot = -1;
+    long long vb = 0, eb = 0, rb = 0;
+};
+
+}  // namespace
+
+struct sgr_server {
+    sgr_server_config cfg{};
+    int device = 0, sms = 0, per_sm = 0, grid = 0;
+    cudaStream_t stream = nullptr;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    int fatal = SGR_OK;
+    std::deque<Request *> pending;
+    std::unordered_map<uint64_t, Request *> reqs;
+    std::vector<Request *> slot_req;
+    std::vector<int> free_slots;
+    uint64_t next_id = 1;
+    RangeAlloc va, ea, ra;
+    long long Vcap = 0, Ecap = 0, Rcap = 0;
+    int G = 0;
+    char *dmem = nullptr;
+    size_t dbytes = 0;
+    sgr::Params P{};
+    long long *vbase_d = nullptr, *ebase_d = nullptr, *robase_d = nullptr;
+    int32_t *nv_d = nullptr, *rem_d = nullptr, *kmax_d = nullptr;
+    std::vector<int32_t> rem_h, kmax_h;
+    long long round = 1;
+    // statistics
+    std::vector<double> lat_ms;
+    long long submitted = 0, completed = 0, failed = 0, launches = 0, rounds_run = 0;
+    bool any_submit = false;
+    Clock::time_point t_first_submit, t_last_done;
+};
+
+namespace {
+
+// Per-vertex device bytes: colors, 8 bitmap words, lower count, witness, graph
+// id, two parities of three worklists and hub chunk bases, six hub arrays, one
+// row offset.
+constexpr long long kVertexBytes = 4 + 32 + 4 + 4 + 4 + 2 * 4 * 4 + 6 * 4 + 4;
+
+int carve(sgr_server *S) {
+    const long long budget = S->cfg.hbm_budget_bytes;
+    const int G = S->G;
+    const size_t fixed = align_up(sizeof(sgr::Counters)) +
+                         align_up(sizeof(long long) * sgr::kTraceCap * sgr::kTraceFields) +
+                         3 * align_up((size_t)G * 8) + 3 * align_up((size_t)G * 4) + 64 * 256;
+    if (budget < (long long)fixed + (1 << 20)) return SGR_ERR_INVALID_ARG;
+    long long Vcap = (long long)((budget - (long long)fixed) * 0.3) / kVertexBytes;
+    Vcap = std::min<long long>(Vcap, (1ll << 31) - 2 * G - 64);
+    Vcap = Vcap / 64 * 64;
+    long long Ecap = (budget - (long long)fixed - Vcap * kVertexBytes) / 4 - 64;
+    if (Vcap < 64 || Ecap < 64) return SGR_ERR_INVALID_ARG;
+    S->Vcap = Vcap;
+    S->Ecap = Ecap;
+    S->Rcap = Vcap + G;
+    size_t off = 0;
+    std::vector<std::pair<void **, size_t>> parts;
+    sgr::Params &P = S->P;
+    std::memset(&P, 0, sizeof(P));
+    auto take = [&](void **dst, size_t bytes) { parts.push_back({dst, bytes}); };
+    int32_t *lw0, *lw1, *mw0, *mw1, *hw0, *hw1, *gid, *ro, *ci;
+    unsigned *hcb0, *hcb1;
+    take((void **)&P.ctr, sizeof(sgr::Counters));
+    take((void **)&P.hdone, (size_t)Vcap * 4);
+    take((void **)&P.hconf, (size_t)Vcap * 4);
+    take((void **)&P.trace, sizeof(long long) * sgr::kTraceCap * sgr::kTraceFields);
+    take((void **)&P.colors, (size_t)Vcap * 4);
+    take((void **)&P.bm, (size_t)Vcap * 8 * 4);
+    take((void **)&P.lowdeg, (size_t)Vcap * 4);
+    take((void **)&P.witness, (size_t)Vcap * 4);
+    take((void **)&gid, (size_t)Vcap * 4);
+    take((void **)&lw0, (size_t)Vcap * 4);
+    take((void **)&lw1, (size_t)Vcap * 4);
+    take((void **)&mw0, (size_t)Vcap * 4);
+    take((void **)&mw1, (size_t)Vcap * 4);
+    take((void **)&hw0, (size_t)Vcap * 4);
+    take((void **)&hw1, (size_t)Vcap * 4);
+    take((void **)&hcb0, (size_t)Vcap * 4);
+    take((void **)&hcb1, (size_t)Vcap * 4);
+    take((void **)&P.hvert, (size_t)Vcap * 4);
+    take((void **)&P.hbase, (size_t)Vcap * 4);
+    take((void **)&P.sw, (size_t)Vcap * 4);
+    take((void **)&P.scb, (size_t)Vcap * 4);
+    take((void **)&P.hbits, 256);
+    take((void **)&S->vbase_d, (size_t)G * 8);
+    take((void **)&S->ebase_d, (size_t)G * 8);
+    take((void **)&S->robase_d, (size_t)G * 8);
+    take((void **)&S->nv_d, (size_t)G * 4);
+    take((void **)&S->rem_d, (size_t)G * 4);
+    take((void **)&S->kmax_d, (size_t)G * 4);
+    take((void **)&ro, (size_t)S->Rcap * 4);
+    take((void **)&ci, (size_t)Ecap * 4 + 64);
+    for (auto &pr : parts) off += align_up(pr.second);
+    cudaError_t e = cudaMalloc(&S->dmem, off);
+    if (e != cudaSuccess) {
+        S->dmem = nullptr;
+        return map_err(e);
+    }
+    S->dbytes = off;
+    off = 0;
+    for (auto &pr : parts) {
+        *pr.first = S->dmem + off;
+        off += align_up(pr.second);
+    }
+    if ((e = cudaMemset(S->dmem, 0, S->dbytes)) != cudaSuccess) return map_err(e);
+    P.ro = ro;
+    P.ci = ci;
+    P.gid = gid;
+    P.vbase = S->vbase_d;
+    P.ebase = S->ebase_d;
+    P.robase = S->robase_d;
+    P.m = Ecap;
+    P.n = (int32_t)Vcap;
+    P.np = Vcap;
+    P.lw[0] = lw0; P.lw[1] = lw1;
+    P.mw[0] = mw0; P.mw[1] = mw1;
+    P.hw[0] = hw0; P.hw[1] = hw1;
+    P.hcb[0] = hcb0; P.hcb[1] = hcb1;
+    const sgr_tuning t = sgr::tuning_snapshot();
+    P.light_max = t.light_max;
+    P.chunk = t.chunk;
+    P.rule = (S->cfg.mode & SGR_RULE_MASK) >> 4;
+    P.max_rounds = LLONG_MAX / 4;
+    P.resume = 1;
+    P.resume_sorted = 1;
+    S->va.init(Vcap);
+    S->ea.init(Ecap);
+    S->ra.init(S->Rcap);
+    // the first round number must be visible to the first resumable launch
+    sgr::Counters c0;
+    std::memset(&c0, 0, sizeof(c0));
+    c0.round = 1;
+    if ((e = cudaMemcpy(P.ctr, &c0, sizeof(c0), cudaMemcpyHostToDevice)) != cudaSuccess) return map_err(e);
+    return SGR_OK;
+}
+
+void finish(sgr_server *S, Request *q, int status) {
+    // caller holds S->mu
+    q->status = status;
+    q->t_done = Clock::now();
+    if (status == SGR_OK) {
+        S->completed++;
+        S->lat_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
+        S->t_last_done = q->t_done;
+    } else {
+        S->failed++;
+    }
+    S->cv_done.notify_all();
+}
+
+void release_slot(sgr_server *S, Request *q) {
+    // caller holds S->mu
+    S->va.release(q->vb, q->n);
+    S->ea.release(q->eb, q->m);
+    S->ra.release(q->rb, (long long)q->n + 1);
+    S->slot_req[q->slot] = nullptr;
+    S->free_slots.push_back(q->slot);
+    q->slot = -1;
+}
+
+void fail_all_resident(sgr_server *S, int status) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (int g = 0; g < S->G; ++g) {
+        Request *q = S->slot_req[g];
+        if (!q) continue;
+        release_slot(S, q);
+        finish(S, q, status);
+    }
+}
+
+void worker_loop(sgr_server *S) {
+    cudaSetDevice(S->device);
+    const int32_t zero = 0;
+    for (;;) {
+        std::vector<Request *> admitted;
+        int resident = 0;
+        bool have_pending = false;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->stop) break;
+            for (auto it = S->pending.begin(); it != S->pending.end();) {
+                Request *q = *it;
+                if (S->free_slots.empty()) break;
+                const long long vb = S->va.alloc(q->n);
+                if (vb < 0) { ++it; continue; }
+                const long long eb = S->ea.alloc(q->m);
+                if (eb < 0) { S->va.release(vb, q->n); ++it; continue; }
+                const long long rb = S->ra.alloc((long long)q->n + 1);
+                if (rb < 0) { S->va.release(vb, q->n); S->ea.release(eb, q->m); ++it; continue; }
+                q->slot = S->free_slots.back();
+                S->free_slots.pop_back();
+                q->vb = vb;
+                q->eb = eb;
+                q->rb = rb;
+                S->slot_req[q->slot] = q;
+                admitted.push_back(q);
+                it = S->pending.erase(it);
+            }
+            resident = S->G - (int)S->free_slots.size();
+            have_pending = !S->pending.empty();
+            if (resident == 0) {
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+                continue;
+            }
+        }
+        std::lock_guard<std::mutex> dev_lk(sgr::device_launch_mutex(S->device));
+        cudaStream_t st = S->stream;
+        cudaError_t e = cudaSuccess;
+        const int par = (int)(S->round & 1);
+        for (Request *q : admitted) {
+            const int g = q->slot;
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync((int32_t *)S->P.ro + q->rb, q->ro.data(), ((size_t)q->n + 1) * 4,
+                                    cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && q->m > 0)
+                e = cudaMemcpyAsync((int32_t *)S->P.ci + q->eb, q->ci.data(), (size_t)q->m * 4,
+                                    cudaMemcpyHostToDevice, st);
+            const long long vb = q->vb, eb = q->eb, rb = q->rb;
+            const int32_t nv = q->n;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(S->vbase_d + g, &vb, 8, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(S->ebase_d + g, &eb, 8, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(S->robase_d + g, &rb, 8, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(S->nv_d + g, &nv, 4, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host sources above live on this frame
+            if (e == cudaSuccess) e = sgr::launch_admit(S->P, g, vb, nv, par, S->sms * 4, st);
+        }
+        int R = S->cfg.rounds_per_launch > 0 ? S->cfg.rounds_per_launch : (have_pending ? 8 : 64);
+        sgr::Params P = S->P;
+        P.rounds_per_launch = R;
+        P.nblocks = (unsigned)S->grid;
+        // fresh barrier and error state for this launch
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(&P.ctr->bar_count, 0, 2 * sizeof(unsigned), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&P.ctr->err, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = sgr::launch_color(P, false, true, S->grid, st);
+        if (e == cudaSuccess)
+            e = sgr::launch_slot_status(P.colors, S->vbase_d, S->nv_d, S->G, S->rem_d, S->kmax_d, st);
+        sgr::Counters h;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, P.ctr, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S->rem_h.data(), S->rem_d, (size_t)S->G * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S->kmax_h.data(), S->kmax_d, (size_t)S->G * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess || h.err != 0) {
+            const int status = e != cudaSuccess ? map_err(e) : h.err;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->fatal = status;
+            }
+            fail_all_resident(S, status);
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->stop = true;
+            break;
+        }
+        S->launches++;
+        S->rounds_run += h.round - S->round;
+        S->round = h.round;
+        // Retire finished graphs, unless a hub's color still waits to be
+        // scattered into neighbour bitmaps (its range must not be reused yet).
+        if (h.sc64 != 0) continue;
+        for (int g = 0; g < S->G; ++g) {
+            Request *q = S->slot_req[g];
+            if (!q) continue;
+            // A resident graph always finishes: in every round the worklist vertex that
+            // wins against all its neighbours under the rule keeps its color.
+            if (S->rem_h[g] != 0) continue;
+            q->colors.resize(q->n);
+            e = cudaMemcpyAsync(q->colors.data(), P.colors + q->vb, (size_t)q->n * 4,
+                                cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(S->nv_d + g, &zero, 4, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            q->k = S->kmax_h[g];
+            std::lock_guard<std::mutex> lk(S->mu);
+            release_slot(S, q);
+            finish(S, q, e != cudaSuccess ? map_err(e) : SGR_OK);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sgr_server_create(const sgr_server_config *cfg, sgr_server **out) {
+    if (!cfg || !out) return SGR_ERR_INVALID_ARG;
+    if ((cfg->mode & SGR_MODE_MASK) != SGR_MODE_DETERMINISTIC) return SGR_ERR_INVALID_ARG;
+    if (cfg->mode & ~(SGR_MODE_MASK | SGR_RULE_MASK) || ((cfg->mode & SGR_RULE_MASK) >> 4) > 2)
+        return SGR_ERR_INVALID_ARG;
+    if (cfg->max_inflight < 0 || cfg->rounds_per_launch < 0 || cfg->hbm_budget_bytes < 0)
+        return SGR_ERR_INVALID_ARG;
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess) return SGR_ERR_CUDA;
+    sgr_server *S = new sgr_server();
+    S->cfg = *cfg;
+    if (S->cfg.hbm_budget_bytes == 0) S->cfg.hbm_budget_bytes = 1ll << 30;
+    S->G = S->cfg.max_inflight > 0 ? S->cfg.max_inflight : 1024;
+    S->device = cfg->device;
+    int rc = SGR_OK;
+    if (cudaSetDevice(S->device) != cudaSuccess) rc = SGR_ERR_INVALID_ARG;
+    if (rc == SGR_OK && cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess)
+        rc = SGR_ERR_CUDA;
+    if (rc == SGR_OK && sgr::occupancy_blocks_per_sm(false, true, &S->per_sm) != 0) rc = SGR_ERR_CUDA;
+    if (rc == SGR_OK) {
+        const sgr_tuning t = sgr::tuning_snapshot();
+        if (t.blocks_per_sm > 0) S->per_sm = std::min(S->per_sm, t.blocks_per_sm);
+        S->grid = S->per_sm * S->sms;
+        if (S->grid < 1) rc = SGR_ERR_CUDA;
+    }
+    if (rc == SGR_OK && cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = SGR_ERR_CUDA;
+    if (rc == SGR_OK) rc = carve(S);
+    if (rc == SGR_OK) {
+        S->slot_req.assign(S->G, nullptr);
+        for (int g = S->G - 1; g >= 0; --g) S->free_slots.push_back(g);
+        S->rem_h.assign(S->G, 0);
+        S->kmax_h.assign(S->G, 0);
+        S->worker = std::thread(worker_loop, S);
+    }
+    cudaSetDevice(prev);
+    if (rc != SGR_OK) {
+        if (S->dmem) cudaFree(S->dmem);
+        if (S->stream) cudaStreamDestroy(S->stream);
+        delete S;
+        return rc;
+    }
+    *out = S;
+    return SGR_OK;
+}
+
+int sgr_server_submit(sgr_server *S, int32_t n, const int32_t *ro, const int32_t *ci,
+                      uint64_t *req_id) {
+    if (!S || !req_id || n < 0 || (n > 0 && !ro)) return SGR_ERR_INVALID_ARG;
+    const long long m = n > 0 ? ro[n] : 0;
+    if (n > 0 && (ro[0] != 0 || m < 0)) return SGR_ERR_INVALID_GRAPH;
+    if (m > 0 && !ci) return SGR_ERR_INVALID_ARG;
+    Request *q = new Request();
+    q->n = n;
+    q->m = m;
+    if (n > 0) {
+        q->ro.assign(ro, ro + n + 1);
+        q->ci.assign(ci, ci + m);
+        for (int32_t v = 0; v < n; ++v) {
+            const int32_t a = ro[v], b = ro[v + 1];
+            if (b < a || b > m) { delete q; return SGR_ERR_INVALID_GRAPH; }
+            bool asc = true;
+            for (int32_t i = a; i < b; ++i) {
+                const int32_t w = q->ci[i];
+                if (w < 0 || w >= n || w == v) { delete q; return SGR_ERR_INVALID_GRAPH; }
+                if (i > a && q->ci[i - 1] >= w) asc = false;
+            }
+            if (!asc) std::sort(q->ci.begin() + a, q->ci.begin() + b);  // order within a row is free
+        }
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->fatal != SGR_OK) { delete q; return S->fatal; }
+    if (n > S->Vcap || m > S->Ecap) { delete q; return SGR_ERR_OUT_OF_MEMORY; }
+    q->id = S->next_id++;
+    q->t_submit = Clock::now();
+    if (!S->any_submit) {
+        S->any_submit = true;
+        S->t_first_submit = q->t_submit;
+    }
+    S->submitted++;
+    S->reqs[q->id] = q;
+    *req_id = q->id;
+    if (n == 0) {
+        finish(S, q, SGR_OK);
+        return SGR_OK;
+    }
+    S->pending.push_back(q);
+    S->cv_work.notify_one();
+    return SGR_OK;
+}
+
+int sgr_server_poll(sgr_server *S, uint64_t req_id, int32_t *colors_host, int32_t *num_colors,
+                    int timeout_ms) {
+    if (!S) return SGR_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(req_id);
+    if (it == S->reqs.end()) return SGR_ERR_NOT_FOUND;
+    Request *q = it->second;
+    auto ready = [&] { return q->status != SGR_PENDING; };
+    if (timeout_ms < 0) S->cv_done.wait(lk, ready);
+    else if (timeout_ms > 0) S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+    if (q->status == SGR_PENDING) return SGR_PENDING;
+    const int status = q->status;
+    if (status == SGR_OK) {
+        if (colors_host && q->n) std::memcpy(colors_host, q->colors.data(), (size_t)q->n * 4);
+        if (num_colors) *num_colors = q->k;
+    }
+    S->reqs.erase(it);
+    delete q;
+    return status;
+}
+
+int sgr_server_stats(sgr_server *S, sgr_server_counters *out) {
+    if (!S || !out) return SGR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = S->submitted;
+    out->completed = S->completed;
+    out->failed = S->failed;
+    out->pending = (int64_t)S->pending.size();
+    out->resident = S->G - (int64_t)S->free_slots.size();
+    out->launches = S->launches;
+    out->rounds = S->rounds_run;
+    out->hbm_bytes = (int64_t)S->dbytes;
+    out->vertex_capacity = S->Vcap;
+    out->entry_capacity = S->Ecap;
+    if (!S->lat_ms.empty()) {
+        std::vector<double> v = S->lat_ms;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double p) {
+            const size_t i = (size_t)std::min<double>(v.size() - 1, std::max(0.0, p * (v.size() - 1)));
+            return v[i];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        double s = 0;
+        for (double x : v) s += x;
+        out->mean_ms = s / v.size();
+        const double span =
+            std::chrono::duration<double>(S->t_last_done - S->t_first_submit).count();
+        out->graphs_per_s = span > 0 ? S->completed / span : 0;
+    }
+    return S->fatal;
+}
+
+int sgr_server_destroy(sgr_server *S) {
+    if (!S) return SGR_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(S->device);
+    if (S->stream) cudaStreamSynchronize(S->stream);
+    if (S->dmem) cudaFree(S->dmem);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    cudaSetDevice(prev);
+    for (auto &kv : S->reqs) delete kv.second;
+    delete S;
+    return SGR_OK;
+}
+
+}  // extern "C"

@@ -38,7 +38,8 @@ RULES = {"low_keeps": SGR_RULE_LOW_KEEPS, "low_loses": SGR_RULE_LOW_LOSES,
 # every symbol include/sgrcolor.h declares (checked by the tests)
 EXPORTS = ["sgr_color", "sgr_color_noalloc", "sgr_color_host", "sgr_color_batch", "sgr_validate_csr",
            "sgr_last_stats", "sgr_last_trace", "sgr_get_tuning", "sgr_set_tuning", "sgr_release_scratch",
-           "sgr_status_string", "sgr_version"]
+           "sgr_status_string", "sgr_version", "sgr_server_create", "sgr_server_submit",
+           "sgr_server_poll", "sgr_server_stats", "sgr_server_destroy"]
 
 
 class SgrError(RuntimeError):
@@ -54,6 +55,22 @@ class Stats(ctypes.Structure):
                 ("num_colors", ctypes.c_int32),
                 ("rows_sorted", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("device_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("rounds_per_launch", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "failed", "pending",
+                                              "resident", "launches", "rounds", "hbm_bytes",
+                                              "vertex_capacity", "entry_capacity")] + \
+               [(f, ctypes.c_double) for f in ("p50_ms", "p99_ms", "mean_ms", "graphs_per_s")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -82,6 +99,11 @@ def _load():
     lib.sgr_status_string.argtypes = [ctypes.c_int]
     lib.sgr_status_string.restype = ctypes.c_char_p
     lib.sgr_version.argtypes = []
+    lib.sgr_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    lib.sgr_server_submit.argtypes = [vp, i32, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.sgr_server_poll.argtypes = [vp, ctypes.c_uint64, vp, pi32, ctypes.c_int]
+    lib.sgr_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    lib.sgr_server_destroy.argtypes = [vp]
     for name in EXPORTS:
         if name != "sgr_status_string":
             getattr(lib, name).restype = ctypes.c_int
@@ -221,6 +243,57 @@ def sgr_release_scratch() -> None:
 
 def sgr_version() -> int:
     return int(_lib.sgr_version())
+
+
+class Server:
+    """Continuous-batching coloring server (sgr_server_*): submit host CSR
+    graphs, poll for their colors."""
+
+    def __init__(self, hbm_budget_bytes=1 << 30, max_inflight=0, mode="det", device=0,
+                 rounds_per_launch=0):
+        cfg = ServerConfig(int(hbm_budget_bytes), int(max_inflight), _mode(mode), int(device),
+                           int(rounds_per_launch))
+        h = ctypes.c_void_p()
+        _check(_lib.sgr_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sgr_server_create")
+        self._h = h
+
+    def submit(self, row_offsets, col_idx) -> int:
+        import numpy as np
+        ro = np.ascontiguousarray(row_offsets, dtype=np.int32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        rid = ctypes.c_uint64(0)
+        _check(_lib.sgr_server_submit(self._h, ro.shape[0] - 1, ro.ctypes.data,
+                                      ci.ctypes.data if ci.size else None, ctypes.byref(rid)),
+               "sgr_server_submit")
+        return int(rid.value)
+
+    def poll(self, req_id: int, n: int, timeout_ms: int = -1):
+        """(colors, k) when finished, None while pending."""
+        import numpy as np
+        out = np.empty(n, dtype=np.int32)
+        k = ctypes.c_int32(0)
+        rc = _lib.sgr_server_poll(self._h, req_id, out.ctypes.data if n else None,
+                                  ctypes.byref(k), int(timeout_ms))
+        if rc == SGR_PENDING:
+            return None
+        _check(rc, "sgr_server_poll")
+        return out, int(k.value)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib.sgr_server_stats(self._h, ctypes.byref(st)), "sgr_server_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            _check(_lib.sgr_server_destroy(self._h), "sgr_server_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 # ------------------------------------------------------------ torch helpers
