@@ -473,25 +473,144 @@ def run_batch(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+def run_serve(args, rank, world, local):
+    """Served workload: an open-loop Poisson stream of requests drawn from a
+    pool of distinct-seed graphs (sizes log-uniform in [1k, 4M], the batch
+    mix's kinds), through the continuous-batching server with its HBM budget,
+    against the same requests colored one at a time by sgr_color_host (both
+    include the host-device copies)."""
+    import threading
+
+    import torch
+
+    from paper_1606_06025_gb300 import sgrcolor as lib
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    specs = gg.mix_specs(args.pool, 1000, 4000000, 7 + rank)
+    pool = [gg.mix_graph(s) for s in specs]
+    rnd = np.random.default_rng(11 + rank)
+    picks = rnd.integers(0, len(pool), size=args.requests)
+    # sequential plain path: mean time per request over the pick distribution
+    seq = []
+    for g in pool:
+        out = np.empty(g.n, dtype=np.int32)
+        lib.sgr_color_host(g.n, g.row_offsets, g.col_idx, out, "det")  # warm-up
+        t0 = time.perf_counter()
+        lib.sgr_color_host(g.n, g.row_offsets, g.col_idx, out, "det")
+        seq.append(time.perf_counter() - t0)
+    seq_mean = float(np.mean([seq[j] for j in picks]))
+    seq_gps = 1.0 / seq_mean
+    budget = int(args.budget_gb * (1 << 30))
+    results = {}
+
+    def drain(srv, ids, done):
+        for i, rid in ids:
+            got = srv.poll(rid, pool[picks[i]].n, timeout_ms=-1)
+            done[i] = (time.perf_counter(), got[1])
+
+    with lib.Server(hbm_budget_bytes=budget, mode="det") as srv:
+        # capacity: a burst of requests submitted at once
+        burst = min(args.requests, 64)
+        t0 = time.perf_counter()
+        bids = [(i, srv.submit(pool[picks[i]].row_offsets, pool[picks[i]].col_idx))
+                for i in range(burst)]
+        bdone = {}
+        drain(srv, bids, bdone)
+        capacity = burst / (time.perf_counter() - t0)
+    rate = args.rate if args.rate > 0 else 0.7 * capacity
+    gaps = rnd.exponential(1.0 / rate, size=args.requests)
+    with lib.Server(hbm_budget_bytes=budget, mode="det") as srv:
+        sub_t = {}
+        ids = []
+        lock = threading.Lock()
+        done = {}
+        t_start = time.perf_counter()
+        t_next = t_start
+
+        def poller():  # non-blocking sweeps, so each completion is seen when it happens
+            outstanding = []
+            while len(done) < args.requests:
+                with lock:
+                    outstanding.extend(ids)
+                    ids.clear()
+                still = []
+                for i, rid in outstanding:
+                    got = srv.poll(rid, pool[picks[i]].n, timeout_ms=0)
+                    if got is None:
+                        still.append((i, rid))
+                    else:
+                        done[i] = (time.perf_counter(), got[1])
+                outstanding = still
+                time.sleep(0.0002)
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        for i in range(args.requests):
+            t_next += gaps[i]
+            delay = t_next - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            g = pool[picks[i]]
+            sub_t[i] = time.perf_counter()
+            rid = srv.submit(g.row_offsets, g.col_idx)
+            with lock:
+                ids.append((i, rid))
+        th.join()
+        t_end = max(t for t, _ in done.values())
+        st = srv.stats()
+    lat = np.array([(done[i][0] - sub_t[i]) * 1e3 for i in range(args.requests)])
+    value = args.requests / (t_end - t_start)
+    if rank != 0:
+        return
+    sizes = [pool[j].n for j in picks]
+    line = {
+        "metric": "served graphs/s, p50/p99 latency", "value": value, "unit": "graphs/s",
+        "n_gpus": world, "steps": args.requests, "warmup": burst, "ms_per_step": 1e3 / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "serve", "requests": args.requests, "pool": args.pool,
+                   "sizes": "log-uniform [1k, 4M] vertices; 1/3 uniform, 1/3 R-MAT, 1/3 stencils",
+                   "arrivals": "open-loop Poisson", "arrival_rate_per_s": rate,
+                   "hbm_budget_gb": args.budget_gb, "mode": "det",
+                   "mean_vertices": float(np.mean(sizes))},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "server_p50_ms": st["p50_ms"], "server_p99_ms": st["p99_ms"],
+        "burst_capacity_graphs_per_s": capacity, "sequential_graphs_per_s": seq_gps,
+        "speedup_vs_sequential": value / seq_gps,
+        "launches": st["launches"], "rounds": st["rounds"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS) + list(BATCH_WORKLOADS),
+    ap.add_argument("--workload", choices=list(WORKLOADS) + list(BATCH_WORKLOADS) + ["serve"],
                     default="rmat20")
     ap.add_argument("--mode", choices=["det", "fast"], default="det")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--timeline", default="", help="write the per-round device timeline here")
     ap.add_argument("--tune", default="", help="light_max,chunk,blocks_per_sm (0 = default)")
+    ap.add_argument("--requests", type=int, default=600, help="serve: requests in the stream")
+    ap.add_argument("--pool", type=int, default=24, help="serve: distinct graphs drawn from")
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="serve: arrivals per second (0: 0.7 x measured capacity)")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: server HBM budget")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
     elif args.workload in BATCH_WORKLOADS:
         run_batch(args, rank, world, local)
+    elif args.workload == "serve":
+        run_serve(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 
