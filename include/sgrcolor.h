@@ -198,6 +198,8 @@ typedef struct {
     int32_t mode;              /* SGR_MODE_DETERMINISTIC | SGR_RULE_* */
     int32_t device;            /* CUDA device ordinal */
     int32_t rounds_per_launch; /* rounds advanced per launch (0: 8 while requests wait, else 64) */
+    int64_t staging_bytes;     /* pinned host memory for request copies (0: 1 GiB, < 0: none);
+                                  requests that do not fit use ordinary memory */
 } sgr_server_config;
 
 typedef struct {

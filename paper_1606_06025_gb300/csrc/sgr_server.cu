@@ -84,14 +84,22 @@ struct RangeAlloc {
     }
 };
 
+// Host copy of a request's CSR ([row offsets | col_idx]) and later of its
+// colors: in the server's pinned staging pool when there is room (the copies
+// to and from the device are then asynchronous), in ordinary memory otherwise.
+struct HostBuf {
+    int32_t *ptr = nullptr;
+    long long off = -1, len = 0;  // range in the pinned pool, off < 0: in vec
+    std::vector<int32_t> vec;
+};
+
 struct Request {
     uint64_t id = 0;
     int32_t n = 0;
     long long m = 0;
-    std::vector<int32_t> ro, ci;
+    HostBuf csr, out;
     Clock::time_point t_submit, t_done;
     int status = SGR_PENDING;
-    std::vector<int32_t> colors;
     int32_t k = 0;
     int slot = -1;
     long long vb = 0, eb = 0, rb = 0;
@@ -121,7 +129,11 @@ struct sgr_server {
     sgr::Params P{};
     long long *vbase_d = nullptr, *ebase_d = nullptr, *robase_d = nullptr;
     int32_t *nv_d = nullptr, *rem_d = nullptr, *kmax_d = nullptr;
-    std::vector<int32_t> rem_h, kmax_h;
+    int32_t *pinned = nullptr;    // staging pool (int32 words)
+    RangeAlloc pa;                // ranges of the staging pool
+    long long *tab_h = nullptr;   // pinned mirrors: vbase, ebase, robase (G each)
+    int32_t *nv_h = nullptr, *rem_h = nullptr, *kmax_h = nullptr;
+    sgr::Counters *ctr_h = nullptr;
     long long round = 1;
     // statistics
     std::vector<double> lat_ms;
@@ -247,6 +259,27 @@ void finish(sgr_server *S, Request *q, int status) {
     S->cv_done.notify_all();
 }
 
+// caller holds S->mu
+void host_alloc(sgr_server *S, HostBuf &b, long long words) {
+    b.len = words;
+    b.off = words > 0 ? S->pa.alloc(words) : -1;
+    if (b.off >= 0) {
+        b.ptr = S->pinned + b.off;
+    } else {
+        b.vec.resize((size_t)std::max<long long>(words, 1));
+        b.ptr = b.vec.data();
+    }
+}
+
+// caller holds S->mu
+void host_free(sgr_server *S, HostBuf &b) {
+    if (b.off >= 0) S->pa.release(b.off, b.len);
+    b.off = -1;
+    b.len = 0;
+    b.ptr = nullptr;
+    std::vector<int32_t>().swap(b.vec);
+}
+
 void release_slot(sgr_server *S, Request *q) {
     // caller holds S->mu
     S->va.release(q->vb, q->n);
@@ -269,7 +302,6 @@ void fail_all_resident(sgr_server *S, int status) {
 
 void worker_loop(sgr_server *S) {
     cudaSetDevice(S->device);
-    const int32_t zero = 0;
     for (;;) {
         std::vector<Request *> admitted;
         int resident = 0;
@@ -306,41 +338,52 @@ void worker_loop(sgr_server *S) {
         cudaStream_t st = S->stream;
         cudaError_t e = cudaSuccess;
         const int par = (int)(S->round & 1);
-        for (Request *q : admitted) {
+        const int G = S->G;
+        for (Request *q : admitted) {  // copy the CSR into the arenas (async from pinned staging)
             const int g = q->slot;
+            S->tab_h[g] = q->vb;
+            S->tab_h[G + g] = q->eb;
+            S->tab_h[2 * G + g] = q->rb;
+            S->nv_h[g] = q->n;
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync((int32_t *)S->P.ro + q->rb, q->ro.data(), ((size_t)q->n + 1) * 4,
+                e = cudaMemcpyAsync((int32_t *)S->P.ro + q->rb, q->csr.ptr, ((size_t)q->n + 1) * 4,
                                     cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess && q->m > 0)
-                e = cudaMemcpyAsync((int32_t *)S->P.ci + q->eb, q->ci.data(), (size_t)q->m * 4,
-                                    cudaMemcpyHostToDevice, st);
-            const long long vb = q->vb, eb = q->eb, rb = q->rb;
-            const int32_t nv = q->n;
-            if (e == cudaSuccess) e = cudaMemcpyAsync(S->vbase_d + g, &vb, 8, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(S->ebase_d + g, &eb, 8, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(S->robase_d + g, &rb, 8, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(S->nv_d + g, &nv, 4, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host sources above live on this frame
-            if (e == cudaSuccess) e = sgr::launch_admit(S->P, g, vb, nv, par, S->sms * 4, st);
+                e = cudaMemcpyAsync((int32_t *)S->P.ci + q->eb, q->csr.ptr + q->n + 1,
+                                    (size_t)q->m * 4, cudaMemcpyHostToDevice, st);
         }
-        int R = S->cfg.rounds_per_launch > 0 ? S->cfg.rounds_per_launch : (have_pending ? 8 : 64);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S->vbase_d, S->tab_h, (size_t)G * 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S->ebase_d, S->tab_h + G, (size_t)G * 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S->robase_d, S->tab_h + 2 * G, (size_t)G * 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S->nv_d, S->nv_h, (size_t)G * 4, cudaMemcpyHostToDevice, st);
+        for (Request *q : admitted)
+            if (e == cudaSuccess) e = sgr::launch_admit(S->P, q->slot, q->vb, q->n, par, S->sms * 4, st);
+        const int R = S->cfg.rounds_per_launch > 0 ? S->cfg.rounds_per_launch : (have_pending ? 8 : 64);
         sgr::Params P = S->P;
         P.rounds_per_launch = R;
         P.nblocks = (unsigned)S->grid;
         // fresh barrier and error state for this launch
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(&P.ctr->bar_count, 0, 2 * sizeof(unsigned), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&P.ctr->bar_count, 0, 2 * sizeof(unsigned), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(&P.ctr->err, 0, sizeof(int), st);
         if (e == cudaSuccess) e = sgr::launch_color(P, false, true, S->grid, st);
         if (e == cudaSuccess)
-            e = sgr::launch_slot_status(P.colors, S->vbase_d, S->nv_d, S->G, S->rem_d, S->kmax_d, st);
-        sgr::Counters h;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, P.ctr, sizeof(h), cudaMemcpyDeviceToHost, st);
+            e = sgr::launch_slot_status(P.colors, S->vbase_d, S->nv_d, G, S->rem_d, S->kmax_d, st);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(S->rem_h.data(), S->rem_d, (size_t)S->G * 4, cudaMemcpyDeviceToHost, st);
+            e = cudaMemcpyAsync(S->ctr_h, P.ctr, sizeof(sgr::Counters), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(S->kmax_h.data(), S->kmax_d, (size_t)S->G * 4, cudaMemcpyDeviceToHost, st);
+            e = cudaMemcpyAsync(S->rem_h, S->rem_d, (size_t)G * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S->kmax_h, S->kmax_d, (size_t)G * 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (!admitted.empty()) {  // their CSR is on the device now
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (Request *q : admitted) host_free(S, q->csr);
+        }
+        const sgr::Counters h = *S->ctr_h;
         if (e != cudaSuccess || h.err != 0) {
             const int status = e != cudaSuccess ? map_err(e) : h.err;
             {
@@ -357,20 +400,27 @@ void worker_loop(sgr_server *S) {
         S->round = h.round;
         // Retire finished graphs, unless a hub's color still waits to be
         // scattered into neighbour bitmaps (its range must not be reused yet).
+        // A resident graph always finishes: in every round the worklist vertex
+        // that wins against all its neighbours under the rule keeps its color.
         if (h.sc64 != 0) continue;
-        for (int g = 0; g < S->G; ++g) {
+        std::vector<Request *> retiring;
+        for (int g = 0; g < G; ++g) {
             Request *q = S->slot_req[g];
-            if (!q) continue;
-            // A resident graph always finishes: in every round the worklist vertex that
-            // wins against all its neighbours under the rule keeps its color.
-            if (S->rem_h[g] != 0) continue;
-            q->colors.resize(q->n);
-            e = cudaMemcpyAsync(q->colors.data(), P.colors + q->vb, (size_t)q->n * 4,
-                                cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(S->nv_d + g, &zero, 4, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (!q || S->rem_h[g] != 0) continue;
+            retiring.push_back(q);
             q->k = S->kmax_h[g];
-            std::lock_guard<std::mutex> lk(S->mu);
+            S->nv_h[g] = 0;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                host_alloc(S, q->out, q->n);
+            }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(q->out.ptr, P.colors + q->vb, (size_t)q->n * 4, cudaMemcpyDeviceToHost, st);
+        }
+        if (retiring.empty()) continue;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (Request *q : retiring) {
             release_slot(S, q);
             finish(S, q, e != cudaSuccess ? map_err(e) : SGR_OK);
         }
@@ -393,6 +443,8 @@ int sgr_server_create(const sgr_server_config *cfg, sgr_server **out) {
     sgr_server *S = new sgr_server();
     S->cfg = *cfg;
     if (S->cfg.hbm_budget_bytes == 0) S->cfg.hbm_budget_bytes = 1ll << 30;
+    if (S->cfg.staging_bytes == 0) S->cfg.staging_bytes = 1ll << 30;
+    if (S->cfg.staging_bytes < 0) S->cfg.staging_bytes = 0;
     S->G = S->cfg.max_inflight > 0 ? S->cfg.max_inflight : 1024;
     S->device = cfg->device;
     int rc = SGR_OK;
@@ -410,15 +462,33 @@ int sgr_server_create(const sgr_server_config *cfg, sgr_server **out) {
         rc = SGR_ERR_CUDA;
     if (rc == SGR_OK) rc = carve(S);
     if (rc == SGR_OK) {
+        const long long words = S->cfg.staging_bytes / 4;
+        const size_t mirror = (size_t)S->G * (3 * 8 + 3 * 4) + sizeof(sgr::Counters) + 256;
+        char *m = nullptr;
+        if (cudaMallocHost(&m, mirror) != cudaSuccess) rc = SGR_ERR_OUT_OF_MEMORY;
+        else {
+            std::memset(m, 0, mirror);
+            S->tab_h = (long long *)m;
+            S->nv_h = (int32_t *)(m + (size_t)S->G * 24);
+            S->rem_h = S->nv_h + S->G;
+            S->kmax_h = S->rem_h + S->G;
+            S->ctr_h = (sgr::Counters *)(((uintptr_t)(S->kmax_h + S->G) + 255) & ~(uintptr_t)255);
+        }
+        if (rc == SGR_OK && words > 0) {
+            if (cudaMallocHost(&S->pinned, (size_t)words * 4) != cudaSuccess) rc = SGR_ERR_OUT_OF_MEMORY;
+            else S->pa.init(words);
+        }
+    }
+    if (rc == SGR_OK) {
         S->slot_req.assign(S->G, nullptr);
         for (int g = S->G - 1; g >= 0; --g) S->free_slots.push_back(g);
-        S->rem_h.assign(S->G, 0);
-        S->kmax_h.assign(S->G, 0);
         S->worker = std::thread(worker_loop, S);
     }
     cudaSetDevice(prev);
     if (rc != SGR_OK) {
         if (S->dmem) cudaFree(S->dmem);
+        if (S->pinned) cudaFreeHost(S->pinned);
+        if (S->tab_h) cudaFreeHost(S->tab_h);
         if (S->stream) cudaStreamDestroy(S->stream);
         delete S;
         return rc;
@@ -433,27 +503,43 @@ int sgr_server_submit(sgr_server *S, int32_t n, const int32_t *ro, const int32_t
     const long long m = n > 0 ? ro[n] : 0;
     if (n > 0 && (ro[0] != 0 || m < 0)) return SGR_ERR_INVALID_GRAPH;
     if (m > 0 && !ci) return SGR_ERR_INVALID_ARG;
+    for (int32_t v = 0; v < n; ++v)
+        if (ro[v + 1] < ro[v] || ro[v + 1] > m) return SGR_ERR_INVALID_GRAPH;
+    if (n > S->Vcap || m > S->Ecap) return SGR_ERR_OUT_OF_MEMORY;
     Request *q = new Request();
     q->n = n;
     q->m = m;
+    auto reject = [&](int status) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        host_free(S, q->csr);
+        delete q;
+        return status;
+    };
     if (n > 0) {
-        q->ro.assign(ro, ro + n + 1);
-        q->ci.assign(ci, ci + m);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            host_alloc(S, q->csr, (long long)n + 1 + m);
+        }
+        int32_t *hro = q->csr.ptr, *hci = q->csr.ptr + n + 1;
+        std::memcpy(hro, ro, ((size_t)n + 1) * 4);
+        if (m) std::memcpy(hci, ci, (size_t)m * 4);
         for (int32_t v = 0; v < n; ++v) {
-            const int32_t a = ro[v], b = ro[v + 1];
-            if (b < a || b > m) { delete q; return SGR_ERR_INVALID_GRAPH; }
+            const int32_t a = hro[v], b = hro[v + 1];
             bool asc = true;
             for (int32_t i = a; i < b; ++i) {
-                const int32_t w = q->ci[i];
-                if (w < 0 || w >= n || w == v) { delete q; return SGR_ERR_INVALID_GRAPH; }
-                if (i > a && q->ci[i - 1] >= w) asc = false;
+                const int32_t w = hci[i];
+                if (w < 0 || w >= n || w == v) return reject(SGR_ERR_INVALID_GRAPH);
+                if (i > a && hci[i - 1] >= w) asc = false;
             }
-            if (!asc) std::sort(q->ci.begin() + a, q->ci.begin() + b);  // order within a row is free
+            if (!asc) std::sort(hci + a, hci + b);  // the order within a row is free
         }
     }
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->fatal != SGR_OK) { delete q; return S->fatal; }
-    if (n > S->Vcap || m > S->Ecap) { delete q; return SGR_ERR_OUT_OF_MEMORY; }
+    if (S->fatal != SGR_OK) {
+        host_free(S, q->csr);
+        delete q;
+        return S->fatal;
+    }
     q->id = S->next_id++;
     q->t_submit = Clock::now();
     if (!S->any_submit) {
@@ -485,9 +571,11 @@ int sgr_server_poll(sgr_server *S, uint64_t req_id, int32_t *colors_host, int32_
     if (q->status == SGR_PENDING) return SGR_PENDING;
     const int status = q->status;
     if (status == SGR_OK) {
-        if (colors_host && q->n) std::memcpy(colors_host, q->colors.data(), (size_t)q->n * 4);
+        if (colors_host && q->n) std::memcpy(colors_host, q->out.ptr, (size_t)q->n * 4);
         if (num_colors) *num_colors = q->k;
     }
+    host_free(S, q->out);
+    host_free(S, q->csr);
     S->reqs.erase(it);
     delete q;
     return status;
@@ -539,9 +627,11 @@ int sgr_server_destroy(sgr_server *S) {
     cudaSetDevice(S->device);
     if (S->stream) cudaStreamSynchronize(S->stream);
     if (S->dmem) cudaFree(S->dmem);
+    if (S->pinned) cudaFreeHost(S->pinned);
+    if (S->tab_h) cudaFreeHost(S->tab_h);
     if (S->stream) cudaStreamDestroy(S->stream);
     cudaSetDevice(prev);
-    for (auto &kv : S->reqs) delete kv.second;
+    for (auto &kv : S->reqs) delete kv.second;  // their pinned ranges go with the pool
     delete S;
     return SGR_OK;
 }

@@ -63,7 +63,7 @@ class Stats(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("rounds_per_launch", ctypes.c_int32)]
+                ("rounds_per_launch", ctypes.c_int32), ("staging_bytes", ctypes.c_int64)]
 
 
 class ServerStats(ctypes.Structure):
@@ -250,9 +250,9 @@ class Server:
     graphs, poll for their colors."""
 
     def __init__(self, hbm_budget_bytes=1 << 30, max_inflight=0, mode="det", device=0,
-                 rounds_per_launch=0):
+                 rounds_per_launch=0, staging_bytes=0):
         cfg = ServerConfig(int(hbm_budget_bytes), int(max_inflight), _mode(mode), int(device),
-                           int(rounds_per_launch))
+                           int(rounds_per_launch), int(staging_bytes))
         h = ctypes.c_void_p()
         _check(_lib.sgr_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sgr_server_create")
         self._h = h
