@@ -221,10 +221,11 @@ typedef struct {
 int sgr_server_create(const sgr_server_config *cfg, sgr_server **out);
 
 /* Queue one graph (HOST CSR, same contract as sgr_color; rows need not be
- * sorted).  The CSR is copied; the caller may free it on return.  Checks
- * offsets, id range and self-loops (SGR_ERR_INVALID_GRAPH); a graph larger
- * than the server's capacity gives SGR_ERR_OUT_OF_MEMORY.  *req_id receives a
- * fresh id.  Thread-safe. */
+ * sorted, self-loop entries are ignored).  The CSR is copied (into the pinned
+ * staging pool when it has room); the caller may free it on return.  Checks
+ * offsets and the id range (SGR_ERR_INVALID_GRAPH); a graph larger than the
+ * server's capacity gives SGR_ERR_OUT_OF_MEMORY.  *req_id receives a fresh
+ * id.  Thread-safe. */
 int sgr_server_submit(sgr_server *s, int32_t n, const int32_t *row_offsets_host,
                       const int32_t *col_idx_host, uint64_t *req_id);
 

@@ -522,17 +522,24 @@ int sgr_server_submit(sgr_server *S, int32_t n, const int32_t *ro, const int32_t
         }
         int32_t *hro = q->csr.ptr, *hci = q->csr.ptr + n + 1;
         std::memcpy(hro, ro, ((size_t)n + 1) * 4);
-        if (m) std::memcpy(hci, ci, (size_t)m * 4);
+        // One pass: copy col_idx, count ids outside [0, n) and adjacent
+        // descending pairs; rows are ascending iff every descending pair sits
+        // on a row boundary.
+        long long bad = 0, desc = 0, bnd = 0;
+        const uint32_t un = (uint32_t)n;
+        for (long long i = 0; i < m; ++i) {
+            const int32_t w = ci[i];
+            hci[i] = w;
+            bad += (uint32_t)w >= un;
+            desc += (i + 1 < m) & (w >= ci[i + 1 < m ? i + 1 : i]);
+        }
+        if (bad) return reject(SGR_ERR_INVALID_GRAPH);
         for (int32_t v = 0; v < n; ++v) {
             const int32_t a = hro[v], b = hro[v + 1];
-            bool asc = true;
-            for (int32_t i = a; i < b; ++i) {
-                const int32_t w = hci[i];
-                if (w < 0 || w >= n || w == v) return reject(SGR_ERR_INVALID_GRAPH);
-                if (i > a && hci[i - 1] >= w) asc = false;
-            }
-            if (!asc) std::sort(hci + a, hci + b);  // the order within a row is free
+            if (b > a && b < m) bnd += hci[b - 1] >= hci[b];
         }
+        if (desc != bnd)  // some row is not ascending: sort rows (the order within a row is free)
+            for (int32_t v = 0; v < n; ++v) std::sort(hci + hro[v], hci + hro[v + 1]);
     }
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->fatal != SGR_OK) {

@@ -113,9 +113,13 @@ def test_server_edge_cases(gpu_lib):
         k = ctypes.c_int32(0)
         assert gpu_lib._lib.sgr_server_poll(srv._h, 987654321, None, ctypes.byref(k), 0) == \
             gpu_lib.SGR_ERR_NOT_FOUND
+        # a self-loop entry is ignored: vertex 0 still gets color 1
+        rid = srv.submit(np.array([0, 1, 1], dtype=np.int32), np.array([0], dtype=np.int32))
+        colors, k = srv.poll(rid, 2, timeout_ms=10000)
+        assert list(colors) == [1, 1] and k == 1
         # invalid graphs
         with pytest.raises(gpu_lib.SgrError) as e:
-            srv.submit(np.array([0, 1, 1], dtype=np.int32), np.array([0], dtype=np.int32))  # self-loop
+            srv.submit(np.array([0, 2, 1], dtype=np.int32), np.array([1, 0], dtype=np.int32))  # offsets
         assert e.value.status == gpu_lib.SGR_ERR_INVALID_GRAPH
         with pytest.raises(gpu_lib.SgrError) as e:
             srv.submit(np.array([0, 1, 2], dtype=np.int32), np.array([1, 5], dtype=np.int32))  # id 5 >= n
