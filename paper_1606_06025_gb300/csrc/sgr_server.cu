@@ -522,17 +522,17 @@ int sgr_server_submit(sgr_server *S, int32_t n, const int32_t *ro, const int32_t
         }
         int32_t *hro = q->csr.ptr, *hci = q->csr.ptr + n + 1;
         std::memcpy(hro, ro, ((size_t)n + 1) * 4);
-        // One pass: copy col_idx, count ids outside [0, n) and adjacent
-        // descending pairs; rows are ascending iff every descending pair sits
-        // on a row boundary.
+        // Copy col_idx, then count ids outside [0, n) and adjacent descending
+        // pairs; rows are ascending iff every descending pair sits on a row
+        // boundary.
+        if (m) std::memcpy(hci, ci, (size_t)m * 4);
         long long bad = 0, desc = 0, bnd = 0;
         const uint32_t un = (uint32_t)n;
-        for (long long i = 0; i < m; ++i) {
-            const int32_t w = ci[i];
-            hci[i] = w;
-            bad += (uint32_t)w >= un;
-            desc += (i + 1 < m) & (w >= ci[i + 1 < m ? i + 1 : i]);
+        for (long long i = 0; i + 1 < m; ++i) {
+            bad += (uint32_t)hci[i] >= un;
+            desc += hci[i] >= hci[i + 1];
         }
+        if (m) bad += (uint32_t)hci[m - 1] >= un;
         if (bad) return reject(SGR_ERR_INVALID_GRAPH);
         for (int32_t v = 0; v < n; ++v) {
             const int32_t a = hro[v], b = hro[v + 1];
