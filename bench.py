@@ -260,6 +260,9 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     mode = args.mode
+    tuned = None
+    if args.autotune:
+        tuned, tuned_ms = lib.sgr_autotune(n, ro, ci, colors, mode, 3000, stream)
 
     def step():
         return lib.sgr_color(n, ro, ci, colors, mode, stream)
@@ -340,6 +343,7 @@ def run_ours(args, rank, world, local):
         "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "n": n, "m": m, "mode": mode,
                    "tuning": lib.sgr_get_tuning(),
+                   "tuning_source": "autotuned" if tuned else ("--tune" if args.tune else "default"),
                    "l2": "flushed (512 MiB write) before every step",
                    "parallelism": f"replicas x{world}"},
         "num_colors": k, "rounds": st["rounds"], "sum_d": st["sum_d"],
@@ -662,6 +666,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--timeline", default="", help="write the per-round device timeline here")
     ap.add_argument("--tune", default="", help="light_max,chunk,blocks_per_sm (0 = default)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="measure the tuning candidates on the workload before timing")
     ap.add_argument("--requests", type=int, default=600, help="serve: requests in the stream")
     ap.add_argument("--pool", type=int, default=24, help="serve: distinct graphs drawn from")
     ap.add_argument("--rate", type=float, default=0.0,

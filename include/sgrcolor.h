@@ -254,6 +254,21 @@ int sgr_server_destroy(sgr_server *s);
 int sgr_validate_csr(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
                      int32_t *rows_sorted, sgr_stream_t stream);
 
+/*
+ * Pick the tuning for a graph by measurement: color it (sgr_color, device
+ * buffers) under a grid of candidates -- degree bound of the lane-per-vertex
+ * bin {32, 16}, hub chunk size {512, 256, 1024, 2048}, CTAs per SM {all, 2},
+ * best of two runs each by the kernel's event time -- until budget_ms of
+ * device time is spent (0: 2000 ms; at least one candidate always runs).  The
+ * fastest candidate becomes the process-wide tuning and is returned in *best
+ * (HOST) with its time in *best_ms (HOST, may be NULL).  colors_out receives
+ * a valid coloring.  The paper leaves autotuning out of its scope (Sect. 3.2,
+ * thread coarsening).  Errors as sgr_color; the tuning is restored on error.
+ */
+int sgr_autotune(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
+                 int32_t *colors_out, int mode, int32_t budget_ms, sgr_tuning *best,
+                 double *best_ms, sgr_stream_t stream);
+
 /* Statistics of the last sgr_color / sgr_color_host / sgr_color_batch call
  * on this host thread. */
 int sgr_last_stats(sgr_stats *out);

@@ -548,6 +548,55 @@ int sgr_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
     return SGR_OK;
 }
 
+int sgr_autotune(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
+                 int32_t *colors_out, int mode, int32_t budget_ms, sgr_tuning *best,
+                 double *best_ms, sgr_stream_t stream) {
+    if (!best || !valid_mode(mode) || n < 0) return SGR_ERR_INVALID_ARG;
+    const sgr_tuning start = current_tuning();
+    if (n == 0) {
+        *best = start;
+        if (best_ms) *best_ms = 0;
+        return SGR_OK;
+    }
+    // Candidates: degree bound of the lane-per-vertex bin, hub chunk size (also
+    // the warp-per-vertex bound) and CTAs per SM (0 = as many as fit).
+    const int32_t lights[] = {32, 16};
+    const int32_t chunks[] = {512, 256, 1024, 2048};
+    const int32_t ctas[] = {0, 2};
+    const double budget = budget_ms > 0 ? budget_ms : 2000.0;
+    double spent = 0, best_t = 1e300;
+    sgr_tuning bt = start;
+    int32_t k = 0;
+    int tried = 0;
+    for (int32_t b : ctas)
+        for (int32_t c : chunks)
+            for (int32_t l : lights) {
+                if (tried > 0 && spent > budget) continue;
+                sgr_tuning t = {l, c, b, 0};
+                int rc = sgr_set_tuning(&t);
+                if (rc != SGR_OK) continue;
+                double tmin = 1e300;
+                for (int rep = 0; rep < 2; ++rep) {  // the first run also warms caches
+                    rc = sgr_color(n, row_offsets, col_idx, colors_out, &k, mode, stream);
+                    if (rc != SGR_OK) {
+                        sgr_set_tuning(&start);
+                        return rc;
+                    }
+                    tmin = std::min(tmin, t_stats.device_ms);
+                    spent += t_stats.device_ms;
+                }
+                ++tried;
+                if (tmin < best_t) {
+                    best_t = tmin;
+                    bt = t;
+                }
+            }
+    sgr_set_tuning(&bt);
+    *best = bt;
+    if (best_ms) *best_ms = best_t;
+    return SGR_OK;
+}
+
 int sgr_validate_csr(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
                      int32_t *rows_sorted, sgr_stream_t stream) {
     if (n < 0) return SGR_ERR_INVALID_ARG;
