@@ -66,6 +66,24 @@ def dist_env():
     return rank, world, local
 
 
+def shard(items, rank, world):
+    """The share of independent work items (graphs) a rank colors: every
+    world-th item, so each item is colored by exactly one rank."""
+    return list(items)[rank::world]
+
+
+def max_over_ranks(value, device=None):
+    """Largest value over all ranks (the job's time is the slowest rank's);
+    the identity when no process group is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -292,11 +310,8 @@ def run_ours(args, rank, world, local):
         kern_ms.append(st["device_ms"])
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), dev)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     st = stats[-1]
     work = st["sum_d"] * args.steps * world
@@ -322,11 +337,7 @@ def run_ours(args, rank, world, local):
         e1.synchronize()
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_ms) if e2e_ms else float("nan")
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_ms) if e2e_ms else float("nan"), dev)
     e2e_value = st["sum_d"] * args.steps * world / (e2e_total * 1e-3) / 1e9
     if rank != 0:
         if world > 1:
@@ -393,7 +404,7 @@ def run_batch(args, rank, world, local):
     desc, make = BATCH_WORKLOADS[args.workload]
     b = make()
     if world > 1:  # shard the graphs by rank: no exchange on the data path
-        b = gg.pack(b.graphs[rank::world])
+        b = gg.pack(shard(b.graphs, rank, world))
     n, m, G = int(b.vtx_off[-1]), int(b.edge_off[-1]), b.G
     ro = torch.from_numpy(b.row_offsets).to(dev)
     ci = torch.from_numpy(b.col_idx).to(dev)
@@ -426,11 +437,7 @@ def run_batch(args, rank, world, local):
         ms.append(e0.elapsed_time(e1))
     clocks = sampler.stop()
     st = lib.sgr_last_stats()
-    total = sum(ms)
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(sum(ms), dev)
     value = G * world * args.steps / (total * 1e-3)
     # the plain path: one sgr_color per graph, same graphs, same device buffers
     seq_ms = []
@@ -487,7 +494,7 @@ def run_serve_burst(args, rank, world, local):
 
     torch.cuda.set_device(local)
     b = gg.batch_mix(512, 1000, 200000, 0)
-    graphs = b.graphs[rank::world]
+    graphs = shard(b.graphs, rank, world)
     outs = [np.empty(g.n, dtype=np.int32) for g in graphs]
     for g, o in zip(graphs[:8], outs):  # warm-up
         lib.sgr_color_host(g.n, g.row_offsets, g.col_idx, o, "det")
