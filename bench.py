@@ -59,6 +59,24 @@ BATCH_WORKLOADS = {
 }
 
 
+def workload(name):
+    """(description, maker) for a named workload, including the parametric
+    er:N:D (uniform random graph, n = N, average degree D, seed 0) and
+    rmat:S (R-MAT scale S, edge factor 16, the rmat20 parameters)."""
+    if name in WORKLOADS:
+        return WORKLOADS[name]
+    parts = name.split(":")
+    if parts[0] == "er" and len(parts) == 3:
+        n, d = int(parts[1]), float(parts[2])
+        return (f"uniform random graph n={n}, average degree {d:g}, seed 0",
+                lambda: gg.uniform(n, d, 0))
+    if parts[0] == "rmat" and len(parts) == 2:
+        sc = int(parts[1])
+        return (f"RMAT scale {sc}, edge factor 16, (0.57,0.19,0.19,0.05), seed 0",
+                lambda: gg.rmat(sc, 16, (0.57, 0.19, 0.19), 0))
+    raise SystemExit(f"unknown workload {name}")
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -225,7 +243,7 @@ def oracle_baseline(g, budget_s=12.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    desc, make = WORKLOADS[args.workload]
+    desc, make = workload(args.workload)
     g = make()
     import oracle
     # warm-up and timed steps: each step is one full det-SGR run of the oracle
@@ -269,7 +287,7 @@ def run_ours(args, rank, world, local):
     if args.tune:
         lm, ch, bps = (int(x) for x in args.tune.split(","))
         lib.sgr_set_tuning(light_max=lm, chunk=ch, blocks_per_sm=bps)
-    desc, make = WORKLOADS[args.workload]
+    desc, make = workload(args.workload)
     g = make()
     n, m = g.n, g.m
     ro = torch.from_numpy(g.row_offsets).to(dev)
@@ -277,7 +295,7 @@ def run_ours(args, rank, world, local):
     colors = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    mode = args.mode
+    mode = args.mode + "+" + args.rule
     tuned = None
     if args.autotune:
         tuned, tuned_ms = lib.sgr_autotune(n, ro, ci, colors, mode, 3000, stream)
@@ -345,15 +363,15 @@ def run_ours(args, rank, world, local):
         return
     peak, peak_src = read_peaks()
     kmean = statistics.mean(kern_ms)
-    ab = alg_bytes(st, n, m, mode)
+    ab = alg_bytes(st, n, m, args.mode)
     achieved = ab / (kmean * 1e-3) / 1e9
     line = {
         "metric": METRIC_SINGLE, "value": value, "unit": "GTEPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "n": n, "m": m, "mode": mode,
-                   "tuning": lib.sgr_get_tuning(),
+        "config": {"workload": args.workload, "description": desc, "n": n, "m": m,
+                   "mode": args.mode, "rule": args.rule, "tuning": lib.sgr_get_tuning(),
                    "tuning_source": "autotuned" if tuned else ("--tune" if args.tune else "default"),
                    "l2": "flushed (512 MiB write) before every step",
                    "parallelism": f"replicas x{world}"},
@@ -364,7 +382,7 @@ def run_ours(args, rank, world, local):
                 "h2d_bytes_per_step": 4 * (n + 1) + 4 * m, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": args.steps * 1,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": read_traffic(args.workload, mode),
+                     "frac": achieved / peak, "traffic": read_traffic(args.workload, args.mode) if args.rule == "low_keeps" else None,
                      "alg_bytes_per_launch": ab, "kernel_ms": kmean,
                      "kernel": "sgr_color_kernel", "peak_source": peak_src + " of measured"
                      if peak_src.startswith("measured") else peak_src},
@@ -381,7 +399,7 @@ def run_ours(args, rank, world, local):
         line["serial_greedy_colors"] = k_serial
         line["colors_vs_serial"] = k / k_serial if k_serial else None
         line["speedup_vs_serial_greedy"] = t_serial * 1e3 / (total_ms / args.steps)
-        if mode == "det":
+        if args.mode == "det" and args.rule == "low_keeps":
             line["det_matches_oracle"] = bool(
                 np.array_equal(colors.cpu().numpy(), r.colors))
     print(json.dumps(line), flush=True)
@@ -665,10 +683,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload",
-                    choices=list(WORKLOADS) + list(BATCH_WORKLOADS) + ["serve", "serve512"],
-                    default="rmat20")
+    ap.add_argument("--workload", default="rmat20",
+                    help="rmat20 | stencil192 | er20k | stencil128 | batch512 | batch64 | serve | "
+                         "serve512 | er:N:D | rmat:S")
     ap.add_argument("--mode", choices=["det", "fast"], default="det")
+    ap.add_argument("--rule", choices=["low_keeps", "low_loses", "degree"], default="low_keeps",
+                    help="loser rule (Sect. 3.2 heuristic = degree; Alg. 5 as printed = low_loses)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--timeline", default="", help="write the per-round device timeline here")
