@@ -195,6 +195,11 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     unsigned *hcb0 = (unsigned *)take(sp.hub_max * 4), *hcb1 = (unsigned *)take(sp.hub_max * 4);
     int32_t *hvert = (int32_t *)take(sp.hub_max * 4);
     unsigned *hbase = (unsigned *)take(sp.hub_max * 4);
+    const size_t un = j.fast ? 1 : (size_t)j.n, uhub = j.fast ? 1 : sp.hub_max;
+    int32_t *ul0 = (int32_t *)take(un * 4), *ul1 = (int32_t *)take(un * 4);
+    int32_t *um0 = (int32_t *)take(un * 4), *um1 = (int32_t *)take(un * 4);
+    int32_t *uh0 = (int32_t *)take(uhub * 4), *uh1 = (int32_t *)take(uhub * 4);
+    unsigned *ucb0 = (unsigned *)take(uhub * 4), *ucb1 = (unsigned *)take(uhub * 4);
     if (p && base) {
         std::memset(p, 0, sizeof(*p));
         p->ro = j.ro;
@@ -210,6 +215,10 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         p->mw[0] = mw0; p->mw[1] = mw1;
         p->hw[0] = hw0; p->hw[1] = hw1;
         p->hcb[0] = hcb0; p->hcb[1] = hcb1;
+        p->ul[0] = ul0; p->ul[1] = ul1;
+        p->um[0] = um0; p->um[1] = um1;
+        p->uh[0] = uh0; p->uh[1] = uh1;
+        p->ucb[0] = ucb0; p->ucb[1] = ucb1;
         p->hvert = hvert;
         p->hbase = hbase;
         p->hbits = hbits;

@@ -8,6 +8,8 @@
 //                        round parity (Algorithm 7's W_in / W_out swap).
 //   medium lists mw[2]   vertex ids of degree in (light_max, chunk].
 //   hub lists hw[2]      hub slot ids (degree > chunk) + chunk base hcb[2].
+//   det unsettled lists  ul/um/uh(+ucb), by parity: the part of W_r whose
+//                        witness did not settle it in FirstFit, for ConflictResolve.
 //   hub slots            hvert (slot -> vertex), hbase (offset of the slot's
 //                        forbidden-color bitmap in hbits, fast mode), hdone /
 //                        hconf (per-round completion counter and conflict flag).
@@ -48,6 +50,8 @@ struct Counters {
     unsigned int nl[2];             // light list sizes by round parity
     unsigned int nm[2];             // medium list sizes
     unsigned long long h64[2];      // hub lists: (entries << 32) | total chunks
+    unsigned int nul[2], num[2];    // det: unsettled light / medium vertices of the round
+    unsigned long long uh64[2];     // det: unsettled hubs (entries << 32 | chunks)
     unsigned int bar_count;         // grid barrier arrivals
     unsigned int bar_gen;           // grid barrier generation
     unsigned int nslots;            // hub slots handed out
@@ -79,6 +83,10 @@ struct Params {
     int32_t *mw[2];
     int32_t *hw[2];
     unsigned int *hcb[2];
+    int32_t *ul[2];            // det: light vertices the witness did not settle (parity of r)
+    int32_t *um[2];            // det: medium vertices the witness did not settle
+    int32_t *uh[2];            // det: hub slots the witness did not settle
+    unsigned int *ucb[2];      // det: their chunk bases
     int32_t *hvert;
     unsigned int *hbase;
     unsigned int *hbits;

@@ -317,63 +317,147 @@ __device__ __forceinline__ void hub_list_push(unsigned long long *ctr64, int32_t
 
 // ------------------------------------------------------------ det: FirstFit
 
-// Phase A of det mode over one list (vertex ids, or hub slots when `slots`).
-// Each warp takes 128 consecutive entries, four per lane, with all loads of
-// a stage in flight together.
-template <bool kBatched>
-__device__ void det_assign(const Params &p, const int32_t *list, unsigned cnt, bool slots) {
-    constexpr int U = 4;
+// ------------------------------------------------------------ det: FirstFit with witness split
+//
+// During FirstFit every bitmap is fixed, so a vertex can compute the
+// tentative color of any other worklist vertex from that vertex's bitmap.  A
+// vertex whose witness (the neighbour that beat it last time) is still on the
+// worklist (color < 0) and gets the same tentative color has lost again: it
+// goes straight onto W_{r+1}.  The others go onto the unsettled lists U_r for
+// ConflictResolve.
+
+// First-fit color from the bitmap of v given its first word; 0 if colors
+// 1..256 are all forbidden.
+__device__ __forceinline__ int bitmap_color(const Params &p, int32_t v, unsigned w0) {
+    if (~w0) return __ffs(~w0);
+    for (int j = 1; j < 8; ++j) {
+        const unsigned wv = __ldcg(p.bm + (size_t)j * p.np + v);
+        if (~wv) return j * 32 + __ffs(~wv);
+    }
+    return 0;
+}
+
+// FirstFit and witness check for U vertices per lane; returns tentative
+// colors in c[] and whether each is settled.
+template <bool kBatched, int U>
+__device__ __forceinline__ void det_assign_lane(const Params &p, const bool (&act)[U],
+                                                const int32_t (&v)[U], int (&c)[U],
+                                                bool (&settled)[U]) {
     const int lane = threadIdx.x & 31;
-    const unsigned NW = total_warps();
-    for (unsigned base = global_warp() * 32 * U; base < cnt; base += NW * 32 * U) {
-        int32_t v[U];
-        int c[U];
-        bool act[U];
+    unsigned w0[U], ww0[U];
+    int32_t wit[U];
+    int cw[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const unsigned idx = base + u * 32 + lane;
+    for (int u = 0; u < U; ++u) {
+        w0[u] = act[u] ? __ldcg(p.bm + v[u]) : 0u;
+        wit[u] = act[u] ? __ldcg(p.witness + v[u]) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        cw[u] = wit[u] >= 0 ? __ldcg(p.colors + wit[u]) : 0;
+        ww0[u] = wit[u] >= 0 ? __ldcg(p.bm + wit[u]) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) c[u] = act[u] ? bitmap_color(p, v[u], w0[u]) : 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        unsigned need = __ballot_sync(kFull, act[u] && c[u] == 0);
+        while (need) {  // bitmap full: scan the row (colors above 256 are in use)
+            const int src = __ffs(need) - 1;
+            need &= need - 1;
+            const int32_t x = __shfl_sync(kFull, v[u], src);
+            long long s, e;
+            int32_t vb;
+            row_of<kBatched>(p, x, s, e, vb);
+            const int cx = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);
+            if (lane == src) c[u] = cx;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int tw = (act[u] && wit[u] >= 0 && cw[u] < 0) ? bitmap_color(p, wit[u], ww0[u]) : 0;
+        settled[u] = act[u] && tw > 0 && tw == c[u];
+        if (act[u]) __stcg(p.colors + v[u], -c[u]);
+    }
+}
+
+// Light list: CTA tiles, order-preserving pushes of the settled to W_{r+1}
+// and of the rest to U_r.
+template <bool kBatched>
+__device__ void det_assign_light(const Params &p, int par, unsigned cnt, Acc &acc) {
+    const int pn = par ^ 1;
+    const int32_t *list = p.lw[par];
+    const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
+    unsigned long long dummy = 0;
+    for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
+        bool act[kLightUnroll], settled[kLightUnroll], open[kLightUnroll];
+        int32_t v[kLightUnroll];
+        int c[kLightUnroll];
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) {
+            const unsigned idx = tile_index(t, u);
             act[u] = idx < cnt;
             v[u] = act[u] ? __ldcg(list + idx) : 0;
         }
-        if (slots) {
+        det_assign_lane<kBatched, kLightUnroll>(p, act, v, c, settled);
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (act[u]) v[u] = __ldcg(p.hvert + v[u]);
-        }
-        unsigned w0[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) w0[u] = act[u] ? __ldcg(p.bm + v[u]) : 0u;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            c[u] = 0;
-            if (act[u]) {
-                if (~w0[u]) {
-                    c[u] = __ffs(~w0[u]);
-                } else {  // colors 1..32 all forbidden: look at the higher planes
-                    for (int j = 1; j < 8 && c[u] == 0; ++j) {
-                        const unsigned wv = __ldcg(p.bm + (size_t)j * p.np + v[u]);
-                        if (~wv) c[u] = j * 32 + __ffs(~wv);
-                    }
-                }
-            }
-        }
+        for (int u = 0; u < kLightUnroll; ++u) open[u] = act[u] && !settled[u];
+        block_push(settled, v, &p.ctr->nl[pn], p.lw[pn], acc.next);
+        block_push(open, v, &p.ctr->nul[par], p.ul[par], dummy);
+    }
+}
+
+// Medium list: warp chunks of 128 entries, warp-level pushes.
+template <bool kBatched>
+__device__ void det_assign_medium(const Params &p, int par, unsigned cnt, Acc &acc) {
+    constexpr int U = 4;
+    const int pn = par ^ 1;
+    const int32_t *list = p.mw[par];
+    const unsigned NW = total_warps();
+    unsigned long long dummy = 0;
+    for (unsigned base = global_warp() * 32 * U; base < cnt; base += NW * 32 * U) {
+        bool act[U], settled[U];
+        int32_t v[U];
+        int c[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            unsigned need = __ballot_sync(kFull, act[u] && c[u] == 0);
-            while (need) {  // bitmap full: scan the row (colors above 256 are in use)
-                const int src = __ffs(need) - 1;
-                need &= need - 1;
-                const int32_t x = __shfl_sync(kFull, v[u], src);
-                long long s, e;
-                int32_t vb;
-                row_of<kBatched>(p, x, s, e, vb);
-                const int cx = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);
-                if (lane == src) c[u] = cx;
+            const unsigned idx = base + u * 32 + (threadIdx.x & 31);
+            act[u] = idx < cnt;
+            v[u] = act[u] ? __ldcg(list + idx) : 0;
+        }
+        det_assign_lane<kBatched, U>(p, act, v, c, settled);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            warp_push(settled[u], v[u], &p.ctr->nm[pn], p.mw[pn], acc.next);
+            warp_push(act[u] && !settled[u], v[u], &p.ctr->num[par], p.um[par], dummy);
+        }
+    }
+}
+
+// Hub list: one lane per entry (entries are slots; chunk counts come from
+// the chunk bases).
+template <bool kBatched>
+__device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64, Acc &acc) {
+    const int pn = par ^ 1;
+    const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
+    const unsigned NW = total_warps();
+    for (unsigned base = global_warp() * 32; base < cnt; base += NW * 32) {
+        const unsigned idx = base + (threadIdx.x & 31);
+        bool act[1] = {idx < cnt}, settled[1];
+        int32_t slot = act[0] ? __ldcg(p.hw[par] + idx) : 0;
+        int32_t v[1] = {act[0] ? __ldcg(p.hvert + slot) : 0};
+        int c[1];
+        det_assign_lane<kBatched, 1>(p, act, v, c, settled);
+        if (act[0]) {
+            const unsigned cb = __ldcg(p.hcb[par] + idx);
+            const unsigned nchunks = (idx + 1 < cnt ? __ldcg(p.hcb[par] + idx + 1) : nch) - cb;
+            if (settled[0]) {
+                hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
+                acc.next += 1;
+            } else {
+                hub_list_push(&p.ctr->uh64[par], p.uh[par], p.ucb[par], slot, nchunks);
             }
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (act[u]) __stcg(p.colors + v[u], -c[u]);
     }
 }
 
@@ -799,17 +883,16 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
 }
 
 template <bool kBatched>
-__device__ void det_hub_detect(const Params &p, int par, unsigned long long h64, bool prefix,
-                               Acc &acc) {
+__device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsigned *cbs,
+                               unsigned long long h64, int pn, bool prefix, Acc &acc) {
     const int lane = threadIdx.x & 31;
-    const int pn = par ^ 1;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const long long CH = p.chunk;
     const unsigned NW = total_warps();
     for (unsigned q = global_warp(); q < nch; q += NW) {
-        const unsigned i = hub_entry(p.hcb[par], cnt, q);
-        const int32_t slot = __ldcg(p.hw[par] + i);
-        const unsigned j = q - __ldcg(p.hcb[par] + i);
+        const unsigned i = hub_entry(cbs, cnt, q);
+        const int32_t slot = __ldcg(slots + i);
+        const unsigned j = q - __ldcg(cbs + i);
         const int32_t v = __ldcg(p.hvert + slot);
         long long s, e;
         int32_t vb;
@@ -1413,26 +1496,28 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             }
         }
         if (recorder) {
-            ctr->nl[pn] = 0;
-            ctr->nm[pn] = 0;
-            ctr->h64[pn] = 0;
-            if (!kFast) {
+            if (kFast) {
+                ctr->nl[pn] = 0;
+                ctr->nm[pn] = 0;
+                ctr->h64[pn] = 0;
+            } else {  // det: W_{r+1}'s counters were cleared during the last phase B
                 ctr->sc64 = 0;
                 ctr->sum_w += total;                       // |W_r|
                 ctr->sum_d += __ldcg(&ctr->dcur);          // D_r: degrees of W_r
             }
             if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)total;
         }
+        const bool shortcut = !kFast && r == 1 && !p.resume;  // det round 1: all colors are 1
         // ---- phase A: FirstFit over W_r (det round 1: every tentative color is 1)
         if (kFast) {
             const int kmax = __ldcg(&ctr->kmax);
             fast_hub_assign<kBatched>(p, par, h64, kmax, acc);
             fast_medium_assign<kBatched>(p, p.mw[par], nm, acc);
             fast_light_assign<kBatched>(p, p.lw[par], nl, sbuf, acc);
-        } else if (r > 1 || p.resume) {
-            det_assign<kBatched>(p, p.hw[par], (unsigned)(h64 >> 32), true);
-            det_assign<kBatched>(p, p.mw[par], nm, false);
-            det_assign<kBatched>(p, p.lw[par], nl, false);
+        } else if (!shortcut) {
+            det_assign_hubs<kBatched>(p, par, h64, acc);
+            det_assign_medium<kBatched>(p, par, nm, acc);
+            det_assign_light<kBatched>(p, par, nl, acc);
         }
         if (!(ok = grid_barrier(p, gen))) break;
         if (recorder && r <= kTraceCap)
@@ -1444,10 +1529,25 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             fast_medium_detect<kBatched>(p, p.mw[par], nm, p.mw[pn], &ctr->nm[pn], prefix, b);
             fast_light_detect<kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix, sbuf, b);
         } else {
-            det_hub_detect<kBatched>(p, par, h64, prefix, b);
-            det_medium_detect<kBatched>(p, p.mw[par], nm, p.mw[pn], &ctr->nm[pn], prefix, b);
-            det_light_detect<kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix,
-                                       r == 1 && !p.resume, b);
+            // round 1 reads W_1 itself; later rounds only the vertices the
+            // witness did not settle in phase A
+            const unsigned bnl = shortcut ? nl : __ldcg(&ctr->nul[par]);
+            const unsigned bnm = shortcut ? nm : __ldcg(&ctr->num[par]);
+            const unsigned long long bh = shortcut ? h64 : __ldcg(&ctr->uh64[par]);
+            if (recorder) {  // W_r's counters are in registers; U_{r+1} must start empty
+                ctr->nl[par] = 0;
+                ctr->nm[par] = 0;
+                ctr->h64[par] = 0;
+                ctr->nul[pn] = 0;
+                ctr->num[pn] = 0;
+                ctr->uh64[pn] = 0;
+            }
+            det_hub_detect<kBatched>(p, shortcut ? p.hw[par] : p.uh[par],
+                                     shortcut ? p.hcb[par] : p.ucb[par], bh, pn, prefix, b);
+            det_medium_detect<kBatched>(p, shortcut ? p.mw[par] : p.um[par], bnm, p.mw[pn],
+                                        &ctr->nm[pn], prefix, b);
+            det_light_detect<kBatched>(p, shortcut ? p.lw[par] : p.ul[par], bnl, p.lw[pn],
+                                       &ctr->nl[pn], prefix, shortcut, b);
         }
         acc.w += b.w;
         acc.d += b.d;

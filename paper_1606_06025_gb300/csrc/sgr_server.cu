@@ -145,9 +145,9 @@ struct sgr_server {
 namespace {
 
 // Per-vertex device bytes: colors, 8 bitmap words, lower count, witness, graph
-// id, two parities of three worklists and hub chunk bases, six hub arrays, one
-// row offset.
-constexpr long long kVertexBytes = 4 + 32 + 4 + 4 + 4 + 2 * 4 * 4 + 6 * 4 + 4;
+// id, two parities of three worklists and hub chunk bases, the same for the
+// unsettled lists, six hub arrays, one row offset.
+constexpr long long kVertexBytes = 4 + 32 + 4 + 4 + 4 + 2 * 4 * 4 + 2 * 4 * 4 + 6 * 4 + 4;
 
 int carve(sgr_server *S) {
     const long long budget = S->cfg.hbm_budget_bytes;
@@ -171,6 +171,8 @@ int carve(sgr_server *S) {
     auto take = [&](void **dst, size_t bytes) { parts.push_back({dst, bytes}); };
     int32_t *lw0, *lw1, *mw0, *mw1, *hw0, *hw1, *gid, *ro, *ci;
     unsigned *hcb0, *hcb1;
+    int32_t *ul0, *ul1, *um0, *um1, *uh0, *uh1;
+    unsigned *ucb0, *ucb1;
     take((void **)&P.ctr, sizeof(sgr::Counters));
     take((void **)&P.hdone, (size_t)Vcap * 4);
     take((void **)&P.hconf, (size_t)Vcap * 4);
@@ -188,6 +190,14 @@ int carve(sgr_server *S) {
     take((void **)&hw1, (size_t)Vcap * 4);
     take((void **)&hcb0, (size_t)Vcap * 4);
     take((void **)&hcb1, (size_t)Vcap * 4);
+    take((void **)&ul0, (size_t)Vcap * 4);
+    take((void **)&ul1, (size_t)Vcap * 4);
+    take((void **)&um0, (size_t)Vcap * 4);
+    take((void **)&um1, (size_t)Vcap * 4);
+    take((void **)&uh0, (size_t)Vcap * 4);
+    take((void **)&uh1, (size_t)Vcap * 4);
+    take((void **)&ucb0, (size_t)Vcap * 4);
+    take((void **)&ucb1, (size_t)Vcap * 4);
     take((void **)&P.hvert, (size_t)Vcap * 4);
     take((void **)&P.hbase, (size_t)Vcap * 4);
     take((void **)&P.sw, (size_t)Vcap * 4);
@@ -227,6 +237,10 @@ int carve(sgr_server *S) {
     P.mw[0] = mw0; P.mw[1] = mw1;
     P.hw[0] = hw0; P.hw[1] = hw1;
     P.hcb[0] = hcb0; P.hcb[1] = hcb1;
+    P.ul[0] = ul0; P.ul[1] = ul1;
+    P.um[0] = um0; P.um[1] = um1;
+    P.uh[0] = uh0; P.uh[1] = uh1;
+    P.ucb[0] = ucb0; P.ucb[1] = ucb1;
     const sgr_tuning t = sgr::tuning_snapshot();
     P.light_max = t.light_max;
     P.chunk = t.chunk;
