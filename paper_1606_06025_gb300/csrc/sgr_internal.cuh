@@ -37,6 +37,7 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kLightUnroll = 4;                  // 32-vertex sub-tiles per warp and light tile
 constexpr int kLightTile = kBlock * kLightUnroll;
 constexpr int kSlowCap = 2 * kLightTile;          // det: queued slow vertices per CTA
+constexpr int kScatterChunk = 128;               // det: entries per hub-scatter work item (one step)
 constexpr int kMinBlocks = 3;                    // CTAs per SM the register budget targets
 constexpr int kLightMaxStage = 32;               // largest light degree (staged rows per lane)
 constexpr int kTraceCap = 1 << 16;               // rounds recorded in the timeline

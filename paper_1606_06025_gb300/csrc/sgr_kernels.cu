@@ -270,6 +270,52 @@ __device__ __forceinline__ void block_push(const bool (&flag)[kLightUnroll],
     __syncthreads();
 }
 
+// Two order-preserving block compactions in one pass (flags a go to outa,
+// flags b to outb): one scan, the two atomics issued back to back.
+__device__ __forceinline__ void block_push2(const bool (&fa)[kLightUnroll], const bool (&fb)[kLightUnroll],
+                                            const int32_t (&item)[kLightUnroll], unsigned *ca,
+                                            int32_t *outa, unsigned *cb, int32_t *outb,
+                                            unsigned long long &pushed_a) {
+    __shared__ unsigned s_a[kWarps][kLightUnroll], s_b[kWarps][kLightUnroll];
+    __shared__ unsigned s_base[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned ba[kLightUnroll], bb[kLightUnroll];
+#pragma unroll
+    for (int u = 0; u < kLightUnroll; ++u) {
+        ba[u] = __ballot_sync(kFull, fa[u]);
+        bb[u] = __ballot_sync(kFull, fb[u]);
+        if (lane == 0) {
+            s_a[warp][u] = __popc(ba[u]);
+            s_b[warp][u] = __popc(bb[u]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned ta = 0, tb = 0;
+        for (int w = 0; w < kWarps; ++w)
+            for (int u = 0; u < kLightUnroll; ++u) {
+                const unsigned x = s_a[w][u], y = s_b[w][u];
+                s_a[w][u] = ta;
+                s_b[w][u] = tb;
+                ta += x;
+                tb += y;
+            }
+        const unsigned oa = ta ? atomicAdd(ca, ta) : 0u;
+        const unsigned ob = tb ? atomicAdd(cb, tb) : 0u;
+        s_base[0] = oa;
+        s_base[1] = ob;
+        pushed_a += ta;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kLightUnroll; ++u) {
+        const unsigned below = lanemask_lt();
+        if (fa[u]) outa[s_base[0] + s_a[warp][u] + __popc(ba[u] & below)] = item[u];
+        if (fb[u]) outb[s_base[1] + s_b[warp][u] + __popc(bb[u] & below)] = item[u];
+    }
+    __syncthreads();
+}
+
 // Warp-level order-preserving push of one flag per lane.
 __device__ __forceinline__ void warp_push(bool flag, int32_t item, unsigned *counter,
                                           int32_t *out, unsigned long long &pushed) {
@@ -388,7 +434,6 @@ __device__ void det_assign_light(const Params &p, int par, unsigned cnt, Acc &ac
     const int pn = par ^ 1;
     const int32_t *list = p.lw[par];
     const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
-    unsigned long long dummy = 0;
     for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
         bool act[kLightUnroll], settled[kLightUnroll], open[kLightUnroll];
         int32_t v[kLightUnroll];
@@ -402,8 +447,8 @@ __device__ void det_assign_light(const Params &p, int par, unsigned cnt, Acc &ac
         det_assign_lane<kBatched, kLightUnroll>(p, act, v, c, settled);
 #pragma unroll
         for (int u = 0; u < kLightUnroll; ++u) open[u] = act[u] && !settled[u];
-        block_push(settled, v, &p.ctr->nl[pn], p.lw[pn], acc.next);
-        block_push(open, v, &p.ctr->nul[par], p.ul[par], dummy);
+        block_push2(settled, open, v, &p.ctr->nl[pn], p.lw[pn], &p.ctr->nul[par], p.ul[par],
+                    acc.next);
     }
 }
 
@@ -930,7 +975,8 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
                     acc.kmax = max(acc.kmax, c);
                     acc.kdeg += (unsigned long long)deg;
                     acc.scatter += (unsigned long long)deg;
-                    hub_list_push(&p.ctr->sc64, p.sw, p.scb, slot, nchunks);
+                    hub_list_push(&p.ctr->sc64, p.sw, p.scb, slot,
+                                  (unsigned)((deg + kScatterChunk - 1) / kScatterChunk));
                 }
             }
         }
@@ -942,7 +988,7 @@ template <bool kBatched>
 __device__ void det_hub_scatter(const Params &p, unsigned long long sc64) {
     const int lane = threadIdx.x & 31;
     const unsigned cnt = (unsigned)(sc64 >> 32), nch = (unsigned)sc64;
-    const long long CH = p.chunk;
+    const long long CH = kScatterChunk;
     const unsigned NW = total_warps();
     for (unsigned q = global_warp(); q < nch; q += NW) {
         const unsigned i = hub_entry(p.scb, cnt, q);
