@@ -138,20 +138,23 @@ def read_traffic(workload, mode):
 def alg_bytes(st, n, m, mode):
     """Algorithmic DRAM bytes of one coloring launch (the byte model).
 
-    Per worklist vertex and round, 36 B: FirstFit reads the worklist entry (4)
-    and either the first word of the vertex's forbidden-color bitmap (det, 4)
-    or its row offsets (fast, counted with the scan below) and writes the
-    tentative color (4); ConflictResolve reads the entry (4), the row offsets
-    (8), the vertex's color (4) and its lower-neighbour count (4) and writes
-    the commit (4).  4 B per col_idx entry ConflictResolve inspects, 4 B per
-    pushed loser; det mode adds 4 B per entry a committing vertex scatters its
-    color to, fast mode 4 B per entry FirstFit gathers (sum of D_r).  The init
-    pass reads col_idx once (4 B per entry) and 24 B per vertex.  Neighbour
-    color and bitmap accesses hit L2-resident arrays and are not counted."""
-    per = 36 * st["sum_w"] + 4 * st["sum_dscan"] + 4 * st["sum_next"] + 4 * m + 24 * n
+    Deterministic mode, per worklist vertex and round, 20 B: FirstFit reads the
+    worklist entry (4), the first word of the vertex's forbidden-color bitmap
+    (4) and its witness (4), writes the tentative color (4) and pushes the entry
+    onto the next list (4).  A vertex the witness does not settle is rescanned
+    by ConflictResolve: 24 B more (entry 4, row offsets 8, own color 4,
+    lower-neighbour count 4, commit 4) plus 4 B per col_idx entry it inspects.
+    A committing vertex scatters its color: 4 B per entry.  Fast mode, per
+    worklist vertex and round, 36 B (entry and row offsets in both phases, color
+    read and writes) plus 4 B per entry FirstFit gathers (sum of D_r) and per
+    entry ConflictResolve inspects.  The init pass reads col_idx once (4 B per
+    entry) and 24 B per vertex.  Neighbour color and bitmap accesses that hit
+    the L2-resident arrays are not counted."""
     if mode == "det":
-        return per + 4 * st["sum_scatter"]
-    return per + 4 * st["sum_d"]
+        return (20 * st["sum_w"] + 24 * st["sum_rescan"] + 4 * st["sum_dscan"]
+                + 4 * st["sum_scatter"] + 4 * m + 24 * n)
+    return (36 * st["sum_w"] + 4 * st["sum_d"] + 4 * st["sum_dscan"] + 4 * st["sum_next"]
+            + 4 * m + 24 * n)
 
 
 class ClockSampler:

@@ -86,6 +86,7 @@ typedef struct {
     int64_t sum_dscan;     /* col_idx entries ConflictResolve had to inspect */
     int64_t sum_next;      /* sum over rounds of |W_{r+1}| (pushed losers) */
     int64_t sum_scatter;   /* det mode: neighbour bitmap updates by committed vertices */
+    int64_t sum_rescan;    /* det mode: worklist vertices ConflictResolve rescanned */
     int32_t num_colors;    /* k (max color); per-graph values are returned separately */
     int32_t rows_sorted;   /* 1 if every row was strictly ascending */
     int32_t grid_blocks;   /* CTAs of the persistent kernel */

@@ -247,6 +247,7 @@ void fill_stats(const Counters &h, float ms, int grid, int colors) {
     s.sum_dscan = (int64_t)h.sum_dscan;
     s.sum_next = (int64_t)h.sum_next;
     s.sum_scatter = (int64_t)h.sum_scatter;
+    s.sum_rescan = (int64_t)h.sum_rescan;
     s.num_colors = colors;
     s.rows_sorted = h.unsorted_pairs == h.boundary_pairs ? 1 : 0;
     s.grid_blocks = grid;

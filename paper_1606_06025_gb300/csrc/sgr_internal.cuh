@@ -61,7 +61,7 @@ struct Counters {
     int err;                        // 0 or a negative status
     unsigned long long unsorted_pairs;   // adjacent col_idx pairs with a[i] >= a[i+1]
     unsigned long long boundary_pairs;   // ... of them across row boundaries
-    unsigned long long sum_w, sum_d, sum_dscan, sum_next, sum_scatter;
+    unsigned long long sum_w, sum_d, sum_dscan, sum_next, sum_scatter, sum_rescan;
     unsigned long long sc64;        // hub scatter list: (entries << 32) | total chunks
     unsigned long long dcur;        // det: degree sum of the current worklist
     unsigned long long nslow;       // det: worklist vertices that rescanned their row this round

@@ -1475,7 +1475,10 @@ __device__ void flush_phase(const Params &p, int kloc, unsigned long long kdeg,
         }
         if (b > 0 && b > *(volatile int *)&p.ctr->kmax) atomicMax(&p.ctr->kmax, b);
         if (d) atomicAdd(&p.ctr->dcur, 0ull - d);
-        if (sl) atomicAdd(&p.ctr->nslow, sl);
+        if (sl) {
+            atomicAdd(&p.ctr->nslow, sl);
+            atomicAdd(&p.ctr->sum_rescan, sl);
+        }
     }
 }
 

@@ -52,6 +52,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int64), ("sum_w", ctypes.c_int64),
                 ("sum_d", ctypes.c_int64), ("sum_dscan", ctypes.c_int64),
                 ("sum_next", ctypes.c_int64), ("sum_scatter", ctypes.c_int64),
+                ("sum_rescan", ctypes.c_int64),
                 ("num_colors", ctypes.c_int32),
                 ("rows_sorted", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("device_ms", ctypes.c_double)]
