@@ -177,7 +177,7 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     };
     // zeroed region first: counters, hub completion counters / flags, hub bitmaps
     Counters *ctr = (Counters *)take(sizeof(Counters));
-    unsigned *hdone = (unsigned *)take(sp.hub_max * 4);
+    unsigned long long *hdone = (unsigned long long *)take(sp.hub_max * 8);
     unsigned *hconf = (unsigned *)take(sp.hub_max * 4);
     unsigned *hbits = (unsigned *)take(sp.hub_words * 4);
     const size_t zero_fast = off;

@@ -53,8 +53,7 @@ struct Counters {
     unsigned long long h64[2];      // hub lists: (entries << 32) | total chunks
     unsigned int nul[2], num[2];    // det: unsettled light / medium vertices of the round
     unsigned long long uh64[2];     // det: unsettled hubs (entries << 32 | chunks)
-    unsigned int bar_count;         // grid barrier arrivals
-    unsigned int bar_gen;           // grid barrier generation
+    unsigned long long bar;         // grid barrier: arrivals (bits 0..62), error flag (bit 63)
     unsigned int nslots;            // hub slots handed out
     unsigned int hwords;            // hub bitmap words handed out
     int kmax;                       // largest committed color
@@ -91,7 +90,7 @@ struct Params {
     int32_t *hvert;
     unsigned int *hbase;
     unsigned int *hbits;
-    unsigned int *hdone;
+    unsigned long long *hdone; // per hub slot: finished items (low word), conflicts (high word, det)
     unsigned int *hconf;
     unsigned int *bm;          // det: 8 planes of np words
     long long np;              // plane stride (>= n, multiple of 64)

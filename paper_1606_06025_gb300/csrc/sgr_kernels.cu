@@ -59,14 +59,18 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ unsigned long long atom_add_release64(unsigned long long *p,
+                                                                 unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;"
+                 : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
 }
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -75,32 +79,42 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-// Bounded grid barrier (arrival counter + generation).  Returns false if this
-// CTA must stop (timeout or a recorded error).
+constexpr unsigned long long kBarErr = 1ull << 63;
+
+// Record an error status and raise the barrier's error flag, so that every
+// CTA leaves at its next barrier.
+__device__ __forceinline__ void raise_error(const Params &p, int code) {
+    atomicCAS(&p.ctr->err, 0, code);
+    atomicOr(&p.ctr->bar, kBarErr);
+}
+
+// Bounded grid barrier on a monotone arrival counter: barrier number `gen`
+// (per CTA, counted from 1) is passed once gen * nblocks CTAs have arrived.
+// The arrival is a release and the poll an acquire, so every write the CTA
+// made before the barrier is visible to every CTA after it.  Returns false
+// if this CTA must stop (timeout, or an error flagged by any CTA).
 __device__ bool grid_barrier(const Params &p, unsigned &gen) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        Counters *c = p.ctr;
         gen += 1;
+        const unsigned long long target = (unsigned long long)gen * p.nblocks;
+        unsigned long long seen = atom_add_release64(&p.ctr->bar, 1ull) + 1ull;
         int ok = 1;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&c->bar_count, 1u);
-        if (arrived == p.nblocks - 1) {
-            c->bar_count = 0;
-            st_release(&c->bar_gen, gen);
-        } else {
+        if ((seen & ~kBarErr) < target && !(seen & kBarErr)) {
             const unsigned long long t0 = globaltimer();
-            while ((int)(ld_acquire(&c->bar_gen) - gen) < 0) {
+            for (;;) {
+                seen = ld_acquire64(&p.ctr->bar);
+                if ((seen & ~kBarErr) >= target || (seen & kBarErr)) break;
                 __nanosleep(32);
                 if (globaltimer() - t0 > kWaitTimeoutNs) {
-                    atomicCAS(&c->err, 0, kErrTimeout);
-                    ok = 0;
+                    raise_error(p, kErrTimeout);
+                    seen |= kBarErr;
                     break;
                 }
             }
         }
-        if (ok && *(volatile int *)&c->err != 0) ok = 0;
+        if (seen & kBarErr) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -163,6 +177,17 @@ __device__ __forceinline__ unsigned global_warp() {
 }
 
 __device__ __forceinline__ unsigned total_warps() { return (gridDim.x * blockDim.x) >> 5; }
+
+// The hub, medium and light lists of a phase start on different CTAs (a third
+// of the grid apart), so that on short lists no warp works through items of
+// all three one after the other.
+__device__ __forceinline__ unsigned rot_block(int part) {
+    return (blockIdx.x + (unsigned)part * (gridDim.x / 3)) % gridDim.x;
+}
+
+__device__ __forceinline__ unsigned rot_warp(int part) {
+    return (rot_block(part) * blockDim.x + threadIdx.x) >> 5;
+}
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     return (1u << (threadIdx.x & 31)) - 1u;
@@ -434,7 +459,7 @@ __device__ void det_assign_light(const Params &p, int par, unsigned cnt, Acc &ac
     const int pn = par ^ 1;
     const int32_t *list = p.lw[par];
     const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
-    for (unsigned t = blockIdx.x; t < tiles; t += gridDim.x) {
+    for (unsigned t = rot_block(2); t < tiles; t += gridDim.x) {
         bool act[kLightUnroll], settled[kLightUnroll], open[kLightUnroll];
         int32_t v[kLightUnroll];
         int c[kLightUnroll];
@@ -460,7 +485,7 @@ __device__ void det_assign_medium(const Params &p, int par, unsigned cnt, Acc &a
     const int32_t *list = p.mw[par];
     const unsigned NW = total_warps();
     unsigned long long dummy = 0;
-    for (unsigned base = global_warp() * 32 * U; base < cnt; base += NW * 32 * U) {
+    for (unsigned base = rot_warp(1) * 32 * U; base < cnt; base += NW * 32 * U) {
         bool act[U], settled[U];
         int32_t v[U];
         int c[U];
@@ -734,7 +759,7 @@ __device__ void det_light_detect(const Params &p, const int32_t *list, unsigned 
     if (cnt < 2u * gridDim.x * kLightTile) {
         // short worklist: 32 entries per warp, spread over every warp of the grid
         const unsigned NW = total_warps();
-        for (unsigned base = global_warp() * 32; base < cnt; base += NW * 32) {
+        for (unsigned base = rot_warp(2) * 32; base < cnt; base += NW * 32) {
             const unsigned idx[1] = {base + (threadIdx.x & 31)};
             bool flag[1], slow[1];
             int32_t v[1], c[1];
@@ -754,7 +779,7 @@ __device__ void det_light_detect(const Params &p, const int32_t *list, unsigned 
     if (threadIdx.x == 0) s_sn = 0;
     __syncthreads();
     const unsigned tiles = (cnt + kLightTile - 1) / kLightTile;
-    for (unsigned t = blockIdx.x;; t += gridDim.x) {
+    for (unsigned t = rot_block(2);; t += gridDim.x) {
         const bool more = t < tiles;
         if (more) {
             bool flag[kLightUnroll], slow[kLightUnroll];
@@ -882,7 +907,7 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
                                   unsigned *out_cnt, bool prefix, Acc &acc) {
     const int lane = threadIdx.x & 31;
     const unsigned NW = total_warps(), B = warp_batch(cnt);
-    for (unsigned b = global_warp() * B; b < cnt; b += NW * B) {
+    for (unsigned b = rot_warp(1) * B; b < cnt; b += NW * B) {
         const unsigned i = b + lane;
         const int nb = (int)min(B, cnt - b);
         int32_t vl = 0, vbl = 0, wl = -1;
@@ -960,13 +985,21 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
         }
         const unsigned nchunks = (unsigned)((deg + CH - 1) / CH);
         if (lane == 0) {
-            if (conf) atomicOr(p.hconf + slot, 1u);
-            __threadfence();
-            if (atomicAdd(p.hdone + slot, 1u) == nchunks - 1) {
+            // hconf stops the other items early; the decision travels in the
+            // completion counter itself (conflicts in the high word).  The
+            // fences order a conflict's hconf write before its count and the
+            // last item's reset of hconf after every count.
+            if (conf) {
+                atomicOr(p.hconf + slot, 1u);
                 __threadfence();
-                const unsigned lost = __ldcg(p.hconf + slot);
+            }
+            const unsigned long long old =
+                atomicAdd(p.hdone + slot, conf ? (1ull << 32) + 1ull : 1ull);
+            if ((unsigned)old == nchunks - 1) {
+                __threadfence();
+                const bool lost = conf || (old >> 32) != 0;
                 __stcg(p.hconf + slot, 0u);
-                __stcg(p.hdone + slot, 0u);
+                __stcg(p.hdone + slot, 0ull);
                 if (lost) {
                     hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
                     acc.next += 1;
@@ -1306,7 +1339,7 @@ __device__ void fast_hub_assign(const Params &p, int par, unsigned long long h64
         unsigned last = 0;
         if (lane == 0) {
             __threadfence();
-            last = (atomicAdd(p.hdone + slot, 1u) == nchunks - 1) ? 1u : 0u;
+            last = ((unsigned)atomicAdd(p.hdone + slot, 1ull) == nchunks - 1) ? 1u : 0u;
             if (last) __threadfence();
         }
         last = __shfl_sync(kFull, last, 0);
@@ -1323,7 +1356,7 @@ __device__ void fast_hub_assign(const Params &p, int par, unsigned long long h64
             else c = warp_first_fit(p.ci, p.m, p.colors, s, e, vb, lane, p.n);
             if (lane == 0) {
                 __stcg(p.colors + v, c);
-                __stcg(p.hdone + slot, 0u);
+                __stcg(p.hdone + slot, 0ull);
                 acc.w += 1;
                 acc.d += (unsigned long long)deg;
             }
@@ -1357,11 +1390,11 @@ __device__ void fast_hub_detect(const Params &p, int par, unsigned long long h64
         if (lane == 0) {
             if (conf) atomicOr(p.hconf + slot, 1u);
             __threadfence();
-            if (atomicAdd(p.hdone + slot, 1u) == nchunks - 1) {
+            if ((unsigned)atomicAdd(p.hdone + slot, 1ull) == nchunks - 1) {
                 __threadfence();
                 const unsigned lost = __ldcg(p.hconf + slot);
                 __stcg(p.hconf + slot, 0u);
-                __stcg(p.hdone + slot, 0u);
+                __stcg(p.hdone + slot, 0ull);
                 if (lost) {
                     __stcg(p.colors + v, 0);
                     hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
@@ -1473,7 +1506,7 @@ __device__ void flush_phase(const Params &p, int kloc, unsigned long long kdeg,
             d += s_d[w];
             sl += s_s[w];
         }
-        if (b > 0 && b > *(volatile int *)&p.ctr->kmax) atomicMax(&p.ctr->kmax, b);
+        if (b > 0) atomicMax(&p.ctr->kmax, b);  // no return value: nothing waits on it
         if (d) atomicAdd(&p.ctr->dcur, 0ull - d);
         if (sl) {
             atomicAdd(&p.ctr->nslow, sl);
@@ -1534,7 +1567,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             break;
         }
         if (r > p.max_rounds) {
-            if (recorder) atomicCAS(&ctr->err, 0, kErrNoConvergence);
+            if (recorder) raise_error(p, kErrNoConvergence);
             break;
         }
         if (!kFast) {  // colors of hubs committed last round go to their neighbours' bitmaps

@@ -174,7 +174,7 @@ int carve(sgr_server *S) {
     int32_t *ul0, *ul1, *um0, *um1, *uh0, *uh1;
     unsigned *ucb0, *ucb1;
     take((void **)&P.ctr, sizeof(sgr::Counters));
-    take((void **)&P.hdone, (size_t)Vcap * 4);
+    take((void **)&P.hdone, (size_t)Vcap * 8);
     take((void **)&P.hconf, (size_t)Vcap * 4);
     take((void **)&P.trace, sizeof(long long) * sgr::kTraceCap * sgr::kTraceFields);
     take((void **)&P.colors, (size_t)Vcap * 4);
@@ -381,7 +381,7 @@ void worker_loop(sgr_server *S) {
         P.rounds_per_launch = R;
         P.nblocks = (unsigned)S->grid;
         // fresh barrier and error state for this launch
-        if (e == cudaSuccess) e = cudaMemsetAsync(&P.ctr->bar_count, 0, 2 * sizeof(unsigned), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&P.ctr->bar, 0, sizeof(unsigned long long), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(&P.ctr->err, 0, sizeof(int), st);
         if (e == cudaSuccess) e = sgr::launch_color(P, false, true, S->grid, st);
         if (e == cudaSuccess)
