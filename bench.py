@@ -288,8 +288,10 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     if args.tune:
-        lm, ch, bps = (int(x) for x in args.tune.split(","))
-        lib.sgr_set_tuning(light_max=lm, chunk=ch, blocks_per_sm=bps)
+        fields = [int(x) for x in args.tune.split(",")]
+        lm, ch, bps = fields[:3]
+        al = fields[3] if len(fields) > 3 else 0
+        lib.sgr_set_tuning(light_max=lm, chunk=ch, blocks_per_sm=bps, active_lists=al)
     desc, make = workload(args.workload)
     g = make()
     n, m = g.n, g.m
@@ -695,7 +697,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--timeline", default="", help="write the per-round device timeline here")
-    ap.add_argument("--tune", default="", help="light_max,chunk,blocks_per_sm (0 = default)")
+    ap.add_argument("--tune", default="", help="light_max,chunk,blocks_per_sm[,active_lists] (0 = default)")
     ap.add_argument("--autotune", action="store_true",
                     help="measure the tuning candidates on the workload before timing")
     ap.add_argument("--requests", type=int, default=600, help="serve: requests in the stream")

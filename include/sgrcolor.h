@@ -101,7 +101,12 @@ typedef struct {
     int32_t chunk;         /* edges per warp work item of the hub bin; also the
                               degree bound of the warp-per-vertex bin (>= 64) */
     int32_t blocks_per_sm; /* persistent CTAs per SM (capped by occupancy) */
-    int32_t reserved;      /* must be 0 */
+    int32_t active_lists;  /* deterministic mode: 0 = a round runs on the
+                              activation lists (the vertices a commit made
+                              stale, plus those whose witness they are) once
+                              that is cheaper than the whole worklist;
+                              1 = never; 2 = from round 2 on.  The colors are
+                              the same in every case. */
 } sgr_tuning;
 
 /*

@@ -63,6 +63,7 @@ struct DevCtx {
     int device = -1;
     int sms = 0;
     int occ[2][2] = {{0, 0}, {0, 0}};  // [fast][batched]
+    int occ_front[2] = {0, 0};          // activation-list kernel, [batched]
     Arena scratch;                      // worklists, counters, bitmaps
     Arena io;                           // device copies for the host-buffer entry
     Counters *host_ctr = nullptr;       // pinned read-back
@@ -109,6 +110,8 @@ int get_ctx(DevCtx **out) {
             for (int b = 0; b < 2; ++b)
                 if (sgr::occupancy_blocks_per_sm(f != 0, b != 0, &c->occ[f][b]) != 0)
                     return SGR_ERR_CUDA;
+        for (int b = 0; b < 2; ++b)
+            if (sgr::occupancy_blocks_per_sm_front(b != 0, &c->occ_front[b]) != 0) return SGR_ERR_CUDA;
         if (cudaMallocHost(&c->host_ctr, sizeof(Counters)) != cudaSuccess) return SGR_ERR_OUT_OF_MEMORY;
         if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
             return SGR_ERR_CUDA;
@@ -163,6 +166,7 @@ struct Job {
     const long long *ebase_dev;
     const long long *robase_dev;
     int32_t *gid_dev;  // filled by the caller for batched jobs
+    bool front;        // det: allocate the activation lists (rounds may run on them)
 };
 
 // Carve the scratch arena for a job.  Returns the byte size; fills p when
@@ -183,6 +187,8 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     const size_t zero_fast = off;
     const long long np = ((long long)j.n + 63) / 64 * 64;
     unsigned *bm = (unsigned *)take((size_t)np * 8 * 4);
+    const bool front = !j.fast && j.front;
+    int32_t *astamp = front ? (int32_t *)take((size_t)j.n * 4) : nullptr;
     if (zero_bytes) *zero_bytes = j.fast ? zero_fast : off;
     int32_t *lowdeg = (int32_t *)take((size_t)j.n * 4);
     int32_t *witness = (int32_t *)take((size_t)j.n * 4);
@@ -200,6 +206,12 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     int32_t *um0 = (int32_t *)take(un * 4), *um1 = (int32_t *)take(un * 4);
     int32_t *uh0 = (int32_t *)take(uhub * 4), *uh1 = (int32_t *)take(uhub * 4);
     unsigned *ucb0 = (unsigned *)take(uhub * 4), *ucb1 = (unsigned *)take(uhub * 4);
+    const size_t an = front ? (size_t)j.n : 1, ahub = front ? sp.hub_max : 1;
+    int32_t *vslot = (int32_t *)take(j.fast ? 4 : (size_t)j.n * 4);
+    int32_t *al0 = (int32_t *)take(an * 4), *al1 = (int32_t *)take(an * 4);
+    int32_t *am0 = (int32_t *)take(an * 4), *am1 = (int32_t *)take(an * 4);
+    int32_t *ah0 = (int32_t *)take(ahub * 4), *ah1 = (int32_t *)take(ahub * 4);
+    unsigned *acb0 = (unsigned *)take(ahub * 4), *acb1 = (unsigned *)take(ahub * 4);
     if (p && base) {
         std::memset(p, 0, sizeof(*p));
         p->ro = j.ro;
@@ -219,6 +231,14 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         p->um[0] = um0; p->um[1] = um1;
         p->uh[0] = uh0; p->uh[1] = uh1;
         p->ucb[0] = ucb0; p->ucb[1] = ucb1;
+        p->al[0] = al0; p->al[1] = al1;
+        p->am[0] = am0; p->am[1] = am1;
+        p->ah[0] = ah0; p->ah[1] = ah1;
+        p->acb[0] = acb0; p->acb[1] = acb1;
+        p->astamp = astamp;
+        p->vslot = vslot;
+        p->front_ok = front ? 1 : 0;
+        p->front_policy = t.active_lists;
         p->hvert = hvert;
         p->hbase = hbase;
         p->hbits = hbits;
@@ -256,8 +276,31 @@ void fill_stats(const Counters &h, float ms, int grid, int colors) {
     t_stats = s;
 }
 
-// Run one persistent coloring launch for a job (single graph or batch) and
-// read back the counters.  Caller holds the device mutex.
+// The coloring launches of a job: the round loop over whole worklists, which
+// also runs init; in deterministic mode with activation lists it may hand the
+// rounds over after init (Counters::handoff) to the activation-list kernel,
+// which is therefore always launched behind it (and returns at once if not
+// needed).  Each launch gets its own grid and a fresh barrier counter.
+cudaError_t launch_rounds(Params p, bool fast, bool batched, int per_sm_full, int per_sm_front,
+                          int sms, const sgr_tuning &t, cudaStream_t st, int *grid_out) {
+    int per_sm = per_sm_full;
+    if (t.blocks_per_sm > 0) per_sm = std::min(per_sm, t.blocks_per_sm);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = per_sm * sms;
+    p.nblocks = (unsigned)grid;
+    *grid_out = grid;
+    cudaError_t e = sgr::launch_color(p, fast, batched, grid, st);
+    if (e != cudaSuccess || fast || !p.front_ok || p.front_policy == 1) return e;
+    int per_sm_f = per_sm_front;
+    if (t.blocks_per_sm > 0) per_sm_f = std::min(per_sm_f, t.blocks_per_sm);
+    if (per_sm_f < 1) return cudaErrorInvalidConfiguration;
+    p.nblocks = (unsigned)(per_sm_f * sms);
+    if ((e = cudaMemsetAsync(&p.ctr->bar, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    return sgr::launch_color_front(p, batched, (int)p.nblocks, st);
+}
+
+// Run the coloring launches for a job (single graph or batch) and read back
+// the counters.  Caller holds the device mutex.
 int run_job(DevCtx *c, Job &j, int mode, cudaStream_t st, int32_t *k_out) {
     const sgr_tuning t = current_tuning();
     const bool fast = (mode & SGR_MODE_MASK) == SGR_MODE_FAST;
@@ -277,18 +320,16 @@ int run_job(DevCtx *c, Job &j, int mode, cudaStream_t st, int32_t *k_out) {
     layout(j, t, c->scratch.ptr, &p, nullptr);
     p.rule = rule;
     p.max_rounds = (long long)j.n + 1;
-    int per_sm = c->occ[fast][j.batched];
-    if (t.blocks_per_sm > 0) per_sm = std::min(per_sm, t.blocks_per_sm);
-    if (per_sm < 1) return SGR_ERR_CUDA;
-    const int grid = per_sm * c->sms;
-    p.nblocks = (unsigned)grid;
     if ((e = cudaMemsetAsync(c->scratch.ptr, 0, zero_bytes, st)) != cudaSuccess) return map_cuda(e);
     if (j.batched) {
         if ((e = sgr::launch_fill_gid(j.gid_dev, j.vbase_dev, j.G, j.n, st)) != cudaSuccess)
             return map_cuda(e);
     }
     if ((e = cudaEventRecord(c->ev0, st)) != cudaSuccess) return map_cuda(e);
-    if ((e = sgr::launch_color(p, fast, j.batched, grid, st)) != cudaSuccess) return map_cuda(e);
+    int grid = 0;
+    if ((e = launch_rounds(p, fast, j.batched, c->occ[fast][j.batched], c->occ_front[j.batched], c->sms,
+                           t, st, &grid)) != cudaSuccess)
+        return map_cuda(e);
     if ((e = cudaEventRecord(c->ev1, st)) != cudaSuccess) return map_cuda(e);
     if ((e = cudaMemcpyAsync(c->host_ctr, p.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
@@ -357,7 +398,8 @@ int sgr_get_tuning(sgr_tuning *out) {
 int sgr_set_tuning(const sgr_tuning *in) {
     if (!in) return SGR_ERR_INVALID_ARG;
     sgr_tuning t = current_tuning();
-    if (in->reserved) return SGR_ERR_INVALID_ARG;
+    if (in->active_lists < 0 || in->active_lists > 2) return SGR_ERR_INVALID_ARG;
+    t.active_lists = in->active_lists;
     if (in->light_max) {
         if (in->light_max < 1 || in->light_max > sgr::kLightMaxStage) return SGR_ERR_INVALID_ARG;
         t.light_max = in->light_max;
@@ -438,6 +480,7 @@ int sgr_color(int32_t n, const int32_t *row_offsets, const int32_t *col_idx, int
     j.ro = row_offsets;
     j.ci = col_idx;
     j.colors = colors_out;
+    j.front = true;
     return run_job(c, j, mode, st, num_colors);
 }
 
@@ -476,6 +519,7 @@ int sgr_color_host(int32_t n, const int32_t *ro_h, const int32_t *ci_h, int32_t 
     j.ro = ro_d;
     j.ci = ci_d;
     j.colors = co_d;
+    j.front = true;
     rc = run_job(c, j, mode, st, num_colors);
     if (rc != SGR_OK) return rc;
     if ((e = cudaMemcpyAsync(colors_h, co_d, (size_t)n * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -519,6 +563,7 @@ int sgr_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
     j.batched = true;
     j.G = G;
     j.fast = (mode & SGR_MODE_MASK) == SGR_MODE_FAST;
+    j.front = true;
     // the batch tail of the arena: gid, vbase, ebase, per-graph k (see run_job)
     const sgr_tuning t = current_tuning();
     size_t zero_bytes = 0;
@@ -725,21 +770,22 @@ extern "C" int sgr_color_noalloc(int32_t n, const int32_t *row_offsets, const in
     j.ci = col_idx;
     j.colors = colors_out;
     size_t zero_bytes = 0;
+    j.front = true;  // the activation lists only if they fit beside the rest
+    if (layout(j, t, nullptr, nullptr, &zero_bytes) > kNoAllocScratchBytes) j.front = false;
     if (layout(j, t, nullptr, nullptr, &zero_bytes) > kNoAllocScratchBytes)
         return SGR_ERR_INVALID_ARG;  // the graph needs more scratch than the fixed array holds
     Params p;
     layout(j, t, base, &p, nullptr);
     p.rule = (mode & SGR_RULE_MASK) >> 4;
     p.max_rounds = (long long)n + 1;
-    int per_sm = 0, sms = 0;
+    int per_sm = 0, per_sm_f = 0, sms = 0;
     if (sgr::occupancy_blocks_per_sm(fast, false, &per_sm) != 0) return SGR_ERR_CUDA;
+    if (sgr::occupancy_blocks_per_sm_front(false, &per_sm_f) != 0) return SGR_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SGR_ERR_CUDA;
-    if (t.blocks_per_sm > 0) per_sm = std::min(per_sm, t.blocks_per_sm);
-    if (per_sm < 1) return SGR_ERR_CUDA;
-    const int grid = per_sm * sms;
-    p.nblocks = (unsigned)grid;
     if ((e = cudaMemsetAsync(base, 0, zero_bytes, st)) != cudaSuccess) return map_cuda(e);
-    if ((e = sgr::launch_color(p, fast, false, grid, st)) != cudaSuccess) return map_cuda(e);
+    int grid = 0;
+    if ((e = launch_rounds(p, fast, false, per_sm, per_sm_f, sms, t, st, &grid)) != cudaSuccess)
+        return map_cuda(e);
     Counters h;
     if ((e = cudaMemcpyAsync(&h, p.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return map_cuda(e);

@@ -19,6 +19,11 @@
 //   witness[n]           det mode: the neighbour that beat v last time, or -1.
 //   hub scatter list     det mode: hubs committed this round (slot + chunk
 //                        base), whose colors are scattered at the next round.
+//   activation lists     det mode al/am/ah(+acb), by parity: the worklist
+//                        vertices whose tentative color a commit of the last
+//                        round made stale (a neighbour committed that color).
+//   astamp[n]            det mode: the round v was last put on an activation list.
+//   vslot[n]             det mode: hub slot of v, or -1 (light) / -2 (medium).
 //   Counters             list sizes, grid barrier, max
 //                        color so far, error code, statistics.
 #pragma once
@@ -37,6 +42,7 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kLightUnroll = 4;                  // 32-vertex sub-tiles per warp and light tile
 constexpr int kLightTile = kBlock * kLightUnroll;
 constexpr int kSlowCap = 2 * kLightTile;          // det: queued slow vertices per CTA
+constexpr int kPushCap = 4096;                   // det: vertices staged per CTA before a list append
 constexpr int kScatterChunk = 128;               // det: entries per hub-scatter work item (one step)
 constexpr int kMinBlocks = 3;                    // CTAs per SM the register budget targets
 constexpr int kLightMaxStage = 32;               // largest light degree (staged rows per lane)
@@ -53,6 +59,13 @@ struct Counters {
     unsigned long long h64[2];      // hub lists: (entries << 32) | total chunks
     unsigned int nul[2], num[2];    // det: unsettled light / medium vertices of the round
     unsigned long long uh64[2];     // det: unsettled hubs (entries << 32 | chunks)
+    unsigned int nal[2], nam[2];    // det: activated light / medium vertices
+    unsigned long long ah64[2];     // det: activated hubs (entries << 32 | chunks)
+    unsigned long long adeg[2];     // det: degree sum of the activated vertices
+    unsigned long long wcount;      // det: |W_r|, vertices not yet committed
+    unsigned long long nroots;      // det: vertices with no entry below them (round-1 keepers on ascending rows)
+    unsigned long long t_start;     // globaltimer at the start of the launch that ran init
+    int handoff;                    // det: init handed the rounds to the activation-list kernel
     unsigned long long bar;         // grid barrier: arrivals (bits 0..62), error flag (bit 63)
     unsigned int nslots;            // hub slots handed out
     unsigned int hwords;            // hub bitmap words handed out
@@ -96,6 +109,14 @@ struct Params {
     long long np;              // plane stride (>= n, multiple of 64)
     int32_t *lowdeg;           // det
     int32_t *witness;          // det: the neighbour that last beat v, or -1
+    int32_t *al[2];            // det: activation lists (light, medium, hub slots + chunk bases)
+    int32_t *am[2];
+    int32_t *ah[2];
+    unsigned int *acb[2];
+    int32_t *astamp;           // det: round v was last activated for (zero-initialised)
+    int32_t *vslot;            // det: hub slot, -1 light, -2 medium
+    int front_ok;              // det: the activation lists are allocated
+    int front_policy;          // det: 0 when few round-1 keepers, 1 never, 2 always
     int32_t *sw;               // det: hub scatter list slots
     unsigned int *scb;         // det: hub scatter list chunk bases
     Counters *ctr;
@@ -133,6 +154,10 @@ std::mutex &device_launch_mutex(int device);
 // Launches (implemented in sgr_kernels.cu).
 int occupancy_blocks_per_sm(bool fast, bool batched, int *out);
 cudaError_t launch_color(const Params &p, bool fast, bool batched, int grid, cudaStream_t s);
+// Deterministic rounds on the activation lists (after an init launch that set
+// Counters::handoff; returns at once if it did not).
+int occupancy_blocks_per_sm_front(bool batched, int *out);
+cudaError_t launch_color_front(const Params &p, bool batched, int grid, cudaStream_t s);
 cudaError_t launch_admit(const Params &p, int g, long long vb, int32_t n, int par, int grid,
                          cudaStream_t s);
 cudaError_t launch_slot_status(const int32_t *colors, const long long *vbase, const int32_t *nv,

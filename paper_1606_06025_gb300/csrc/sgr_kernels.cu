@@ -169,6 +169,7 @@ struct Acc {
     unsigned long long w = 0, d = 0, dscan = 0, next = 0, scatter = 0;
     unsigned long long kdeg = 0;  // det: degree sum of this phase's keepers
     unsigned long long slow = 0;  // det: vertices that rescanned their row
+    unsigned long long keep = 0;  // det: vertices committed in this phase
     int kmax = 0;
 };
 
@@ -187,6 +188,14 @@ __device__ __forceinline__ unsigned rot_block(int part) {
 
 __device__ __forceinline__ unsigned rot_warp(int part) {
     return (rot_block(part) * blockDim.x + threadIdx.x) >> 5;
+}
+
+// Batch of worklist entries a warp takes at a time: spread a short list over
+// all warps, up to 32 entries (one per lane) for long lists.
+__device__ __forceinline__ unsigned warp_batch(unsigned cnt) {
+    const unsigned NW = total_warps();
+    const unsigned b = (cnt + NW - 1) / NW;
+    return b < 1 ? 1 : (b > 32 ? 32 : b);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -262,47 +271,62 @@ __device__ __forceinline__ int warp_first_fit(const int32_t *__restrict__ ci, lo
 
 // Order-preserving block compaction of kLightUnroll flags per thread: item u
 // of thread (warp w, lane l) sits at tile position (w * kLightUnroll + u) * 32
-// + l.  One atomicAdd per CTA tile.
+// + l.  The 32 sub-tile counts are scanned by warp 0; one atomicAdd per CTA
+// tile.  out == nullptr only counts the flags.
+static_assert(kWarps * kLightUnroll == 32, "one scan lane per sub-tile");
+
+// Exclusive scan of one count per lane of warp 0; lane 0 reserves the total
+// at *counter (when out != nullptr) and every lane gets its absolute start.
+__device__ __forceinline__ unsigned warp_reserve(unsigned c, unsigned *counter, bool take,
+                                                 unsigned &total) {
+    const int lane = threadIdx.x & 31;
+    unsigned incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    total = __shfl_sync(kFull, incl, 31);
+    unsigned base = 0;
+    if (lane == 0 && take && total) base = atomicAdd(counter, total);
+    return __shfl_sync(kFull, base, 0) + incl - c;
+}
+
 __device__ __forceinline__ void block_push(const bool (&flag)[kLightUnroll],
                                            const int32_t (&item)[kLightUnroll],
                                            unsigned *counter, int32_t *out,
                                            unsigned long long &pushed) {
-    __shared__ unsigned s_cnt[kWarps][kLightUnroll];
-    __shared__ unsigned s_base;
+    __shared__ unsigned s_pos[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned bal[kLightUnroll];
 #pragma unroll
     for (int u = 0; u < kLightUnroll; ++u) {
         bal[u] = __ballot_sync(kFull, flag[u]);
-        if (lane == 0) s_cnt[warp][u] = __popc(bal[u]);
+        if (lane == 0) s_pos[warp * kLightUnroll + u] = __popc(bal[u]);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned tot = 0;
-        for (int w = 0; w < kWarps; ++w)
-            for (int u = 0; u < kLightUnroll; ++u) {
-                const unsigned c = s_cnt[w][u];
-                s_cnt[w][u] = tot;
-                tot += c;
-            }
-        s_base = tot ? atomicAdd(counter, tot) : 0u;
-        pushed += tot;
+    if (warp == 0) {
+        unsigned tot;
+        const unsigned pos = warp_reserve(s_pos[lane], counter, out != nullptr, tot);
+        s_pos[lane] = pos;
+        if (lane == 0) pushed += tot;
     }
     __syncthreads();
+    if (out) {
 #pragma unroll
-    for (int u = 0; u < kLightUnroll; ++u)
-        if (flag[u]) out[s_base + s_cnt[warp][u] + __popc(bal[u] & lanemask_lt())] = item[u];
+        for (int u = 0; u < kLightUnroll; ++u)
+            if (flag[u]) out[s_pos[warp * kLightUnroll + u] + __popc(bal[u] & lanemask_lt())] = item[u];
+    }
     __syncthreads();
 }
 
 // Two order-preserving block compactions in one pass (flags a go to outa,
-// flags b to outb): one scan, the two atomics issued back to back.
+// flags b to outb): two scans in warp 0, the two atomics issued back to back.
 __device__ __forceinline__ void block_push2(const bool (&fa)[kLightUnroll], const bool (&fb)[kLightUnroll],
                                             const int32_t (&item)[kLightUnroll], unsigned *ca,
                                             int32_t *outa, unsigned *cb, int32_t *outb,
                                             unsigned long long &pushed_a) {
-    __shared__ unsigned s_a[kWarps][kLightUnroll], s_b[kWarps][kLightUnroll];
-    __shared__ unsigned s_base[2];
+    __shared__ unsigned s_a[32], s_b[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned ba[kLightUnroll], bb[kLightUnroll];
 #pragma unroll
@@ -310,47 +334,52 @@ __device__ __forceinline__ void block_push2(const bool (&fa)[kLightUnroll], cons
         ba[u] = __ballot_sync(kFull, fa[u]);
         bb[u] = __ballot_sync(kFull, fb[u]);
         if (lane == 0) {
-            s_a[warp][u] = __popc(ba[u]);
-            s_b[warp][u] = __popc(bb[u]);
+            s_a[warp * kLightUnroll + u] = __popc(ba[u]);
+            s_b[warp * kLightUnroll + u] = __popc(bb[u]);
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned ta = 0, tb = 0;
-        for (int w = 0; w < kWarps; ++w)
-            for (int u = 0; u < kLightUnroll; ++u) {
-                const unsigned x = s_a[w][u], y = s_b[w][u];
-                s_a[w][u] = ta;
-                s_b[w][u] = tb;
-                ta += x;
-                tb += y;
+    if (warp == 0) {
+        const unsigned ca_l = s_a[lane], cb_l = s_b[lane];
+        unsigned ia = ca_l, ib = cb_l;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned x = __shfl_up_sync(kFull, ia, o), y = __shfl_up_sync(kFull, ib, o);
+            if (lane >= o) {
+                ia += x;
+                ib += y;
             }
-        const unsigned oa = ta ? atomicAdd(ca, ta) : 0u;
-        const unsigned ob = tb ? atomicAdd(cb, tb) : 0u;
-        s_base[0] = oa;
-        s_base[1] = ob;
-        pushed_a += ta;
+        }
+        const unsigned ta = __shfl_sync(kFull, ia, 31), tb = __shfl_sync(kFull, ib, 31);
+        unsigned oa = 0, ob = 0;
+        if (lane == 0) {
+            if (ta) oa = atomicAdd(ca, ta);
+            if (tb) ob = atomicAdd(cb, tb);
+            pushed_a += ta;
+        }
+        s_a[lane] = __shfl_sync(kFull, oa, 0) + ia - ca_l;
+        s_b[lane] = __shfl_sync(kFull, ob, 0) + ib - cb_l;
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < kLightUnroll; ++u) {
         const unsigned below = lanemask_lt();
-        if (fa[u]) outa[s_base[0] + s_a[warp][u] + __popc(ba[u] & below)] = item[u];
-        if (fb[u]) outb[s_base[1] + s_b[warp][u] + __popc(bb[u] & below)] = item[u];
+        if (fa[u]) outa[s_a[warp * kLightUnroll + u] + __popc(ba[u] & below)] = item[u];
+        if (fb[u]) outb[s_b[warp * kLightUnroll + u] + __popc(bb[u] & below)] = item[u];
     }
     __syncthreads();
 }
 
-// Warp-level order-preserving push of one flag per lane.
+// Warp-level order-preserving push of one flag per lane (out == nullptr: count
+// only).
 __device__ __forceinline__ void warp_push(bool flag, int32_t item, unsigned *counter,
                                           int32_t *out, unsigned long long &pushed) {
     const unsigned bal = __ballot_sync(kFull, flag);
     if (!bal) return;
+    if ((threadIdx.x & 31) == 0) pushed += (unsigned long long)__popc(bal);
+    if (!out) return;
     unsigned pos = 0;
-    if ((threadIdx.x & 31) == 0) {
-        pos = atomicAdd(counter, (unsigned)__popc(bal));
-        pushed += (unsigned long long)__popc(bal);
-    }
+    if ((threadIdx.x & 31) == 0) pos = atomicAdd(counter, (unsigned)__popc(bal));
     pos = __shfl_sync(kFull, pos, 0);
     if (flag) out[pos + __popc(bal & lanemask_lt())] = item;
 }
@@ -386,7 +415,119 @@ __device__ __forceinline__ void hub_list_push(unsigned long long *ctr64, int32_t
     cb[k] = (unsigned)old;
 }
 
-// ------------------------------------------------------------ det: FirstFit
+// ------------------------------------------------------------ det: list sets and the CTA push buffer
+
+// A light / medium / hub list triple with its counters, as pushes see it:
+// the unsettled lists U (kind 0) or the activation lists A (kind 1) of one
+// parity.  The pointers are taken from the launch parameters where they are
+// used, so that no register holds them across the round loop.
+struct ListSet {
+    int kind;
+    int par;
+};
+
+__device__ __forceinline__ int32_t *ls_l(const Params &p, ListSet L) { return L.kind ? p.al[L.par] : p.ul[L.par]; }
+__device__ __forceinline__ int32_t *ls_m(const Params &p, ListSet L) { return L.kind ? p.am[L.par] : p.um[L.par]; }
+__device__ __forceinline__ int32_t *ls_h(const Params &p, ListSet L) { return L.kind ? p.ah[L.par] : p.uh[L.par]; }
+__device__ __forceinline__ unsigned *ls_hcb(const Params &p, ListSet L) { return L.kind ? p.acb[L.par] : p.ucb[L.par]; }
+__device__ __forceinline__ unsigned *ls_nl(const Params &p, ListSet L) {
+    return L.kind ? &p.ctr->nal[L.par] : &p.ctr->nul[L.par];
+}
+__device__ __forceinline__ unsigned *ls_nm(const Params &p, ListSet L) {
+    return L.kind ? &p.ctr->nam[L.par] : &p.ctr->num[L.par];
+}
+__device__ __forceinline__ unsigned long long *ls_h64(const Params &p, ListSet L) {
+    return L.kind ? &p.ctr->ah64[L.par] : &p.ctr->uh64[L.par];
+}
+// degree sum of the pushed vertices: kept for the activation lists only
+__device__ __forceinline__ unsigned long long *ls_deg(const Params &p, ListSet L) {
+    return L.kind ? &p.ctr->adeg[L.par] : nullptr;
+}
+
+template <bool kBatched>
+__device__ __forceinline__ long long vertex_degree(const Params &p, int32_t v) {
+    long long s, e;
+    int32_t vb;
+    row_of<kBatched>(p, v, s, e, vb);
+    return e - s;
+}
+
+// Append one vertex to its bin of L (one lane, global atomics).
+template <bool kBatched>
+__device__ void list_push_one(const Params &p, ListSet L, int32_t v) {
+    const int32_t bin = __ldcg(p.vslot + v);
+    const long long d = (L.kind || bin >= 0) ? vertex_degree<kBatched>(p, v) : 0;
+    if (bin == -1) {
+        ls_l(p, L)[atomicAdd(ls_nl(p, L), 1u)] = v;
+    } else if (bin == -2) {
+        ls_m(p, L)[atomicAdd(ls_nm(p, L), 1u)] = v;
+    } else {
+        hub_list_push(ls_h64(p, L), ls_h(p, L), ls_hcb(p, L), bin,
+                      (unsigned)((d + p.chunk - 1) / p.chunk));
+    }
+    if (L.kind) atomicAdd(ls_deg(p, L), (unsigned long long)d);
+}
+
+// Vertices pushed by lanes on divergent paths are staged in shared memory and
+// appended to their lists by the whole CTA at the end of the phase
+// (flush_push): one atomic per bin and tile instead of one per vertex.  A
+// full buffer falls back to list_push_one.
+struct PushBuf {
+    int32_t *v;
+    unsigned *n;
+};
+
+__device__ __forceinline__ PushBuf push_buf() {
+    __shared__ int32_t s_pv[kPushCap];
+    __shared__ unsigned s_pn;
+    return PushBuf{s_pv, &s_pn};
+}
+
+template <bool kBatched>
+__device__ __forceinline__ void stage_push(const Params &p, ListSet L, int32_t v) {
+    const PushBuf b = push_buf();
+    const unsigned pos = atomicAdd(b.n, 1u);
+    if (pos < (unsigned)kPushCap) b.v[pos] = v;
+    else list_push_one<kBatched>(p, L, v);
+}
+
+// Bin the staged vertices by vslot and append them to L (all threads of the
+// CTA; ends with the buffer empty).
+template <bool kBatched>
+__device__ void flush_push(const Params &p, ListSet L) {
+    const PushBuf b = push_buf();
+    __syncthreads();
+    const unsigned cnt = min(*b.n, (unsigned)kPushCap);
+    unsigned long long dsum = 0, dummy = 0;
+    for (unsigned base = 0; base < cnt; base += kLightTile) {
+        bool fl[kLightUnroll], fm[kLightUnroll];
+        int32_t it[kLightUnroll];
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) {
+            const unsigned idx = base + tile_index(0, u);
+            const bool act = idx < cnt;
+            it[u] = act ? b.v[idx] : 0;
+            const int32_t bin = act ? __ldcg(p.vslot + it[u]) : -3;
+            fl[u] = bin == -1;
+            fm[u] = bin == -2;
+            if (act && (L.kind || bin >= 0)) {
+                const long long d = vertex_degree<kBatched>(p, it[u]);
+                dsum += (unsigned long long)d;
+                if (bin >= 0)
+                    hub_list_push(ls_h64(p, L), ls_h(p, L), ls_hcb(p, L), bin,
+                                  (unsigned)((d + p.chunk - 1) / p.chunk));
+            }
+        }
+        block_push2(fl, fm, it, ls_nl(p, L), ls_l(p, L), ls_nm(p, L), ls_m(p, L), dummy);
+    }
+    if (L.kind) {
+        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+        if ((threadIdx.x & 31) == 0 && dsum) atomicAdd(ls_deg(p, L), dsum);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *b.n = 0;
+    __syncthreads();
+}
 
 // ------------------------------------------------------------ det: FirstFit with witness split
 //
@@ -408,26 +549,14 @@ __device__ __forceinline__ int bitmap_color(const Params &p, int32_t v, unsigned
     return 0;
 }
 
-// FirstFit and witness check for U vertices per lane; returns tentative
-// colors in c[] and whether each is settled.
+// First-fit colors of U vertices per lane (v[u] active if act[u], w0[u] the
+// first word of its bitmap).  A vertex whose bitmap is full (colors 1..256
+// all forbidden) is resolved by a scan of its row by the whole warp.
 template <bool kBatched, int U>
-__device__ __forceinline__ void det_assign_lane(const Params &p, const bool (&act)[U],
-                                                const int32_t (&v)[U], int (&c)[U],
-                                                bool (&settled)[U]) {
+__device__ __forceinline__ void first_fit_lane(const Params &p, const bool (&act)[U],
+                                               const int32_t (&v)[U], const unsigned (&w0)[U],
+                                               int (&c)[U]) {
     const int lane = threadIdx.x & 31;
-    unsigned w0[U], ww0[U];
-    int32_t wit[U];
-    int cw[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        w0[u] = act[u] ? __ldcg(p.bm + v[u]) : 0u;
-        wit[u] = act[u] ? __ldcg(p.witness + v[u]) : -1;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        cw[u] = wit[u] >= 0 ? __ldcg(p.colors + wit[u]) : 0;
-        ww0[u] = wit[u] >= 0 ? __ldcg(p.bm + wit[u]) : 0u;
-    }
 #pragma unroll
     for (int u = 0; u < U; ++u) c[u] = act[u] ? bitmap_color(p, v[u], w0[u]) : 0;
 #pragma unroll
@@ -444,6 +573,28 @@ __device__ __forceinline__ void det_assign_lane(const Params &p, const bool (&ac
             if (lane == src) c[u] = cx;
         }
     }
+}
+
+// FirstFit and witness check for U vertices per lane; returns tentative
+// colors in c[] and whether each is settled.
+template <bool kBatched, int U>
+__device__ __forceinline__ void det_assign_lane(const Params &p, const bool (&act)[U],
+                                                const int32_t (&v)[U], int (&c)[U],
+                                                bool (&settled)[U]) {
+    unsigned w0[U], ww0[U];
+    int32_t wit[U];
+    int cw[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        w0[u] = act[u] ? __ldcg(p.bm + v[u]) : 0u;
+        wit[u] = act[u] ? __ldcg(p.witness + v[u]) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        cw[u] = wit[u] >= 0 ? __ldcg(p.colors + wit[u]) : 0;
+        ww0[u] = wit[u] >= 0 ? __ldcg(p.bm + wit[u]) : 0u;
+    }
+    first_fit_lane<kBatched, U>(p, act, v, w0, c);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int tw = (act[u] && wit[u] >= 0 && cw[u] < 0) ? bitmap_color(p, wit[u], ww0[u]) : 0;
@@ -531,6 +682,171 @@ __device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64
     }
 }
 
+// ------------------------------------------------------------ det: rounds on the activation lists
+//
+// A worklist vertex keeps its tentative color and its loss from round to
+// round unless a commit touches it: its first-fit color changes only when a
+// neighbour commits that very color (the commit then puts it on an
+// activation list A_{r+1}), and its loss only when its witness changes color
+// or commits.  Once few vertices are touched per round, phase A FirstFits
+// only A_r and hands ConflictResolve A_r plus the vertices whose witness is
+// in A_r (its dependents); every other worklist vertex is left as it is,
+// since it would compute the same color and lose to the same witness again.
+// Results are those of the full round.
+
+// Dependents of y among entries [a, b) of its row (one lane; 16 entries per
+// step with every load of the step in flight): worklist vertices whose
+// witness is y and that are not on A_r themselves.
+template <bool kBatched>
+__device__ __forceinline__ void push_dependents_lane(const Params &p, int32_t y, long long a,
+                                                     long long b, int32_t vb, int r,
+                                                     ListSet L) {
+    for (long long q0 = a >> 2; (q0 << 2) < b; q0 += 4) {
+        int4 x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            x[k] = ((q0 + k) << 2) < b ? load4(p.ci, q0 + k, p.m) : make_int4(0, 0, 0, 0);
+        int32_t z[4][4], wz[4][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long i = ((q0 + k) << 2) + j;
+                z[k][j] = vb + elem(x[k], j);
+                const bool ok = i >= a && i < b && (unsigned)z[k][j] < (unsigned)p.n;
+                wz[k][j] = ok ? __ldcg(p.witness + z[k][j]) : -1;
+            }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (wz[k][j] == y && __ldcg(p.colors + z[k][j]) < 0 &&
+                    __ldcg(p.astamp + z[k][j]) != r)
+                    stage_push<kBatched>(p, L, z[k][j]);
+    }
+}
+
+// The same over entries [a, b) by the whole warp (one 16-byte block per lane
+// and step).
+template <bool kBatched>
+__device__ __forceinline__ void push_dependents_warp(const Params &p, int32_t y, long long a,
+                                                     long long b, int32_t vb, int r,
+                                                     ListSet L) {
+    for (long long q = (a >> 2) + (threadIdx.x & 31); (q << 2) < b; q += 32) {
+        const int4 x = load4(p.ci, q, p.m);
+        int32_t z[4], wz[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long i = (q << 2) + k;
+            z[k] = vb + elem(x, k);
+            const bool ok = i >= a && i < b && (unsigned)z[k] < (unsigned)p.n;
+            wz[k] = ok ? __ldcg(p.witness + z[k]) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (wz[k] == y && __ldcg(p.colors + z[k]) < 0 && __ldcg(p.astamp + z[k]) != r)
+                stage_push<kBatched>(p, L, z[k]);
+    }
+}
+
+// A_r light vertices, one per lane: FirstFit, then the vertex and its
+// dependents go to ConflictResolve (staged for L = U_r).  With ascending rows
+// and the low-keeps rule a dependent of y is above y, so only the entries
+// above y are read.
+template <bool kBatched>
+__device__ void front_assign_light(const Params &p, int par, unsigned cnt, int r, bool prefix,
+                                   ListSet L) {
+    const int32_t *list = p.al[par];
+    const unsigned NW = total_warps();
+    for (unsigned base = rot_warp(2) * 32; base < cnt; base += NW * 32) {
+        const unsigned idx = base + (threadIdx.x & 31);
+        const bool act[1] = {idx < cnt};
+        const int32_t v[1] = {act[0] ? __ldcg(list + idx) : 0};
+        const unsigned w0[1] = {act[0] ? __ldcg(p.bm + v[0]) : 0u};
+        long long s = 0, e = 0;
+        int32_t vb = 0;
+        int ld = 0;
+        if (act[0]) {
+            row_of<kBatched>(p, v[0], s, e, vb);
+            if (prefix) ld = __ldcg(p.lowdeg + v[0]);
+        }
+        int c[1];
+        first_fit_lane<kBatched, 1>(p, act, v, w0, c);
+        if (act[0]) {
+            __stcg(p.colors + v[0], -c[0]);
+            stage_push<kBatched>(p, L, v[0]);
+            push_dependents_lane<kBatched>(p, v[0], s + ld, e, vb, r, L);
+        }
+    }
+}
+
+// A_r medium vertices: FirstFit one per lane, dependents by the whole warp.
+template <bool kBatched>
+__device__ void front_assign_medium(const Params &p, int par, unsigned cnt, int r, bool prefix,
+                                    ListSet L) {
+    const int lane = threadIdx.x & 31;
+    const int32_t *list = p.am[par];
+    const unsigned NW = total_warps(), B = warp_batch(cnt);
+    for (unsigned b0 = rot_warp(1) * B; b0 < cnt; b0 += NW * B) {
+        const int nb = (int)min(B, cnt - b0);
+        const bool act[1] = {lane < nb};
+        const int32_t v[1] = {act[0] ? __ldcg(list + b0 + lane) : 0};
+        const unsigned w0[1] = {act[0] ? __ldcg(p.bm + v[0]) : 0u};
+        long long sl = 0, el = 0;
+        int32_t vbl = 0;
+        int ld = 0;
+        if (act[0]) {
+            row_of<kBatched>(p, v[0], sl, el, vbl);
+            if (prefix) ld = __ldcg(p.lowdeg + v[0]);
+        }
+        int c[1];
+        first_fit_lane<kBatched, 1>(p, act, v, w0, c);
+        if (act[0]) {
+            __stcg(p.colors + v[0], -c[0]);
+            stage_push<kBatched>(p, L, v[0]);
+        }
+        for (int j = 0; j < nb; ++j) {
+            const int32_t y = __shfl_sync(kFull, v[0], j), vb = __shfl_sync(kFull, vbl, j);
+            const long long a = __shfl_sync(kFull, sl, j) + __shfl_sync(kFull, ld, j);
+            const long long e = __shfl_sync(kFull, el, j);
+            push_dependents_warp<kBatched>(p, y, a, e, vb, r, L);
+        }
+    }
+}
+
+// A_r hubs: warp items of `chunk` row entries; item 0 also FirstFits the hub.
+template <bool kBatched>
+__device__ void front_assign_hubs(const Params &p, int par, unsigned long long h64, int r,
+                                  bool prefix, ListSet L) {
+    const int lane = threadIdx.x & 31;
+    const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
+    const long long CH = p.chunk;
+    const unsigned NW = total_warps();
+    for (unsigned q = global_warp(); q < nch; q += NW) {
+        const unsigned i = hub_entry(p.acb[par], cnt, q);
+        const int32_t slot = __ldcg(p.ah[par] + i);
+        const unsigned j = q - __ldcg(p.acb[par] + i);
+        const int32_t v = __ldcg(p.hvert + slot);
+        long long s, e;
+        int32_t vb;
+        row_of<kBatched>(p, v, s, e, vb);
+        if (j == 0) {
+            const bool act[1] = {lane == 0};
+            const int32_t vv[1] = {v};
+            const unsigned w0[1] = {lane == 0 ? __ldcg(p.bm + v) : 0u};
+            int c[1];
+            first_fit_lane<kBatched, 1>(p, act, vv, w0, c);
+            if (lane == 0) {
+                __stcg(p.colors + v, -c[0]);
+                stage_push<kBatched>(p, L, v);
+            }
+        }
+        const long long lo = prefix ? s + __ldcg(p.lowdeg + v) : s;
+        const long long a = max(lo, s + (long long)j * CH), b = min(e, s + (long long)(j + 1) * CH);
+        if (a < b) push_dependents_warp<kBatched>(p, v, a, b, vb, r, L);
+    }
+}
+
 // ------------------------------------------------------------ det: ConflictResolve
 //
 // v (tentative color c) loses iff a neighbour w that wins against it under
@@ -597,22 +913,45 @@ __device__ __forceinline__ int32_t det_scan_lane(const Params &p, int32_t v, int
     return -1;
 }
 
+// A commit of color c reaches worklist neighbour w: if w holds tentative
+// color c its first-fit color changes, so w goes onto the activation list of
+// round act_r (once, whichever commit gets there first).
+template <bool kBatched>
+__device__ __forceinline__ void activate(const Params &p, int32_t w, int cw, int c, int act_r,
+                                         ListSet A) {
+    if (cw == -c && atomicMax(p.astamp + w, act_r) < act_r) stage_push<kBatched>(p, A, w);
+}
+
 // Record final color c in the bitmaps of the neighbours [a, b) (lanes lane0,
 // lane0 + stride, ... over 16-byte blocks).  Colors above 256 are not
-// recorded; FirstFit then falls back to a scan.
+// recorded; FirstFit then falls back to a scan.  act_r > 0: also activate
+// the neighbours that hold tentative color c.
+template <bool kBatched>
 __device__ __forceinline__ void scatter_color(const Params &p, int c, long long a, long long b,
-                                              int32_t vb, int lane0, int stride) {
-    if (c > 256) return;
+                                              int32_t vb, int lane0, int stride, int act_r,
+                                              ListSet A) {
+    const bool bits = c <= 256;
+    if (!bits && !act_r) return;
     unsigned *plane = p.bm + (size_t)((c - 1) >> 5) * p.np;
     const unsigned bit = 1u << ((c - 1) & 31);
     for (long long q = (a >> 2) + lane0; (q << 2) < b; q += stride) {
         const int4 x = load4(p.ci, q, p.m);
         const long long i0 = q << 2;
+        int32_t w[4];
+        bool ok[4];
+        int cw[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const long long i = i0 + k;
-            const int32_t w = vb + elem(x, k);
-            if (i >= a && i < b && (unsigned)w < (unsigned)p.n) atomicOr(plane + w, bit);
+            w[k] = vb + elem(x, k);
+            ok[k] = i >= a && i < b && (unsigned)w[k] < (unsigned)p.n;
+            cw[k] = (act_r && ok[k]) ? __ldcg(p.colors + w[k]) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!ok[k]) continue;
+            if (bits) atomicOr(plane + w[k], bit);
+            if (act_r) activate<kBatched>(p, w[k], cw[k], c, act_r, A);
         }
     }
 }
@@ -651,10 +990,12 @@ __device__ __forceinline__ int32_t scan_below(const Params &p, int c, long long 
 }
 
 // Record color c in the bitmaps of the neighbours [s, e) (one lane; three
-// 16-byte blocks loaded per batch).
+// 16-byte blocks loaded per batch); act_r > 0 also activates (see activate).
+template <bool kBatched>
 __device__ __forceinline__ void scatter_lane(const Params &p, int c, long long s, long long e,
-                                             int32_t vb) {
-    if (c > 256 || e <= s) return;
+                                             int32_t vb, int act_r, ListSet A) {
+    const bool bits = c <= 256;
+    if ((!bits && !act_r) || e <= s) return;
     unsigned *plane = p.bm + (size_t)((c - 1) >> 5) * p.np;
     const unsigned bit = 1u << ((c - 1) & 31);
     const long long q1 = (e + 3) >> 2;
@@ -662,13 +1003,25 @@ __device__ __forceinline__ void scatter_lane(const Params &p, int c, long long s
         int4 x[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) x[k] = q0 + k < q1 ? load4(p.ci, q0 + k, p.m) : make_int4(0, 0, 0, 0);
+        int32_t w[3][4];
+        bool ok[3][4];
+        int cw[3][4];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const long long i = ((q0 + k) << 2) + j;
-                const int32_t w = vb + elem(x[k], j);
-                if (i >= s && i < e && (unsigned)w < (unsigned)p.n) atomicOr(plane + w, bit);
+                w[k][j] = vb + elem(x[k], j);
+                ok[k][j] = i >= s && i < e && (unsigned)w[k][j] < (unsigned)p.n;
+                cw[k][j] = (act_r && ok[k][j]) ? __ldcg(p.colors + w[k][j]) : 0;
+            }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!ok[k][j]) continue;
+                if (bits) atomicOr(plane + w[k][j], bit);
+                if (act_r) activate<kBatched>(p, w[k][j], cw[k][j], c, act_r, A);
             }
     }
 }
@@ -677,7 +1030,8 @@ __device__ __forceinline__ void scatter_lane(const Params &p, int c, long long s
 // record a new witness or commit and scatter.  Returns true for a loser.
 template <bool kBatched>
 __device__ __forceinline__ bool det_resolve_slow(const Params &p, bool slow, int32_t v, int c,
-                                                 bool prefix, Acc &acc) {
+                                                 bool prefix, int act_r, ListSet A,
+                                                 Acc &acc) {
     if (!slow) return false;
     acc.slow++;
     long long s, e;
@@ -692,9 +1046,10 @@ __device__ __forceinline__ bool det_resolve_slow(const Params &p, bool slow, int
     }
     __stcg(p.colors + v, c);
     acc.kmax = max(acc.kmax, c);
+    acc.keep++;
     acc.kdeg += (unsigned long long)(e - s);
     acc.scatter += (unsigned long long)(e - s);
-    scatter_lane(p, c, s, e, vb);
+    scatter_lane<kBatched>(p, c, s, e, vb, act_r, A);
     return false;
 }
 
@@ -755,7 +1110,8 @@ __device__ __forceinline__ void det_light_fast(const Params &p, const int32_t *l
 
 template <bool kBatched>
 __device__ void det_light_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
-                                 unsigned *out_cnt, bool prefix, bool round1, Acc &acc) {
+                                 unsigned *out_cnt, bool prefix, bool round1, int act_r,
+                                 ListSet A, Acc &acc) {
     if (cnt < 2u * gridDim.x * kLightTile) {
         // short worklist: 32 entries per warp, spread over every warp of the grid
         const unsigned NW = total_warps();
@@ -766,7 +1122,8 @@ __device__ void det_light_detect(const Params &p, const int32_t *list, unsigned 
             det_light_fast<kBatched, 1>(p, list, cnt, idx, prefix, round1, flag, slow, v, c);
             bool lost = flag[0];
             if (__any_sync(kFull, slow[0]))
-                lost = det_resolve_slow<kBatched>(p, slow[0], v[0], c[0], prefix, acc) || lost;
+                lost = det_resolve_slow<kBatched>(p, slow[0], v[0], c[0], prefix, act_r, A, acc) ||
+                       lost;
             warp_push(lost, v[0], out_cnt, out, acc.next);
         }
         return;
@@ -809,7 +1166,7 @@ __device__ void det_light_detect(const Params &p, const int32_t *list, unsigned 
                 const bool sl = g + lane < nslow;
                 const int32_t v = sl ? s_sv[g + lane] : 0;
                 const int c = sl ? s_sc[g + lane] : 0;
-                const bool lost = det_resolve_slow<kBatched>(p, sl, v, c, prefix, acc);
+                const bool lost = det_resolve_slow<kBatched>(p, sl, v, c, prefix, act_r, A, acc);
                 warp_push(lost, v, out_cnt, out, acc.next);
             }
             __syncthreads();
@@ -894,17 +1251,10 @@ __device__ __forceinline__ int32_t det_scan_warp(const Params &p, int32_t v, int
     return -1;
 }
 
-// Batch of worklist entries a warp takes at a time: spread a short list over
-// all warps, up to 32 entries (one per lane) for long lists.
-__device__ __forceinline__ unsigned warp_batch(unsigned cnt) {
-    const unsigned NW = total_warps();
-    const unsigned b = (cnt + NW - 1) / NW;
-    return b < 1 ? 1 : (b > 32 ? 32 : b);
-}
-
 template <bool kBatched>
 __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
-                                  unsigned *out_cnt, bool prefix, Acc &acc) {
+                                  unsigned *out_cnt, bool prefix, int act_r, ListSet A,
+                                  Acc &acc) {
     const int lane = threadIdx.x & 31;
     const unsigned NW = total_warps(), B = warp_batch(cnt);
     for (unsigned b = rot_warp(1) * B; b < cnt; b += NW * B) {
@@ -936,25 +1286,29 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
                 if (lane == 0) {
                     __stcg(p.colors + v, c);
                     acc.kmax = max(acc.kmax, c);
+                    acc.keep++;
                     acc.kdeg += (unsigned long long)(e - s);
                     acc.scatter += (unsigned long long)(e - s);
                 }
-                scatter_color(p, c, s, e, vb, lane, 32);
+                scatter_color<kBatched>(p, c, s, e, vb, lane, 32, act_r, A);
             }
         }
         if (lost) {
-            unsigned pos = 0;
-            if (lane == 0) pos = atomicAdd(out_cnt, (unsigned)__popc(lost));
-            pos = __shfl_sync(kFull, pos, 0);
-            if ((lost >> lane) & 1u) out[pos + __popc(lost & lanemask_lt())] = vl;
             if (lane == 0) acc.next += (unsigned long long)__popc(lost);
+            if (out) {
+                unsigned pos = 0;
+                if (lane == 0) pos = atomicAdd(out_cnt, (unsigned)__popc(lost));
+                pos = __shfl_sync(kFull, pos, 0);
+                if ((lost >> lane) & 1u) out[pos + __popc(lost & lanemask_lt())] = vl;
+            }
         }
     }
 }
 
 template <bool kBatched>
 __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsigned *cbs,
-                               unsigned long long h64, int pn, bool prefix, Acc &acc) {
+                               unsigned long long h64, int pn, bool prefix, bool push_losers,
+                               Acc &acc) {
     const int lane = threadIdx.x & 31;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const long long CH = p.chunk;
@@ -1001,11 +1355,12 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
                 __stcg(p.hconf + slot, 0u);
                 __stcg(p.hdone + slot, 0ull);
                 if (lost) {
-                    hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
+                    if (push_losers) hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
                     acc.next += 1;
                 } else {
                     __stcg(p.colors + v, c);
                     acc.kmax = max(acc.kmax, c);
+                    acc.keep++;
                     acc.kdeg += (unsigned long long)deg;
                     acc.scatter += (unsigned long long)deg;
                     hub_list_push(&p.ctr->sc64, p.sw, p.scb, slot,
@@ -1018,7 +1373,8 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
 
 // Scatter the colors of the hubs committed in the last round (chunked).
 template <bool kBatched>
-__device__ void det_hub_scatter(const Params &p, unsigned long long sc64) {
+__device__ void det_hub_scatter(const Params &p, unsigned long long sc64, int act_r,
+                                ListSet A) {
     const int lane = threadIdx.x & 31;
     const unsigned cnt = (unsigned)(sc64 >> 32), nch = (unsigned)sc64;
     const long long CH = kScatterChunk;
@@ -1032,7 +1388,7 @@ __device__ void det_hub_scatter(const Params &p, unsigned long long sc64) {
         int32_t vb;
         row_of<kBatched>(p, v, s, e, vb);
         const long long a = s + (long long)j * CH, b = min(e, a + CH);
-        scatter_color(p, __ldcg(p.colors + v), a, b, vb, lane, 32);
+        scatter_color<kBatched>(p, __ldcg(p.colors + v), a, b, vb, lane, 32, act_r, A);
     }
 }
 
@@ -1425,7 +1781,7 @@ __device__ void init_phase(const Params &p) {
         if (i0 + 4 < p.m && x.w >= __ldg(p.ci + i0 + 4)) bad++;
     }
     // (2) binning of all vertices into W_1 (parity 1), in vertex order
-    unsigned long long boundary = 0, dummy = 0;
+    unsigned long long boundary = 0, dummy = 0, roots = 0;
     const unsigned nt = ((unsigned)p.n + kLightTile - 1) / kLightTile;
     for (unsigned t = blockIdx.x; t < nt; t += gridDim.x) {
         bool is_light[kLightUnroll], is_med[kLightUnroll];
@@ -1453,14 +1809,18 @@ __device__ void init_phase(const Params &p) {
                     else hi = mid;
                 }
                 p.lowdeg[v] = (int32_t)(lo - s);
+                roots += lo == s;
             }
             if (deg <= p.light_max) {
                 is_light[u] = true;
+                if (!kFast && p.front_ok) p.vslot[v] = -1;
             } else if (deg <= p.chunk) {
                 is_med[u] = true;
+                if (!kFast && p.front_ok) p.vslot[v] = -2;
             } else {
                 const unsigned slot = atomicAdd(&p.ctr->nslots, 1u);
                 const unsigned words = (unsigned)((deg + 2 + 31) / 32);
+                if (!kFast && p.front_ok) p.vslot[v] = (int32_t)slot;
                 p.hvert[slot] = v;
                 p.hbase[slot] = atomicAdd(&p.ctr->hwords, words);
                 hub_list_push(&p.ctr->h64[1], p.hw[1], p.hcb[1], (int32_t)slot,
@@ -1473,41 +1833,48 @@ __device__ void init_phase(const Params &p) {
     for (int o = 16; o > 0; o >>= 1) {
         bad += __shfl_xor_sync(kFull, bad, o);
         boundary += __shfl_xor_sync(kFull, boundary, o);
+        roots += __shfl_xor_sync(kFull, roots, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (bad) atomicAdd(&p.ctr->unsorted_pairs, bad);
         if (boundary) atomicAdd(&p.ctr->boundary_pairs, boundary);
+        if (roots) atomicAdd(&p.ctr->nroots, roots);
     }
 }
 
-// End of phase B: the CTA's largest committed color and (det) the degree sum
-// of its keepers, which leave the worklist.
+// End of phase B: the CTA's largest committed color and (det) the number and
+// degree sum of its keepers, which leave the worklist.
 __device__ void flush_phase(const Params &p, int kloc, unsigned long long kdeg,
-                            unsigned long long nslow) {
+                            unsigned long long nslow, unsigned long long nkeep) {
     __shared__ int s_k[kWarps];
-    __shared__ unsigned long long s_d[kWarps], s_s[kWarps];
+    __shared__ unsigned long long s_d[kWarps], s_s[kWarps], s_n[kWarps];
     int k = kloc;
     for (int o = 16; o > 0; o >>= 1) {
         k = max(k, __shfl_xor_sync(kFull, k, o));
         kdeg += __shfl_xor_sync(kFull, kdeg, o);
         nslow += __shfl_xor_sync(kFull, nslow, o);
+        nkeep += __shfl_xor_sync(kFull, nkeep, o);
     }
     if ((threadIdx.x & 31) == 0) {
         s_k[threadIdx.x >> 5] = k;
         s_d[threadIdx.x >> 5] = kdeg;
         s_s[threadIdx.x >> 5] = nslow;
+        s_n[threadIdx.x >> 5] = nkeep;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         int b = 0;
-        unsigned long long d = 0, sl = 0;
+        unsigned long long d = 0, sl = 0, nk = 0;
         for (int w = 0; w < kWarps; ++w) {
             b = max(b, s_k[w]);
             d += s_d[w];
             sl += s_s[w];
+            nk += s_n[w];
         }
-        if (b > 0) atomicMax(&p.ctr->kmax, b);  // no return value: nothing waits on it
+        // no return values below: nothing waits on these atomics
+        if (b > 0) atomicMax(&p.ctr->kmax, b);
         if (d) atomicAdd(&p.ctr->dcur, 0ull - d);
+        if (nk) atomicAdd(&p.ctr->wcount, 0ull - nk);
         if (sl) {
             atomicAdd(&p.ctr->nslow, sl);
             atomicAdd(&p.ctr->sum_rescan, sl);
@@ -1529,24 +1896,51 @@ __device__ void flush_stats(const Params &p, Acc &acc) {
     }
 }
 
-template <bool kFast, bool kBatched>
+// The round loop.  kFront (det only): rounds 2.. run on the activation lists;
+// the launch continues after an init launch of the kFront = false kernel that
+// handed the rounds over (Counters::handoff), and returns at once otherwise.
+// The two kinds of rounds are separate kernels so that neither pays for the
+// registers of the other.
+template <bool kFast, bool kBatched, bool kFront>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Params p) {
+    static_assert(!(kFast && kFront), "activation lists are a deterministic-mode path");
     __shared__ int32_t s_stage[kFast ? kWarps : 1][kFast ? 32 * kLightMaxStage : 1];
     int32_t *sbuf = s_stage[kFast ? (threadIdx.x >> 5) : 0];
     Acc acc;
     unsigned gen = 0;
     Counters *ctr = p.ctr;
     const bool recorder = blockIdx.x == 0 && threadIdx.x == 0;
-    const unsigned long long t0 = globaltimer();
+    unsigned long long t0 = globaltimer();
+    if (kFront && threadIdx.x == 0) *push_buf().n = 0;  // first used after a barrier
     bool sorted;
     long long r;
-    if (!p.resume) {
-        if (recorder && !kFast) ctr->dcur = (unsigned long long)p.m;
+    if (kFront) {
+        if (__ldcg(&ctr->handoff) == 0) return;  // the init launch colored everything
+        t0 = __ldcg(&ctr->t_start);
+        sorted = __ldcg(&ctr->unsorted_pairs) == __ldcg(&ctr->boundary_pairs);
+        r = 1;
+    } else if (!p.resume) {
+        if (recorder) {
+            ctr->t_start = t0;
+            if (!kFast) {
+                ctr->dcur = (unsigned long long)p.m;
+                ctr->wcount = (unsigned long long)p.n;
+            }
+        }
         init_phase<kFast, kBatched>(p);
         if (!grid_barrier(p, gen)) { flush_stats(p, acc); return; }
         if (recorder) ctr->t_init_ns = (long long)(globaltimer() - t0);
         sorted = __ldcg(&ctr->unsorted_pairs) == __ldcg(&ctr->boundary_pairs);
         r = 1;
+        if (!kFast && p.front_ok && p.front_policy != 1) {
+            // hand the rounds to the activation-list kernel when few vertices
+            // commit in round 1 (every CTA decides alike from the counters)
+            const bool few = sorted && p.rule == 0 && 8 * __ldcg(&ctr->nroots) < (unsigned long long)p.n;
+            if (p.front_policy == 2 || few) {
+                if (recorder) ctr->handoff = 1;
+                return;
+            }
+        }
     } else {  // continue the rounds of an earlier launch (graphs admitted in between)
         sorted = p.resume_sorted != 0;
         r = __ldcg(&ctr->round);
@@ -1560,9 +1954,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
         const unsigned nl = __ldcg(&ctr->nl[par]);
         const unsigned nm = __ldcg(&ctr->nm[par]);
         const unsigned long long h64 = __ldcg(&ctr->h64[par]);
-        const unsigned long long total =
-            (unsigned long long)nl + nm + (unsigned long long)(h64 >> 32);
-        if (total == 0) {
+        // |W_r|: the list sizes, or (activation lists: not every loser is
+        // pushed) the count of uncommitted vertices
+        const unsigned long long wsize =
+            kFront ? __ldcg(&ctr->wcount)
+                   : (unsigned long long)nl + nm + (unsigned long long)(h64 >> 32);
+        if (wsize == 0) {
             if (recorder && !kFast) ctr->sc64 = 0;  // nobody is left to read those bitmaps
             break;
         }
@@ -1570,11 +1967,25 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             if (recorder) raise_error(p, kErrNoConvergence);
             break;
         }
+        const bool front = kFront && r >= 2;  // this round runs on A_r
         if (!kFast) {  // colors of hubs committed last round go to their neighbours' bitmaps
             const unsigned long long sc64 = __ldcg(&ctr->sc64);
             if (sc64 >> 32) {
-                det_hub_scatter<kBatched>(p, sc64);
+                det_hub_scatter<kBatched>(p, sc64, kFront ? (int)r : 0, ListSet{1, par});
+                if (kFront) flush_push<kBatched>(p, ListSet{1, par});
                 if (!(ok = grid_barrier(p, gen))) break;
+            }
+        }
+        unsigned anl = 0, anm = 0;
+        unsigned long long ah = 0;
+        if (front) {  // A_r is complete now
+            anl = __ldcg(&ctr->nal[par]);
+            anm = __ldcg(&ctr->nam[par]);
+            ah = __ldcg(&ctr->ah64[par]);
+            if ((unsigned long long)anl + anm + (ah >> 32) == 0) {
+                // nothing can change: only a non-symmetric input gets here
+                if (recorder) raise_error(p, kErrNoConvergence);
+                break;
             }
         }
         if (recorder) {
@@ -1584,10 +1995,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
                 ctr->h64[pn] = 0;
             } else {  // det: W_{r+1}'s counters were cleared during the last phase B
                 ctr->sc64 = 0;
-                ctr->sum_w += total;                       // |W_r|
+                ctr->sum_w += wsize;                       // |W_r|
                 ctr->sum_d += __ldcg(&ctr->dcur);          // D_r: degrees of W_r
+                if (kFront && r >= 2) ctr->sum_next += wsize;  // |W_r| = losers of round r-1
             }
-            if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)total;
+            if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)wsize;
         }
         const bool shortcut = !kFast && r == 1 && !p.resume;  // det round 1: all colors are 1
         // ---- phase A: FirstFit over W_r (det round 1: every tentative color is 1)
@@ -1596,6 +2008,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             fast_hub_assign<kBatched>(p, par, h64, kmax, acc);
             fast_medium_assign<kBatched>(p, p.mw[par], nm, acc);
             fast_light_assign<kBatched>(p, p.lw[par], nl, sbuf, acc);
+        } else if (front) {  // FirstFit over A_r; A_r and its dependents go to ConflictResolve
+            front_assign_hubs<kBatched>(p, par, ah, (int)r, prefix, ListSet{0, par});
+            front_assign_medium<kBatched>(p, par, anm, (int)r, prefix, ListSet{0, par});
+            front_assign_light<kBatched>(p, par, anl, (int)r, prefix, ListSet{0, par});
+            flush_push<kBatched>(p, ListSet{0, par});
         } else if (!shortcut) {
             det_assign_hubs<kBatched>(p, par, h64, acc);
             det_assign_medium<kBatched>(p, par, nm, acc);
@@ -1612,10 +2029,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             fast_light_detect<kBatched>(p, p.lw[par], nl, p.lw[pn], &ctr->nl[pn], prefix, sbuf, b);
         } else {
             // round 1 reads W_1 itself; later rounds only the vertices the
-            // witness did not settle in phase A
+            // witness did not settle in phase A (or, on the activation lists,
+            // A_r and its dependents).  On the activation lists every commit
+            // activates its stale neighbours for round r+1 and no loser is
+            // pushed: the ones not activated stay as they are.
             const unsigned bnl = shortcut ? nl : __ldcg(&ctr->nul[par]);
             const unsigned bnm = shortcut ? nm : __ldcg(&ctr->num[par]);
             const unsigned long long bh = shortcut ? h64 : __ldcg(&ctr->uh64[par]);
+            const int act_r = kFront ? (int)(r + 1) : 0;
             if (recorder) {  // W_r's counters are in registers; U_{r+1} must start empty
                 ctr->nl[par] = 0;
                 ctr->nm[par] = 0;
@@ -1623,20 +2044,29 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
                 ctr->nul[pn] = 0;
                 ctr->num[pn] = 0;
                 ctr->uh64[pn] = 0;
+                if (kFront) {  // A_r's too
+                    ctr->nal[par] = 0;
+                    ctr->nam[par] = 0;
+                    ctr->ah64[par] = 0;
+                    ctr->adeg[par] = 0;
+                }
             }
             det_hub_detect<kBatched>(p, shortcut ? p.hw[par] : p.uh[par],
-                                     shortcut ? p.hcb[par] : p.ucb[par], bh, pn, prefix, b);
-            det_medium_detect<kBatched>(p, shortcut ? p.mw[par] : p.um[par], bnm, p.mw[pn],
-                                        &ctr->nm[pn], prefix, b);
-            det_light_detect<kBatched>(p, shortcut ? p.lw[par] : p.ul[par], bnl, p.lw[pn],
-                                       &ctr->nl[pn], prefix, shortcut, b);
+                                     shortcut ? p.hcb[par] : p.ucb[par], bh, pn, prefix, !kFront, b);
+            det_medium_detect<kBatched>(p, shortcut ? p.mw[par] : p.um[par], bnm,
+                                        kFront ? nullptr : p.mw[pn], &ctr->nm[pn], prefix, act_r,
+                                        ListSet{1, pn}, b);
+            det_light_detect<kBatched>(p, shortcut ? p.lw[par] : p.ul[par], bnl,
+                                       kFront ? nullptr : p.lw[pn], &ctr->nl[pn], prefix, shortcut,
+                                       act_r, ListSet{1, pn}, b);
+            if (kFront) flush_push<kBatched>(p, ListSet{1, pn});
         }
         acc.w += b.w;
         acc.d += b.d;
         acc.dscan += b.dscan;
         acc.next += b.next;
         acc.scatter += b.scatter;
-        flush_phase(p, b.kmax, b.kdeg, b.slow);
+        flush_phase(p, b.kmax, b.kdeg, b.slow, b.keep);
         if (!(ok = grid_barrier(p, gen))) break;
         if (recorder && r <= kTraceCap) {
             p.trace[kTraceFields * (r - 1) + 2] = (long long)(globaltimer() - t0);
@@ -1648,6 +2078,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
         ctr->rounds = r - 1;
         ctr->round = r;
     }
+    if (kFront) acc.next = 0;  // counted from |W_r| above
     flush_stats(p, acc);
 }
 
@@ -1833,25 +2264,39 @@ int occupancy_blocks_per_sm(bool fast, bool batched, int *out) {
     cudaError_t e;
     if (fast) {
         e = batched ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                          out, sgr_color_kernel<true, true>, kBlock, 0)
+                          out, sgr_color_kernel<true, true, false>, kBlock, 0)
                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                          out, sgr_color_kernel<true, false>, kBlock, 0);
+                          out, sgr_color_kernel<true, false, false>, kBlock, 0);
     } else {
         e = batched ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                          out, sgr_color_kernel<false, true>, kBlock, 0)
+                          out, sgr_color_kernel<false, true, false>, kBlock, 0)
                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                          out, sgr_color_kernel<false, false>, kBlock, 0);
+                          out, sgr_color_kernel<false, false, false>, kBlock, 0);
     }
     return (int)e;
+}
+
+int occupancy_blocks_per_sm_front(bool batched, int *out) {
+    return (int)(batched ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                               out, sgr_color_kernel<false, true, true>, kBlock, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                               out, sgr_color_kernel<false, false, true>, kBlock, 0));
 }
 
 cudaError_t launch_color(const Params &p, bool fast, bool batched, int grid, cudaStream_t s) {
     void *args[] = {(void *)&p};
     const void *fn;
-    if (fast) fn = batched ? (const void *)sgr_color_kernel<true, true>
-                           : (const void *)sgr_color_kernel<true, false>;
-    else fn = batched ? (const void *)sgr_color_kernel<false, true>
-                      : (const void *)sgr_color_kernel<false, false>;
+    if (fast) fn = batched ? (const void *)sgr_color_kernel<true, true, false>
+                           : (const void *)sgr_color_kernel<true, false, false>;
+    else fn = batched ? (const void *)sgr_color_kernel<false, true, false>
+                      : (const void *)sgr_color_kernel<false, false, false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
+}
+
+cudaError_t launch_color_front(const Params &p, bool batched, int grid, cudaStream_t s) {
+    void *args[] = {(void *)&p};
+    const void *fn = batched ? (const void *)sgr_color_kernel<false, true, true>
+                             : (const void *)sgr_color_kernel<false, false, true>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
 }
 

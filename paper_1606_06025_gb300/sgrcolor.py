@@ -79,7 +79,7 @@ class ServerStats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("light_max", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("active_lists", ctypes.c_int32)]
 
 
 def _load():
@@ -246,8 +246,8 @@ def sgr_get_tuning() -> dict:
     return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
 
-def sgr_set_tuning(light_max=0, chunk=0, blocks_per_sm=0, reserved=0) -> None:
-    t = Tuning(light_max, chunk, blocks_per_sm, reserved)
+def sgr_set_tuning(light_max=0, chunk=0, blocks_per_sm=0, active_lists=0) -> None:
+    t = Tuning(light_max, chunk, blocks_per_sm, active_lists)
     _check(_lib.sgr_set_tuning(ctypes.byref(t)), "sgr_set_tuning")
 
 

@@ -39,7 +39,7 @@ def test_host_only_calls_without_gpu():
     t = sgrcolor.sgr_get_tuning()
     assert 1 <= t["light_max"] <= 32
     # invalid tunings are refused, valid ones round-trip
-    for bad in [dict(reserved=3), dict(light_max=33), dict(chunk=10), dict(blocks_per_sm=-1)]:
+    for bad in [dict(active_lists=3), dict(light_max=33), dict(chunk=10), dict(blocks_per_sm=-1)]:
         try:
             sgrcolor.sgr_set_tuning(**bad)
         except sgrcolor.SgrError as e:

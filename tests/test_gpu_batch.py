@@ -83,6 +83,16 @@ def test_batch_det_across_bins(tuning, tune):
         assert np.array_equal(got[i], ref.colors) and k[i] == ref.num_colors
 
 
+@pytest.mark.parametrize("policy", [1, 2])
+def test_batch_det_active_list_policies(tuning, policy):
+    tuning.sgr_set_tuning(active_lists=policy, light_max=8, chunk=128)
+    graphs = small_mix(6, count=20, n_lo=100, n_hi=9000) + [gg.rmat(12, 16, seed=2)]
+    got, k = run_batch(tuning, gg.pack(graphs))
+    for i, g in enumerate(graphs):
+        ref = oracle.det_sgr(g)
+        assert np.array_equal(got[i], ref.colors) and k[i] == ref.num_colors
+
+
 def test_batch_fast_valid(gpu_lib):
     graphs = small_mix(4)
     got, k = run_batch(gpu_lib, gg.pack(graphs), "fast")

@@ -139,6 +139,23 @@ def test_det_parity_unsorted_rows(tuning, rule):
     assert st["rows_sorted"] == 1
 
 
+# Deterministic rounds either run over the whole worklist or (active_lists)
+# only over the vertices a commit made stale plus those whose witness they
+# are; the automatic choice uses both on most inputs.  Forcing each one must
+# give the oracle's result everywhere, including hubs split into work items,
+# the fallback for full bitmaps, unsorted rows and every loser rule.
+@pytest.mark.parametrize("policy", [1, 2])
+@pytest.mark.parametrize("tune", [dict(), dict(light_max=4, chunk=64), dict(light_max=1, chunk=2048)])
+def test_det_parity_active_lists(tuning, policy, tune):
+    tuning.sgr_set_tuning(active_lists=policy, **tune)
+    graphs = [gg.rmat(13, 16, seed=21), star(700), complete(300), gg.stencil(12, 11, 10, 27),
+              gg.stencil(40, 37, 1, 9), gg.uniform(6000, 14.0, seed=8),
+              shuffled_rows(gg.rmat(12, 16, seed=3), 1), gg.from_edges(9, [])]
+    for g in graphs:
+        for rule in ["low_keeps", "low_loses", "degree"]:
+            assert_det_parity(tuning, g, rule)
+
+
 def test_det_ragged_sizes_around_tiles(lib):
     # sizes straddling the 1024-vertex light tile and the 4-entry vector loads
     for n in [1, 2, 3, 31, 32, 33, 1023, 1024, 1025, 4097]:
@@ -272,3 +289,17 @@ def test_full_size_fast_valid(lib, name):
     chk = oracle.check(g, got)
     assert chk["valid"] and chk["num_colors"] == k
     assert k <= GOLDEN[name]["max_degree"] + 1
+
+
+@pytest.mark.parametrize("policy", [1, 2])
+@pytest.mark.parametrize("name", list(FULL))
+def test_full_size_det_active_list_policies(tuning, policy, name):
+    """The full-size digests again with the round mode forced each way."""
+    tuning.sgr_set_tuning(active_lists=policy)
+    gold = GOLDEN[name]
+    g = FULL[name]()
+    got, k, st = run(tuning, g, "det")
+    assert k == gold["det_num_colors"] and st["rounds"] == gold["det_rounds"]
+    assert st["sum_w"] == gold["det_sum_w"] and st["sum_d"] == gold["det_sum_d"]
+    assert st["sum_next"] == gold["det_sum_next"]
+    assert digest(got) == gold["det_colors_sha256"]
