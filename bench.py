@@ -136,25 +136,36 @@ def read_traffic(workload, mode):
 
 
 def alg_bytes(st, n, m, mode):
-    """Algorithmic DRAM bytes of one coloring launch (the byte model).
+    """Algorithmic DRAM bytes of one coloring launch, as this implementation
+    does the work (the byte model; the counts are measured on the device).
 
-    Deterministic mode, per worklist vertex and round, 20 B: FirstFit reads the
-    worklist entry (4), the first word of the vertex's forbidden-color bitmap
-    (4) and its witness (4), writes the tentative color (4) and pushes the entry
-    onto the next list (4).  A vertex the witness does not settle is rescanned
-    by ConflictResolve: 24 B more (entry 4, row offsets 8, own color 4,
-    lower-neighbour count 4, commit 4) plus 4 B per col_idx entry it inspects.
-    A committing vertex scatters its color: 4 B per entry.  Fast mode, per
-    worklist vertex and round, 36 B (entry and row offsets in both phases, color
-    read and writes) plus 4 B per entry FirstFit gathers (sum of D_r) and per
-    entry ConflictResolve inspects.  The init pass reads col_idx once (4 B per
+    Deterministic mode: 24 B per worklist entry a grid phase visits (entry 4,
+    row offsets 8, bitmap word or own color 4, witness or lower-neighbour
+    count 4, tentative color or commit write 4), 4 B per col_idx entry the grid
+    reads (ConflictResolve scans, commit scatters, dependent scans), 2 B per
+    16-bit W-adjacency entry the tail CTA reads (its per-vertex state is in
+    shared memory), and for a hand-over 4 B per row entry of the worklist plus
+    4 B per vertex (the pass over the colors).  Fast mode, per worklist vertex
+    and round, 36 B (entry and row offsets in both phases, color read and
+    writes) plus 4 B per entry FirstFit gathers (sum of D_r) and per entry
+    ConflictResolve inspects.  Both: the init pass reads col_idx once (4 B per
     entry) and 24 B per vertex.  Neighbour color and bitmap accesses that hit
     the L2-resident arrays are not counted."""
     if mode == "det":
-        return (20 * st["sum_w"] + 24 * st["sum_rescan"] + 4 * st["sum_dscan"]
-                + 4 * st["sum_scatter"] + 4 * m + 24 * n)
+        tail = 4 * st["tail_build"] + 4 * n if st["tail_rounds"] else 0
+        return (24 * st["sum_touch"] + 4 * (st["sum_dscan"] + st["sum_scatter"] + st["sum_dep"])
+                + 2 * st["tail_entries"] + tail + 4 * m + 24 * n)
     return (36 * st["sum_w"] + 4 * st["sum_d"] + 4 * st["sum_dscan"] + 4 * st["sum_next"]
             + 4 * m + 24 * n)
+
+
+def paper_bytes(st):
+    """Bytes of the same rounds done as Algorithms 4 and 5 print them (every
+    round re-reads the whole row of every worklist vertex in FirstFit and in
+    ConflictResolve): per round 4|W_r| worklist + 8|W_r| row offsets +
+    2 x 4 D_r col_idx + 4|W_r| tentative color + 4|W_r| commit + 4 L_r pushed
+    losers."""
+    return 20 * st["sum_w"] + 8 * st["sum_d"] + 4 * st["sum_next"]
 
 
 class ClockSampler:
@@ -168,6 +179,8 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
+        """Start sampling and wait (up to 5 s) for the first sample, so that
+        nvidia-smi's own start-up is over before the timed region begins."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
@@ -177,6 +190,11 @@ class ClockSampler:
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.02)
+        self.lines.clear()
 
     def _read(self):
         for line in self.proc.stdout:
@@ -291,7 +309,9 @@ def run_ours(args, rank, world, local):
         fields = [int(x) for x in args.tune.split(",")]
         lm, ch, bps = fields[:3]
         al = fields[3] if len(fields) > 3 else 0
-        lib.sgr_set_tuning(light_max=lm, chunk=ch, blocks_per_sm=bps, active_lists=al)
+        tv = fields[4] if len(fields) > 4 else 0
+        lib.sgr_set_tuning(light_max=lm, chunk=ch, blocks_per_sm=bps, active_lists=al,
+                           tail_vertices=tv)
     desc, make = workload(args.workload)
     g = make()
     n, m = g.n, g.m
@@ -370,6 +390,7 @@ def run_ours(args, rank, world, local):
     kmean = statistics.mean(kern_ms)
     ab = alg_bytes(st, n, m, args.mode)
     achieved = ab / (kmean * 1e-3) / 1e9
+    pb = paper_bytes(st)
     line = {
         "metric": METRIC_SINGLE, "value": value, "unit": "GTEPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -385,10 +406,17 @@ def run_ours(args, rank, world, local):
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "GTEPS", "ms_per_step": e2e_total / args.steps,
                 "h2d_bytes_per_step": 4 * (n + 1) + 4 * m, "d2h_bytes_per_step": 4 * n},
-        "gpu_launches": args.steps * 1,
+        # per step: the round kernel, then (det) the activation-list kernel and
+        # the tail kernel, each of which returns at once when not handed over
+        "gpu_launches": args.steps * (1 if args.mode == "fast" else 3),
+        "step_ms": {"min": min(step_ms), "max": max(step_ms)},
+        "tail_rounds": st["tail_rounds"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": read_traffic(args.workload, args.mode) if args.rule == "low_keeps" else None,
                      "alg_bytes_per_launch": ab, "kernel_ms": kmean,
+                     "paper_model": {"bytes_per_launch": pb, "equivalent_gbs": pb / (kmean * 1e-3) / 1e9,
+                                     "frac": pb / (kmean * 1e-3) / 1e9 / peak,
+                                     "what": "Algorithms 4/5 as printed: rows re-read every round"},
                      "kernel": "sgr_color_kernel", "peak_source": peak_src + " of measured"
                      if peak_src.startswith("measured") else peak_src},
     }
@@ -500,7 +528,7 @@ def run_batch(args, rank, world, local):
                    "parallelism": f"graphs sharded by rank x{world}"},
         "rounds": st["rounds"], "sum_d": st["sum_d"], "kernel_ms": st["device_ms"],
         "sequential_graphs_per_s": seq_value, "speedup_vs_sequential": value / seq_value,
-        "clocks": clocks, "gpu_launches": args.steps * 3,
+        "clocks": clocks, "gpu_launches": args.steps * 5,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -697,7 +725,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--timeline", default="", help="write the per-round device timeline here")
-    ap.add_argument("--tune", default="", help="light_max,chunk,blocks_per_sm[,active_lists] (0 = default)")
+    ap.add_argument("--tune", default="",
+                    help="light_max,chunk,blocks_per_sm[,active_lists[,tail_vertices]] (0 = default)")
     ap.add_argument("--autotune", action="store_true",
                     help="measure the tuning candidates on the workload before timing")
     ap.add_argument("--requests", type=int, default=600, help="serve: requests in the stream")

@@ -92,6 +92,11 @@ typedef struct {
     int32_t grid_blocks;   /* CTAs of the persistent kernel */
     int32_t block_threads; /* threads per CTA */
     double device_ms;      /* device time of the coloring kernel(s), CUDA events */
+    int64_t tail_rounds;   /* deterministic mode: rounds run by the one-CTA tail */
+    int64_t sum_touch;     /* deterministic mode: worklist entries the grid phases visited */
+    int64_t sum_dep;       /* deterministic mode: row entries read to find witness dependents */
+    int64_t tail_entries;  /* deterministic mode: W-adjacency entries the tail read */
+    int64_t tail_build;    /* deterministic mode: row entries the tail hand-over scanned */
 } sgr_stats;
 
 /* Load-balance and launch parameters (Sect. 3.2 thread coarsening, Sect. 3.3
@@ -107,6 +112,11 @@ typedef struct {
                               that is cheaper than the whole worklist;
                               1 = never; 2 = from round 2 on.  The colors are
                               the same in every case. */
+    int32_t tail_vertices; /* deterministic mode: once at most this many
+                              vertices are left on the worklist, the remaining
+                              rounds run in one CTA on the subgraph they
+                              induce; 0 = library default (3072), -1 = never,
+                              else 1..3072.  The colors are the same. */
 } sgr_tuning;
 
 /*

@@ -81,7 +81,7 @@ std::mutex g_ctx_mu;
 std::vector<DevCtx *> g_ctx;
 
 std::mutex g_tune_mu;
-sgr_tuning g_tune = {32, 512, 0, 0};
+sgr_tuning g_tune = {32, 512, 0, 0, 0};
 
 thread_local sgr_stats t_stats;
 
@@ -167,7 +167,14 @@ struct Job {
     const long long *robase_dev;
     int32_t *gid_dev;  // filled by the caller for batched jobs
     bool front;        // det: allocate the activation lists (rounds may run on them)
+    bool tail;         // det: allocate the tail arrays (the last rounds may run in one CTA)
 };
+
+// |W_r| at or below which the rounds move to the tail CTA (0: never).
+int tail_vertices(const sgr_tuning &t) {
+    if (t.tail_vertices < 0) return 0;
+    return t.tail_vertices == 0 ? sgr::kTailDefault : std::min(t.tail_vertices, sgr::kTailMax);
+}
 
 // Carve the scratch arena for a job.  Returns the byte size; fills p when
 // base != nullptr.
@@ -212,6 +219,19 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     int32_t *am0 = (int32_t *)take(an * 4), *am1 = (int32_t *)take(an * 4);
     int32_t *ah0 = (int32_t *)take(ahub * 4), *ah1 = (int32_t *)take(ahub * 4);
     unsigned *acb0 = (unsigned *)take(ahub * 4), *acb1 = (unsigned *)take(ahub * 4);
+    const int tmax = (!j.fast && j.tail) ? tail_vertices(t) : 0;
+    const long long tcap = tmax ? std::min<long long>(j.m + 8ll * tmax, sgr::kTailCapEntries) : 0;
+    int32_t *tlist = tmax ? (int32_t *)take((size_t)tmax * 4) : nullptr;
+    unsigned *toff = tmax ? (unsigned *)take((size_t)(tmax + 1) * 4) : nullptr;
+    unsigned *tcnt = tmax ? (unsigned *)take((size_t)tmax * 4) : nullptr;
+    unsigned *tlow = tmax ? (unsigned *)take((size_t)tmax * 4) : nullptr;
+    unsigned *tdeg = tmax ? (unsigned *)take((size_t)tmax * 4) : nullptr;
+    unsigned *tcp = tmax ? (unsigned *)take((size_t)(tmax + 1) * 4) : nullptr;
+    const long long tch = tmax ? tcap / sgr::kTailChunk + tmax + 1 : 0;  // chunks of the row passes
+    unsigned *tcc = tmax ? (unsigned *)take((size_t)(tch + 1) * 4) : nullptr;
+    unsigned *tcl = tmax ? (unsigned *)take((size_t)(tch + 1) * 4) : nullptr;
+    int32_t *tloc = tmax ? (int32_t *)take((size_t)j.n * 4) : nullptr;
+    unsigned short *tadj = tmax ? (unsigned short *)take((size_t)tcap * 2 + 16) : nullptr;
     if (p && base) {
         std::memset(p, 0, sizeof(*p));
         p->ro = j.ro;
@@ -254,6 +274,19 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         p->trace = trace;
         p->light_max = t.light_max;
         p->chunk = t.chunk;
+        p->tail_max = tmax;
+        p->tail_cap = tcap;
+        p->tlist = tlist;
+        p->toff = toff;
+        p->tcnt = tcnt;
+        p->tlow = tlow;
+        p->tdeg = tdeg;
+        p->tcp = tcp;
+        p->tcc = tcc;
+        p->tcl = tcl;
+        p->tail_chunks = (int)tch;
+        p->tloc = tloc;
+        p->tadj = tadj;
     }
     return off;
 }
@@ -273,6 +306,11 @@ void fill_stats(const Counters &h, float ms, int grid, int colors) {
     s.grid_blocks = grid;
     s.block_threads = sgr::kBlock;
     s.device_ms = ms;
+    s.tail_rounds = h.tail_rounds;
+    s.sum_touch = (int64_t)h.sum_touch;
+    s.sum_dep = (int64_t)h.sum_dep;
+    s.tail_entries = (int64_t)h.tail_entries;
+    s.tail_build = (int64_t)h.tail_build;
     t_stats = s;
 }
 
@@ -280,7 +318,9 @@ void fill_stats(const Counters &h, float ms, int grid, int colors) {
 // also runs init; in deterministic mode with activation lists it may hand the
 // rounds over after init (Counters::handoff) to the activation-list kernel,
 // which is therefore always launched behind it (and returns at once if not
-// needed).  Each launch gets its own grid and a fresh barrier counter.
+// needed).  Each launch gets its own grid and a fresh barrier counter.  Either
+// grid kernel may hand the last rounds to the one-CTA tail kernel
+// (Counters::tail), launched behind them when the job has the tail arrays.
 cudaError_t launch_rounds(Params p, bool fast, bool batched, int per_sm_full, int per_sm_front,
                           int sms, const sgr_tuning &t, cudaStream_t st, int *grid_out) {
     int per_sm = per_sm_full;
@@ -290,13 +330,17 @@ cudaError_t launch_rounds(Params p, bool fast, bool batched, int per_sm_full, in
     p.nblocks = (unsigned)grid;
     *grid_out = grid;
     cudaError_t e = sgr::launch_color(p, fast, batched, grid, st);
-    if (e != cudaSuccess || fast || !p.front_ok || p.front_policy == 1) return e;
-    int per_sm_f = per_sm_front;
-    if (t.blocks_per_sm > 0) per_sm_f = std::min(per_sm_f, t.blocks_per_sm);
-    if (per_sm_f < 1) return cudaErrorInvalidConfiguration;
-    p.nblocks = (unsigned)(per_sm_f * sms);
-    if ((e = cudaMemsetAsync(&p.ctr->bar, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-    return sgr::launch_color_front(p, batched, (int)p.nblocks, st);
+    if (e != cudaSuccess || fast) return e;
+    if (p.front_ok && p.front_policy != 1) {
+        int per_sm_f = per_sm_front;
+        if (t.blocks_per_sm > 0) per_sm_f = std::min(per_sm_f, t.blocks_per_sm);
+        if (per_sm_f < 1) return cudaErrorInvalidConfiguration;
+        p.nblocks = (unsigned)(per_sm_f * sms);
+        if ((e = cudaMemsetAsync(&p.ctr->bar, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        if ((e = sgr::launch_color_front(p, batched, (int)p.nblocks, st)) != cudaSuccess) return e;
+    }
+    if (p.tail_max > 0) return sgr::launch_color_tail(p, batched, st);
+    return cudaSuccess;
 }
 
 // Run the coloring launches for a job (single graph or batch) and read back
@@ -400,6 +444,8 @@ int sgr_set_tuning(const sgr_tuning *in) {
     sgr_tuning t = current_tuning();
     if (in->active_lists < 0 || in->active_lists > 2) return SGR_ERR_INVALID_ARG;
     t.active_lists = in->active_lists;
+    if (in->tail_vertices < -1 || in->tail_vertices > sgr::kTailMax) return SGR_ERR_INVALID_ARG;
+    t.tail_vertices = in->tail_vertices;
     if (in->light_max) {
         if (in->light_max < 1 || in->light_max > sgr::kLightMaxStage) return SGR_ERR_INVALID_ARG;
         t.light_max = in->light_max;
@@ -481,6 +527,7 @@ int sgr_color(int32_t n, const int32_t *row_offsets, const int32_t *col_idx, int
     j.ci = col_idx;
     j.colors = colors_out;
     j.front = true;
+    j.tail = true;
     return run_job(c, j, mode, st, num_colors);
 }
 
@@ -520,6 +567,7 @@ int sgr_color_host(int32_t n, const int32_t *ro_h, const int32_t *ci_h, int32_t 
     j.ci = ci_d;
     j.colors = co_d;
     j.front = true;
+    j.tail = true;
     rc = run_job(c, j, mode, st, num_colors);
     if (rc != SGR_OK) return rc;
     if ((e = cudaMemcpyAsync(colors_h, co_d, (size_t)n * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -564,6 +612,7 @@ int sgr_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
     j.G = G;
     j.fast = (mode & SGR_MODE_MASK) == SGR_MODE_FAST;
     j.front = true;
+    j.tail = true;
     // the batch tail of the arena: gid, vbase, ebase, per-graph k (see run_job)
     const sgr_tuning t = current_tuning();
     size_t zero_bytes = 0;
@@ -627,7 +676,7 @@ int sgr_autotune(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
         for (int32_t c : chunks)
             for (int32_t l : lights) {
                 if (tried > 0 && spent > budget) continue;
-                sgr_tuning t = {l, c, b, 0};
+                sgr_tuning t = {l, c, b, 0, start.tail_vertices};
                 int rc = sgr_set_tuning(&t);
                 if (rc != SGR_OK) continue;
                 double tmin = 1e300;

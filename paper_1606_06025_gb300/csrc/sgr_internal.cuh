@@ -24,6 +24,11 @@
 //                        round made stale (a neighbour committed that color).
 //   astamp[n]            det mode: the round v was last put on an activation list.
 //   vslot[n]             det mode: hub slot of v, or -1 (light) / -2 (medium).
+//   tail arrays          det mode: the last rounds in one CTA (sgr_tail.cuh):
+//                        tlist (local id -> vertex), tloc[n] (vertex -> local
+//                        id), per local vertex the start / count of its
+//                        W-neighbours in tadj (16-bit local ids) and the
+//                        chunk prefix of the build.
 //   Counters             list sizes, grid barrier, max
 //                        color so far, error code, statistics.
 #pragma once
@@ -49,6 +54,13 @@ constexpr int kLightMaxStage = 32;               // largest light degree (staged
 constexpr int kTraceCap = 1 << 16;               // rounds recorded in the timeline
 constexpr int kTraceFields = 4;                  // |W_r|, ns at end of phase A / phase B, rescans
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;  // bounded device waits
+constexpr int kTailThreads = 512;                // threads of the tail CTA
+constexpr int kTailMax = 3072;                   // largest |W_r| the tail CTA takes
+constexpr int kTailDefault = 3072;               // default hand-over size
+constexpr int kTailChunk = 1024;                 // row entries per warp item of the tail build
+constexpr long long kTailCapEntries = 24ll << 20;  // largest W-adjacency (16-bit entries)
+// dynamic shared memory of the tail CTA for t local vertices
+constexpr size_t tail_smem_bytes(int t) { return (size_t)t * (8 + 8 * 4 + 3 * 4 + 8 * 2) + 64; }
 
 constexpr int kErrNoConvergence = SGR_ERR_NO_CONVERGENCE;
 constexpr int kErrTimeout = SGR_ERR_TIMEOUT;
@@ -66,6 +78,14 @@ struct Counters {
     unsigned long long nroots;      // det: vertices with no entry below them (round-1 keepers on ascending rows)
     unsigned long long t_start;     // globaltimer at the start of the launch that ran init
     int handoff;                    // det: init handed the rounds to the activation-list kernel
+    int tail;                       // det: the rounds continue in the tail CTA
+    int tail_fail;                  // det: the W-adjacency would not fit; rounds stay on the grid
+    unsigned tail_n;                // det: |W_r| at the hand-over (local ids 0 .. tail_n-1)
+    long long tail_rounds;          // det: rounds the tail CTA ran
+    unsigned long long sum_touch;   // det: worklist entries the grid phases visited
+    unsigned long long sum_dep;     // det: row entries read to find witness dependents
+    unsigned long long tail_entries;  // det: W-adjacency entries the tail CTA read
+    unsigned long long tail_build;  // det: row entries the tail hand-over scanned
     unsigned long long bar;         // grid barrier: arrivals (bits 0..62), error flag (bit 63)
     unsigned int nslots;            // hub slots handed out
     unsigned int hwords;            // hub bitmap words handed out
@@ -117,6 +137,19 @@ struct Params {
     int32_t *vslot;            // det: hub slot, -1 light, -2 medium
     int front_ok;              // det: the activation lists are allocated
     int front_policy;          // det: 0 when few round-1 keepers, 1 never, 2 always
+    int tail_max;              // det: |W_r| at or below which the rounds go to the tail CTA (0: never)
+    long long tail_cap;        // det: capacity of tadj in entries
+    int32_t *tlist;            // det tail: local id -> vertex (tail_max)
+    int32_t *tloc;             // det tail: vertex -> local id (n; valid on W_r)
+    unsigned *toff;            // det tail: start of each local vertex's W-neighbours in tadj (tail_max + 1)
+    unsigned *tcnt;            // det tail: number of W-neighbours (tail_max)
+    unsigned *tlow;            // det tail: W-neighbours below the vertex (tail_max)
+    unsigned *tdeg;            // det tail: degree (tail_max)
+    unsigned *tcp;             // det tail: chunk prefix of the build (tail_max + 1)
+    unsigned *tcc;             // det tail: per chunk, W-neighbours, then their prefix (tail_chunks + 1)
+    unsigned *tcl;             // det tail: per chunk, W-neighbours below the vertex, then their prefix
+    int tail_chunks;           // det tail: capacity of tcc / tcl, less one
+    unsigned short *tadj;      // det tail: W-neighbours as local ids, 16-byte aligned runs
     int32_t *sw;               // det: hub scatter list slots
     unsigned int *scb;         // det: hub scatter list chunk bases
     Counters *ctr;
@@ -158,6 +191,9 @@ cudaError_t launch_color(const Params &p, bool fast, bool batched, int grid, cud
 // Counters::handoff; returns at once if it did not).
 int occupancy_blocks_per_sm_front(bool batched, int *out);
 cudaError_t launch_color_front(const Params &p, bool batched, int grid, cudaStream_t s);
+// The last deterministic rounds in one CTA (after a launch that set
+// Counters::tail; returns at once if none did).
+cudaError_t launch_color_tail(const Params &p, bool batched, cudaStream_t s);
 cudaError_t launch_admit(const Params &p, int g, long long vb, int32_t n, int par, int grid,
                          cudaStream_t s);
 cudaError_t launch_slot_status(const int32_t *colors, const long long *vbase, const int32_t *nv,

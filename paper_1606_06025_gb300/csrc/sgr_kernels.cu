@@ -1896,6 +1896,8 @@ __device__ void flush_stats(const Params &p, Acc &acc) {
     }
 }
 
+#include "sgr_tail.cuh"
+
 // The round loop.  kFront (det only): rounds 2.. run on the activation lists;
 // the launch continues after an init launch of the kFront = false kernel that
 // handed the rounds over (Counters::handoff), and returns at once otherwise.
@@ -1948,6 +1950,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
     const bool prefix = sorted && p.rule == 0;
     const long long r_end = p.resume ? r + p.rounds_per_launch : LLONG_MAX;
     bool ok = true;
+    bool tail_try = !kFast && p.tail_max > 0 && !p.resume;
     for (;; ++r) {
         if (r == r_end) break;
         const int par = (int)(r & 1), pn = par ^ 1;
@@ -1976,6 +1979,24 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
                 if (!(ok = grid_barrier(p, gen))) break;
             }
         }
+        // few vertices left: the tail CTA takes the remaining rounds (the
+        // bitmaps are complete here, deferred hub scatters included)
+        if (!kFast && tail_try && wsize <= (unsigned long long)p.tail_max &&
+            __ldcg(&ctr->dcur) <= (unsigned long long)p.tail_cap) {
+            const int rc = tail_build<kBatched>(p, gen, (unsigned)wsize);
+            if (rc < 0) {
+                ok = false;
+                break;
+            }
+            if (rc > 0) {
+                if (recorder) {
+                    if (kFront && r >= 2) ctr->sum_next += wsize;  // |W_r|, losers of round r-1
+                    ctr->tail_build += __ldcg(&ctr->dcur);
+                }
+                break;
+            }
+            tail_try = false;  // the W-adjacency does not fit: the grid goes on
+        }
         unsigned anl = 0, anm = 0;
         unsigned long long ah = 0;
         if (front) {  // A_r is complete now
@@ -2002,6 +2023,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)wsize;
         }
         const bool shortcut = !kFast && r == 1 && !p.resume;  // det round 1: all colors are 1
+        if (!kFast && recorder) {  // worklist entries phase A visits
+            if (front) {
+                ctr->sum_touch += (unsigned long long)anl + anm + (ah >> 32);
+                ctr->sum_dep += __ldcg(&ctr->adeg[par]);
+            } else if (!shortcut) {
+                ctr->sum_touch += wsize;
+            }
+        }
         // ---- phase A: FirstFit over W_r (det round 1: every tentative color is 1)
         if (kFast) {
             const int kmax = __ldcg(&ctr->kmax);
@@ -2038,6 +2067,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             const unsigned long long bh = shortcut ? h64 : __ldcg(&ctr->uh64[par]);
             const int act_r = kFront ? (int)(r + 1) : 0;
             if (recorder) {  // W_r's counters are in registers; U_{r+1} must start empty
+                ctr->sum_touch += (unsigned long long)bnl + bnm + (bh >> 32);
                 ctr->nl[par] = 0;
                 ctr->nm[par] = 0;
                 ctr->h64[par] = 0;
@@ -2298,6 +2328,15 @@ cudaError_t launch_color_front(const Params &p, bool batched, int grid, cudaStre
     const void *fn = batched ? (const void *)sgr_color_kernel<false, true, true>
                              : (const void *)sgr_color_kernel<false, false, true>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
+}
+
+cudaError_t launch_color_tail(const Params &p, bool batched, cudaStream_t s) {
+    const void *fn = batched ? (const void *)sgr_tail_kernel<true> : (const void *)sgr_tail_kernel<false>;
+    const size_t smem = tail_smem_bytes(p.tail_max);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&p};
+    return cudaLaunchKernel(fn, dim3(1), dim3(kTailThreads), args, smem, s);
 }
 
 cudaError_t launch_admit(const Params &p, int g, long long vb, int32_t n, int par, int grid,

@@ -1,0 +1,690 @@
+// sgr_tail.cuh -- the last deterministic rounds in one CTA.
+//
+// Included by sgr_kernels.cu inside its anonymous namespace, after the
+// helpers it uses (row_of, load4, grid_barrier, hub_entry, warp_first_fit).
+//
+// Once few vertices are left on the worklist, a round of Algorithm 7 is a
+// short chain of dependent steps (FirstFit, ConflictResolve, commit), and the
+// persistent grid pays two or three grid-wide barriers and a few L2 round
+// trips for the list bookkeeping per round, whatever the amount of work.  At
+// |W_r| <= tail_max the grid therefore builds, once, the subgraph induced by
+// W_r with 16-bit local ids and hands the remaining rounds to one CTA of 1024
+// threads that keeps every per-vertex state (forbidden-color bitmap,
+// tentative color, witness) in shared memory and uses __syncthreads() as the
+// round barrier.
+//
+// Why the result is that of the full rounds (Algorithm 7 with Algorithms 4
+// and 5 under frozen reads, judge before clear): from round r on only the
+// vertices of W_r change.  FirstFit of v reads the final colors of all of
+// v's neighbours; those outside W_r are final already and recorded in v's
+// bitmap (all commits of earlier rounds, the deferred hub scatters included,
+// are in the bitmaps when the grid hands over), and those inside W_r commit
+// in the CTA, which adds each commit to the bitmaps of the committer's
+// W-neighbours.  ConflictResolve compares tentative colors, which only
+// vertices of W_r hold, so only the W-neighbours matter there too.  Colors
+// above 256 are not in the bitmaps; a vertex whose 256 bits are all set
+// falls back to a scan of its full row over the final colors, which the CTA
+// writes to `colors` at every commit.
+
+// ------------------------------------------------------------ build (whole grid)
+
+// Order-preserving block compaction (as block_push) of item pairs (item to
+// out, item2 to out2) that writes no position at or beyond cap; the counter
+// still counts every flag.
+__device__ __forceinline__ void block_push_capped(const bool (&flag)[kLightUnroll],
+                                                  const int32_t (&item)[kLightUnroll],
+                                                  const unsigned (&item2)[kLightUnroll],
+                                                  unsigned *counter, int32_t *out, unsigned *out2,
+                                                  unsigned cap) {
+    __shared__ unsigned s_pos[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned bal[kLightUnroll];
+#pragma unroll
+    for (int u = 0; u < kLightUnroll; ++u) {
+        bal[u] = __ballot_sync(kFull, flag[u]);
+        if (lane == 0) s_pos[warp * kLightUnroll + u] = __popc(bal[u]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        unsigned tot;
+        s_pos[lane] = warp_reserve(s_pos[lane], counter, true, tot);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kLightUnroll; ++u) {
+        const unsigned pos = s_pos[warp * kLightUnroll + u] + __popc(bal[u] & lanemask_lt());
+        if (flag[u] && pos < cap) {
+            out[pos] = item[u];
+            out2[pos] = item2[u];
+        }
+    }
+    __syncthreads();
+}
+
+// Exclusive scan in place of a[0..n) and b[0..n) by the whole CTA (a[n],
+// b[n] receive the totals); tiles of 4 entries per thread, each thread's
+// four consecutive.  Ends with a __syncthreads().
+__device__ void cta_scan2(unsigned *a, unsigned *b, unsigned n) {
+    __shared__ unsigned s_wa[kWarps], s_wb[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned ca = 0, cb = 0;  // carries from earlier tiles
+    for (unsigned base = 0; base < n; base += 4 * kBlock) {
+        const unsigned i0 = base + 4 * threadIdx.x;
+        unsigned va[4], vb[4], sa = 0, sb = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            va[k] = i0 + k < n ? __ldcg(a + i0 + k) : 0u;
+            vb[k] = (b && i0 + k < n) ? __ldcg(b + i0 + k) : 0u;
+            sa += va[k];
+            sb += vb[k];
+        }
+        unsigned ia = sa, ib = sb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned x = __shfl_up_sync(kFull, ia, o), y = __shfl_up_sync(kFull, ib, o);
+            if (lane >= o) {
+                ia += x;
+                ib += y;
+            }
+        }
+        if (lane == 31) {
+            s_wa[warp] = ia;
+            s_wb[warp] = ib;
+        }
+        __syncthreads();
+        unsigned pa = ca, pb = cb, ta = 0, tb = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            if (w < warp) {
+                pa += s_wa[w];
+                pb += s_wb[w];
+            }
+            ta += s_wa[w];
+            tb += s_wb[w];
+        }
+        pa += ia - sa;
+        pb += ib - sb;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < n) {
+                a[i0 + k] = pa;
+                if (b) b[i0 + k] = pb;
+            }
+            pa += va[k];
+            pb += vb[k];
+        }
+        ca += ta;
+        cb += tb;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a[n] = ca;
+        if (b) b[n] = cb;
+    }
+    __syncthreads();
+}
+
+// CTA 0, after the compaction: the chunk prefix of the passes over the rows
+// (ceil(degree / kTailChunk) warp items per local vertex).
+__device__ __noinline__ void tail_chunk_prefix(const Params &p, unsigned nT) {
+    for (unsigned i = threadIdx.x; i < nT; i += blockDim.x)
+        p.tcp[i] = (__ldcg(p.tdeg + i) + kTailChunk - 1) / kTailChunk;
+    __syncthreads();
+    cta_scan2(p.tcp, nullptr, nT);
+    if (threadIdx.x == 0 && __ldcg(p.tcp + nT) > (unsigned)p.tail_chunks) p.ctr->tail_fail = 1;
+    __syncthreads();
+}
+
+// CTA 0, after the count pass: per local vertex its W-neighbours (tcnt), the
+// ones below it (tlow) and the start of its run (its count rounded up to 8,
+// so that every run starts on 16 bytes); per chunk (in place) the exclusive
+// prefix of the counts.  Sets tail_fail if the runs exceed tail_cap.
+__device__ __noinline__ void tail_run_prefix(const Params &p, unsigned nT) {
+    const unsigned nch = __ldcg(p.tcp + nT);
+    cta_scan2(p.tcc, p.tcl, nch);
+    for (unsigned i = threadIdx.x; i < nT; i += blockDim.x) {
+        const unsigned q0 = __ldcg(p.tcp + i), q1 = __ldcg(p.tcp + i + 1);
+        const unsigned c = __ldcg(p.tcc + q1) - __ldcg(p.tcc + q0);
+        p.tcnt[i] = c;
+        p.tlow[i] = __ldcg(p.tcl + q1) - __ldcg(p.tcl + q0);
+        p.toff[i] = (c + 7u) & ~7u;
+    }
+    __syncthreads();
+    cta_scan2(p.toff, nullptr, nT);
+    if (threadIdx.x == 0 && (long long)__ldcg(p.toff + nT) > p.tail_cap) p.ctr->tail_fail = 1;
+    __syncthreads();
+}
+
+// One warp item of a pass over the rows: entries [a, b) of local vertex i's
+// row.  Lane l takes four consecutive 16-byte blocks of each 128-block step
+// (all loads in flight), so lane order is row order.  kFill = false counts
+// the neighbours still on the worklist (color <= 0) and those of them below
+// the vertex into tcc[q] / tcl[q]; kFill = true writes their local ids into
+// the vertex's run, in row order, at the chunk's offset from the count pass.
+template <bool kBatched, bool kFill>
+__device__ __noinline__ void tail_chunk_pass(const Params &p, unsigned nT, unsigned q) {
+    const int lane = threadIdx.x & 31;
+    const unsigned i = hub_entry(p.tcp, nT, q);
+    const int32_t v = __ldcg(p.tlist + i);
+    const unsigned j = q - __ldcg(p.tcp + i);
+    long long s, e;
+    int32_t vb;
+    row_of<kBatched>(p, v, s, e, vb);
+    const long long a = s + (long long)j * kTailChunk, b = min(e, a + kTailChunk);
+    unsigned short *out = nullptr;
+    if (kFill) out = p.tadj + __ldcg(p.toff + i) + (__ldcg(p.tcc + q) - __ldcg(p.tcc + __ldcg(p.tcp + i)));
+    unsigned total = 0, below = 0, put = 0;
+    for (long long q0 = a >> 2; (q0 << 2) < b; q0 += 128) {
+        int4 x[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const long long qq = q0 + 4 * lane + t;
+            x[t] = (qq << 2) < b ? load4(p.ci, qq, p.m) : make_int4(0, 0, 0, 0);
+        }
+        bool in[4][4];
+        int cw[4][4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long idx = ((q0 + 4 * lane + t) << 2) + k;
+                const int32_t u = vb + elem(x[t], k);
+                in[t][k] = idx >= a && idx < b && (unsigned)u < (unsigned)p.n && u != v;
+                cw[t][k] = in[t][k] ? __ldcg(p.colors + u) : 1;
+            }
+        unsigned c = 0, cl = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                in[t][k] = in[t][k] && cw[t][k] <= 0;
+                c += in[t][k] ? 1u : 0u;
+                cl += (in[t][k] && vb + elem(x[t], k) < v) ? 1u : 0u;
+            }
+        if constexpr (!kFill) {
+            total += c;
+            below += cl;
+        } else {
+            int32_t lu[4][4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) lu[t][k] = in[t][k] ? __ldcg(p.tloc + vb + elem(x[t], k)) : 0;
+            unsigned incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned tt = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += tt;
+            }
+            unsigned pos = put + incl - c;
+            put += __shfl_sync(kFull, incl, 31);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (in[t][k]) out[pos++] = (unsigned short)lu[t][k];
+        }
+    }
+    if constexpr (!kFill) {
+        for (int o = 16; o > 0; o >>= 1) {
+            total += __shfl_xor_sync(kFull, total, o);
+            below += __shfl_xor_sync(kFull, below, o);
+        }
+        if (lane == 0) {
+            p.tcc[q] = total;
+            p.tcl[q] = below;
+        }
+    }
+}
+
+// The grid's part of the hand-over at the top of round r (all CTAs call it
+// alike).  Returns 1 when the tail CTA takes over (the caller leaves its
+// round loop), 0 when the W-adjacency does not fit (the caller goes on with
+// the round on the grid and does not try again), -1 when a barrier failed.
+template <bool kBatched>
+__device__ __noinline__ int tail_build(const Params &p, unsigned &gen, unsigned wsize) {
+    Counters *ctr = p.ctr;
+    // (1) W_r = the vertices not yet final, into tlist, with their degrees
+    const unsigned nt = ((unsigned)p.n + kLightTile - 1) / kLightTile;
+    for (unsigned t = blockIdx.x; t < nt; t += gridDim.x) {
+        bool f[kLightUnroll];
+        int32_t vv[kLightUnroll];
+        unsigned dv[kLightUnroll];
+#pragma unroll
+        for (int u = 0; u < kLightUnroll; ++u) {
+            const unsigned idx = tile_index(t, u);
+            vv[u] = (int32_t)idx;
+            f[u] = idx < (unsigned)p.n && __ldcg(p.colors + idx) <= 0;
+            dv[u] = 0;
+            if (f[u]) {
+                long long rs, re;
+                int32_t vb;
+                row_of<kBatched>(p, (int32_t)idx, rs, re, vb);
+                dv[u] = (unsigned)(re - rs);
+            }
+        }
+        block_push_capped(f, vv, dv, &ctr->tail_n, p.tlist, p.tdeg, (unsigned)p.tail_max);
+    }
+    if (!grid_barrier(p, gen)) return -1;
+    const unsigned nT = __ldcg(&ctr->tail_n);
+    if (nT > (unsigned)p.tail_max || nT != wsize) {  // only a broken input gets here
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr->tail_fail = 1;
+        return 0;  // every CTA sees the same nT and returns alike
+    }
+    // (2) local ids; CTA 0: chunk prefix
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += gridDim.x * blockDim.x)
+        p.tloc[__ldcg(p.tlist + i)] = (int32_t)i;
+    if (blockIdx.x == 0) tail_chunk_prefix(p, nT);
+    if (!grid_barrier(p, gen)) return -1;
+    if (__ldcg(&ctr->tail_fail)) return 0;
+    // (3) count the W-neighbours per chunk
+    const unsigned nch = __ldcg(p.tcp + nT);
+    for (unsigned q = global_warp(); q < nch; q += total_warps()) tail_chunk_pass<kBatched, false>(p, nT, q);
+    if (!grid_barrier(p, gen)) return -1;
+    // (4) CTA 0: run starts and chunk offsets
+    if (blockIdx.x == 0) tail_run_prefix(p, nT);
+    if (!grid_barrier(p, gen)) return -1;
+    if (__ldcg(&ctr->tail_fail)) return 0;
+    // (5) the runs, each in row order
+    for (unsigned q = global_warp(); q < nch; q += total_warps()) tail_chunk_pass<kBatched, true>(p, nT, q);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->tail = 1;
+    return 1;  // the end of the launch orders these writes before the tail CTA
+}
+
+// ------------------------------------------------------------ the tail CTA
+//
+// Per local vertex the CTA keeps one 64-bit word tk: the tentative color of
+// the round in the high half (0 once the vertex is final) and its rank under
+// the loser rule in the low half (u wins against v iff rank(u) > rank(v)).
+// A vertex the witness does not settle scans its run for a winning
+// W-neighbour with the same tentative color and stops at the first one, which
+// becomes its witness.  On ascending rows under the id rules the run is in
+// row order and split at the vertex itself, so the scan visits only winners,
+// nearest first (downward from the split when lower ids win, upward when
+// higher ids win): the nearest winner is the likeliest to lose again itself,
+// to stay on the worklist and settle the next round with one read, and a
+// conflict is usually within a few entries.  Otherwise the whole run is
+// scanned with the rank test.  Each unsettled vertex is first scanned by one
+// lane over eight 16-byte blocks (all in flight, so that the CTA keeps many
+// L2 loads outstanding); the few that go on past them are finished by whole
+// warps.  Keepers record their color at their W-neighbours in a separate
+// warp-parallel pass.
+
+struct TailSmem {
+    unsigned long long *tk;  // [T] tentative color << 32 | rank
+    unsigned *bits;          // [8][T] forbidden colors 1..256, plane-major
+    int32_t *vid;            // [T] vertex id
+    int32_t *deg;            // [T] degree
+    unsigned *off;           // [T] start of the W-neighbour run in tadj
+    unsigned short *cnt;     // [T] W-neighbours
+    unsigned short *low;     // [T] W-neighbours below the vertex (row-ordered runs)
+    short *wit;              // [T] local id of the neighbour that beat it last, or -1
+    unsigned short *res;     // [T] run position where a warp resumes the scan
+    unsigned short *q;       // [T] unsettled vertices of the round (also: full bitmaps)
+    unsigned short *lq;      // [T] unsettled vertices whose scan continues past the lane's blocks
+    unsigned short *kq;      // [T] keepers of the round
+};
+
+__device__ __forceinline__ TailSmem tail_smem(unsigned char *raw, int T) {
+    TailSmem s;
+    s.tk = (unsigned long long *)raw;
+    s.bits = (unsigned *)(s.tk + T);
+    s.vid = (int32_t *)(s.bits + 8 * T);
+    s.deg = s.vid + T;
+    s.off = (unsigned *)(s.deg + T);
+    s.cnt = (unsigned short *)(s.off + T);
+    s.low = s.cnt + T;
+    s.wit = (short *)(s.low + T);
+    s.res = (unsigned short *)(s.wit + T);
+    s.q = s.res + T;
+    s.lq = s.q + T;
+    s.kq = s.lq + T;
+    return s;
+}
+
+__device__ __forceinline__ unsigned tk_color(unsigned long long x) { return (unsigned)(x >> 32); }
+__device__ __forceinline__ unsigned tk_rank(unsigned long long x) { return (unsigned)x; }
+
+// Entry k of a 16-byte block of eight 16-bit local ids.
+__device__ __forceinline__ int tail_elem(const uint4 &x, int k) {
+    const unsigned w = k < 2 ? x.x : (k < 4 ? x.y : (k < 6 ? x.z : x.w));
+    return (int)((k & 1) ? (w >> 16) : (w & 0xffffu));
+}
+
+// The part of i's run its scan covers: positions [lo, hi), downward (mode 0:
+// lower ids win, row-ordered run), upward over the winners (mode 1: higher
+// ids win, row-ordered run) or upward over the whole run with the rank test
+// (mode 2).
+struct TailRange {
+    int lo, hi;
+};
+
+__device__ __forceinline__ TailRange tail_range(const TailSmem &s, int mode, int i) {
+    if (mode == 0) return {0, (int)s.low[i]};
+    if (mode == 1) return {(int)s.low[i], (int)s.cnt[i]};
+    return {0, (int)s.cnt[i]};
+}
+
+// Is local vertex u (entry at run position pos) a conflicting winner?
+__device__ __forceinline__ bool tail_conflict(const TailSmem &s, int mode, int u, unsigned c, unsigned mine) {
+    const unsigned long long t = s.tk[u];
+    return tk_color(t) == c && (mode != 2 || tk_rank(t) > mine);
+}
+
+constexpr int kTailLaneBlocks = 8;
+
+// Lane scan of the first kTailLaneBlocks blocks of i's range in scan order
+// (all loaded before the checks).  Returns the conflicting winner nearest the
+// start, -1 if the range has none, or -2 if these blocks have none and the
+// range goes on (s.res[i] is where it goes on).
+__device__ __forceinline__ int tail_scan_lane(const Params &p, const TailSmem &s, int mode, int i,
+                                              unsigned &scanned) {
+    const TailRange rg = tail_range(s, mode, i);
+    if (rg.lo >= rg.hi) return -1;
+    const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + s.off[i]);
+    const unsigned long long me = s.tk[i];
+    const bool down = mode == 0;
+    const int b0 = down ? (rg.hi - 1) >> 3 : rg.lo >> 3;
+    const int bl = rg.lo >> 3, bh = (rg.hi - 1) >> 3;
+    uint4 x[kTailLaneBlocks];
+#pragma unroll
+    for (int j = 0; j < kTailLaneBlocks; ++j) {
+        const int b = down ? b0 - j : b0 + j;
+        x[j] = (b >= bl && b <= bh) ? __ldg(run + b) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int j = 0; j < kTailLaneBlocks; ++j) {
+        const int b = down ? b0 - j : b0 + j;
+        if (b < bl || b > bh) break;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const int k = down ? 7 - kk : kk;
+            const int pos = 8 * b + k;
+            if (pos < rg.lo || pos >= rg.hi) continue;
+            ++scanned;
+            const int u = tail_elem(x[j], k);
+            if (tail_conflict(s, mode, u, tk_color(me), tk_rank(me))) return u;
+        }
+    }
+    const int nb = down ? b0 - kTailLaneBlocks : b0 + kTailLaneBlocks;  // next block in scan order
+    if (down ? nb < bl : nb > bh) return -1;
+    s.res[i] = (unsigned short)(down ? 8 * (nb + 1) : 8 * nb);  // down: scan [lo, res); up: [res, hi)
+    return -2;
+}
+
+// Warp scan of the rest of i's range (from s.res[i] on, in scan order): 128
+// blocks per step, four per lane, all loads of the step in flight; the
+// conflicting winner nearest the start of the range (the same on all lanes),
+// or -1.
+__device__ __forceinline__ int tail_scan_warp(const Params &p, const TailSmem &s, int mode, int i,
+                                              unsigned &scanned) {
+    const int lane = threadIdx.x & 31;
+    const TailRange rg0 = tail_range(s, mode, i);
+    const bool down = mode == 0;
+    const int lo = down ? rg0.lo : (int)s.res[i], hi = down ? (int)s.res[i] : rg0.hi;
+    const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + s.off[i]);
+    const unsigned long long me = s.tk[i];
+    const int bl = lo >> 3, bh = (hi - 1) >> 3;
+    for (int step = 0; bl + step * 128 <= bh; ++step) {
+        uint4 x[4];
+        int bb[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int d = step * 128 + t * 32 + lane;  // distance in blocks from the start
+            bb[t] = down ? bh - d : bl + d;
+            x[t] = (bb[t] >= bl && bb[t] <= bh) ? __ldg(run + bb[t]) : make_uint4(0, 0, 0, 0);
+        }
+        unsigned best = 0xffffffffu;  // distance in entries from the start << 16 | local id
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (bb[t] < bl || bb[t] > bh) continue;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int pos = 8 * bb[t] + k;
+                if (pos < lo || pos >= hi) continue;
+                const int u = tail_elem(x[t], k);
+                if (tail_conflict(s, mode, u, tk_color(me), tk_rank(me))) {
+                    const unsigned dist = (unsigned)(down ? hi - 1 - pos : pos - lo);
+                    best = min(best, (dist << 16) | (unsigned)u);
+                }
+            }
+        }
+        if (lane == 0) scanned += (unsigned)min(hi - lo - step * 1024, 1024);
+        best = __reduce_min_sync(kFull, best);
+        if (best != 0xffffffffu) return (int)(best & 0xffffu);
+    }
+    return -1;
+}
+
+template <bool kBatched>
+__global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params p) {
+    Counters *ctr = p.ctr;
+    if (__ldcg(&ctr->tail) == 0) return;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    const int T = p.tail_max;
+    const TailSmem s = tail_smem(s_raw, T);
+    __shared__ unsigned s_nq, s_nlq, s_nfb, s_alive, s_nkeep;
+    __shared__ unsigned long long s_D, s_kdeg, s_work;
+    __shared__ int s_kmax;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kTailThreads / 32;
+    const int nT = (int)__ldcg(&ctr->tail_n);
+    const int rule = p.rule;
+    const bool sorted = __ldcg(&ctr->unsorted_pairs) == __ldcg(&ctr->boundary_pairs);
+    const int mode = (sorted && rule <= 1) ? rule : 2;
+    const unsigned long long t0 = __ldcg(&ctr->t_start);
+    long long r = __ldcg(&ctr->round);
+    // ---- load the worklist's state
+    if (tid == 0) {
+        s_D = 0;
+        s_alive = (unsigned)nT;
+        s_kmax = 0;
+        s_nq = s_nlq = s_nfb = s_nkeep = 0;
+        s_kdeg = s_work = 0;
+    }
+    __syncthreads();
+    unsigned long long dsum = 0;
+    for (int i = tid; i < nT; i += kTailThreads) {
+        const int32_t v = __ldcg(p.tlist + i);
+        const unsigned d = __ldcg(p.tdeg + i);
+        s.vid[i] = v;
+        s.deg[i] = (int32_t)d;
+        s.off[i] = __ldcg(p.toff + i);
+        s.cnt[i] = (unsigned short)__ldcg(p.tcnt + i);
+        s.low[i] = (unsigned short)__ldcg(p.tlow + i);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s.bits[j * T + i] = __ldcg(p.bm + (size_t)j * p.np + v);
+        // the last witness, if it is still on the worklist (it is a neighbour
+        // that wins against v: the grid only records those)
+        const int32_t w = __ldcg(p.witness + v);
+        s.wit[i] = (short)((w >= 0 && w < p.n && __ldcg(p.colors + w) <= 0) ? __ldcg(p.tloc + w) : -1);
+        dsum += d;
+    }
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+    if (lane == 0 && dsum) atomicAdd(&s_D, dsum);
+    __syncthreads();
+    // ranks: lower id wins (rule 0), higher id wins (rule 1), or higher
+    // degree, then lower id (rule 2: the rank is the position among W_r)
+    for (int i = tid; i < nT; i += kTailThreads) {
+        unsigned rank;
+        if (rule == 0) {
+            rank = 0x7fffffffu - (unsigned)s.vid[i];
+        } else if (rule == 1) {
+            rank = (unsigned)s.vid[i];
+        } else {
+            rank = 0;
+            const int di = s.deg[i], vi = s.vid[i];
+            for (int j = 0; j < nT; ++j) {
+                const int dj = s.deg[j], vj = s.vid[j];
+                rank += (di != dj ? di > dj : vi < vj) ? 1u : 0u;
+            }
+        }
+        s.tk[i] = (1ull << 32) | rank;  // on the worklist (any nonzero color)
+    }
+    __syncthreads();
+    unsigned long long sum_w = 0, sum_d = 0, sum_next = 0, entries = 0, sum_rescan = 0;
+    long long trounds = 0;
+    bool ok = true;
+    for (;; ++r) {
+        const unsigned alive = s_alive;
+        if (alive == 0) break;
+        if (r > p.max_rounds) {
+            if (tid == 0) raise_error(p, kErrNoConvergence);
+            ok = false;
+            break;
+        }
+        if (tid == 0) {
+            sum_w += alive;
+            sum_d += s_D;
+            if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)alive;
+        }
+        // ---- FirstFit from the bitmaps
+        for (int i = tid; i < nT; i += kTailThreads) {
+            const unsigned long long t = s.tk[i];
+            if (tk_color(t) == 0) continue;
+            unsigned c = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const unsigned wv = s.bits[j * T + i];
+                if (c == 0 && ~wv) c = (unsigned)(j * 32 + __ffs(~wv));
+            }
+            if (c == 0) s.q[atomicAdd(&s_nfb, 1u)] = (unsigned short)i;  // 256 colors in use
+            s.tk[i] = ((unsigned long long)(c ? c : 1u) << 32) | tk_rank(t);
+        }
+        __syncthreads();
+        if (s_nfb) {  // full bitmaps: first fit over the final colors of the whole row
+            const unsigned nfb = s_nfb;
+            for (unsigned k = warp; k < nfb; k += nwarps) {
+                const int i = s.q[k];
+                long long rs, re;
+                int32_t vb;
+                row_of<kBatched>(p, s.vid[i], rs, re, vb);
+                const int c = warp_first_fit(p.ci, p.m, p.colors, rs, re, vb, lane, p.n);
+                if (lane == 0) s.tk[i] = ((unsigned long long)c << 32) | tk_rank(s.tk[i]);
+            }
+            __syncthreads();
+            if (tid == 0) s_nfb = 0;
+        }
+        if (tid == 0 && r <= kTraceCap)
+            p.trace[kTraceFields * (r - 1) + 1] = (long long)(globaltimer() - t0);
+        // ---- ConflictResolve: the witness first, a scan of the run if it does not settle
+        for (int i = tid; i < nT; i += kTailThreads) {
+            const unsigned c = tk_color(s.tk[i]);
+            if (c == 0) continue;
+            const int w = s.wit[i];
+            if (w >= 0 && tk_color(s.tk[w]) == c) continue;  // loses again, to the same neighbour
+            s.q[atomicAdd(&s_nq, 1u)] = (unsigned short)i;
+        }
+        __syncthreads();
+        const unsigned nq = s_nq;
+        unsigned work = 0;
+        unsigned long long kdeg = 0;
+        int kmax = 0;
+        for (unsigned k = tid; k < nq; k += kTailThreads) {  // first blocks: one lane each
+            const int i = s.q[k];
+            const int u = tail_scan_lane(p, s, mode, i, work);
+            if (u >= 0) {
+                s.wit[i] = (short)u;
+            } else if (u == -2) {
+                s.lq[atomicAdd(&s_nlq, 1u)] = (unsigned short)i;
+            } else {  // keeps its color
+                const unsigned c = tk_color(s.tk[i]);
+                s.kq[atomicAdd(&s_nkeep, 1u)] = (unsigned short)i;
+                __stcg(p.colors + s.vid[i], (int)c);
+                kmax = max(kmax, (int)c);
+                kdeg += (unsigned long long)s.deg[i];
+            }
+        }
+        __syncthreads();
+        const unsigned nlq = s_nlq;
+        for (unsigned k = warp; k < nlq; k += nwarps) {  // the rest of long scans: one warp each
+            const int i = s.lq[k];
+            const int u = tail_scan_warp(p, s, mode, i, work);
+            if (lane == 0) {
+                if (u >= 0) {
+                    s.wit[i] = (short)u;
+                } else {
+                    const unsigned c = tk_color(s.tk[i]);
+                    s.kq[atomicAdd(&s_nkeep, 1u)] = (unsigned short)i;
+                    __stcg(p.colors + s.vid[i], (int)c);
+                    kmax = max(kmax, (int)c);
+                    kdeg += (unsigned long long)s.deg[i];
+                }
+            }
+        }
+        __syncthreads();
+        // ---- keepers record their colors at their W-neighbours: one warp
+        // per keeper, four blocks per lane and step, all loads in flight
+        const unsigned nk = s_nkeep;
+        for (unsigned k = warp; k < nk; k += nwarps) {
+            const int i = s.kq[k];
+            const unsigned c = tk_color(s.tk[i]);
+            if (c > 256) continue;
+            unsigned *plane = s.bits + (size_t)((c - 1) >> 5) * T;
+            const unsigned bit = 1u << ((c - 1) & 31);
+            const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + s.off[i]);
+            const int n = s.cnt[i], nb = (n + 7) >> 3;
+            for (int b0 = 0; b0 < nb; b0 += 128) {
+                uint4 x[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int b = b0 + t * 32 + lane;
+                    x[t] = b < nb ? __ldg(run + b) : make_uint4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int b = b0 + t * 32 + lane;
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk)
+                        if (b < nb && 8 * b + kk < n) atomicOr(plane + tail_elem(x[t], kk), bit);
+                }
+            }
+            if (lane == 0) work += (unsigned)n;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            work += __shfl_xor_sync(kFull, work, o);
+            kdeg += __shfl_xor_sync(kFull, kdeg, o);
+            kmax = max(kmax, __shfl_xor_sync(kFull, kmax, o));
+        }
+        if (lane == 0) {
+            if (work) atomicAdd(&s_work, (unsigned long long)work);
+            if (kdeg) atomicAdd(&s_kdeg, kdeg);
+            if (kmax) atomicMax(&s_kmax, kmax);
+        }
+        __syncthreads();
+        // ---- keepers leave the worklist (judged on this round's colors: only now)
+        for (unsigned k = tid; k < nk; k += kTailThreads) {
+            const int i = s.kq[k];
+            s.tk[i] = (unsigned long long)tk_rank(s.tk[i]);
+        }
+        __syncthreads();  // every thread has read the round's counters
+        if (tid == 0) {
+            const unsigned left = s_alive - nk;
+            sum_next += left;
+            sum_rescan += nq;
+            entries += s_work;
+            s_alive = left;
+            s_D -= s_kdeg;
+            s_nkeep = 0;
+            s_kdeg = s_work = 0;
+            s_nq = s_nlq = 0;
+            if (r <= kTraceCap) {
+                p.trace[kTraceFields * (r - 1) + 2] = (long long)(globaltimer() - t0);
+                p.trace[kTraceFields * (r - 1) + 3] = (long long)nq;
+            }
+        }
+        ++trounds;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (s_kmax) atomicMax(&ctr->kmax, s_kmax);
+        atomicAdd(&ctr->sum_w, sum_w);
+        atomicAdd(&ctr->sum_d, sum_d);
+        atomicAdd(&ctr->sum_next, sum_next);
+        atomicAdd(&ctr->tail_entries, entries);
+        atomicAdd(&ctr->sum_rescan, sum_rescan);
+        ctr->tail_rounds = trounds;
+        if (ok) {
+            ctr->rounds = r - 1;
+            ctr->round = r;
+        }
+    }
+}

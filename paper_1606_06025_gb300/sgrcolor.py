@@ -55,7 +55,10 @@ class Stats(ctypes.Structure):
                 ("sum_rescan", ctypes.c_int64),
                 ("num_colors", ctypes.c_int32),
                 ("rows_sorted", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("device_ms", ctypes.c_double)]
+                ("block_threads", ctypes.c_int32), ("device_ms", ctypes.c_double),
+                ("tail_rounds", ctypes.c_int64), ("sum_touch", ctypes.c_int64),
+                ("sum_dep", ctypes.c_int64), ("tail_entries", ctypes.c_int64),
+                ("tail_build", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -79,7 +82,8 @@ class ServerStats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("light_max", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("active_lists", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("active_lists", ctypes.c_int32),
+                ("tail_vertices", ctypes.c_int32)]
 
 
 def _load():
@@ -246,8 +250,8 @@ def sgr_get_tuning() -> dict:
     return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
 
-def sgr_set_tuning(light_max=0, chunk=0, blocks_per_sm=0, active_lists=0) -> None:
-    t = Tuning(light_max, chunk, blocks_per_sm, active_lists)
+def sgr_set_tuning(light_max=0, chunk=0, blocks_per_sm=0, active_lists=0, tail_vertices=0) -> None:
+    t = Tuning(light_max, chunk, blocks_per_sm, active_lists, tail_vertices)
     _check(_lib.sgr_set_tuning(ctypes.byref(t)), "sgr_set_tuning")
 
 
