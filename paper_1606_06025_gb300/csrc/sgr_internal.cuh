@@ -54,13 +54,13 @@ constexpr int kLightMaxStage = 32;               // largest light degree (staged
 constexpr int kTraceCap = 1 << 16;               // rounds recorded in the timeline
 constexpr int kTraceFields = 4;                  // |W_r|, ns at end of phase A / phase B, rescans
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;  // bounded device waits
-constexpr int kTailThreads = 512;                // threads of the tail CTA
+constexpr int kTailThreads = 1024;               // threads of the tail CTA
 constexpr int kTailMax = 3072;                   // largest |W_r| the tail CTA takes
 constexpr int kTailDefault = 3072;               // default hand-over size
 constexpr int kTailChunk = 1024;                 // row entries per warp item of the tail build
 constexpr long long kTailCapEntries = 24ll << 20;  // largest W-adjacency (16-bit entries)
 // dynamic shared memory of the tail CTA for t local vertices
-constexpr size_t tail_smem_bytes(int t) { return (size_t)t * (8 + 8 * 4 + 3 * 4 + 8 * 2) + 64; }
+constexpr size_t tail_smem_bytes(int t) { return (size_t)t * (8 + 8 * 4 + 4 * 4 + 9 * 2) + 64; }
 
 constexpr int kErrNoConvergence = SGR_ERR_NO_CONVERGENCE;
 constexpr int kErrTimeout = SGR_ERR_TIMEOUT;
@@ -150,6 +150,7 @@ struct Params {
     unsigned *tcl;             // det tail: per chunk, W-neighbours below the vertex, then their prefix
     int tail_chunks;           // det tail: capacity of tcc / tcl, less one
     unsigned short *tadj;      // det tail: W-neighbours as local ids, 16-byte aligned runs
+    unsigned short *tstage;    // det tail: the same per chunk, kTailChunk entries a chunk
     int32_t *sw;               // det: hub scatter list slots
     unsigned int *scb;         // det: hub scatter list chunk bases
     Counters *ctr;

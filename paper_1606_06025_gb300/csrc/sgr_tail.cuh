@@ -61,20 +61,25 @@ __device__ __forceinline__ void block_push_capped(const bool (&flag)[kLightUnrol
     __syncthreads();
 }
 
-// Exclusive scan in place of a[0..n) and b[0..n) by the whole CTA (a[n],
-// b[n] receive the totals); tiles of 4 entries per thread, each thread's
-// four consecutive.  Ends with a __syncthreads().
+// Exclusive scan in place of a[0..n) and b[0..n) (b may be null) by the
+// whole CTA (a[n], b[n] receive the totals); tiles of 16 consecutive entries
+// per thread, all loads of a tile in flight.  Ends with a __syncthreads().
+constexpr int kScanPer = 16;
+
 __device__ void cta_scan2(unsigned *a, unsigned *b, unsigned n) {
     __shared__ unsigned s_wa[kWarps], s_wb[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned ca = 0, cb = 0;  // carries from earlier tiles
-    for (unsigned base = 0; base < n; base += 4 * kBlock) {
-        const unsigned i0 = base + 4 * threadIdx.x;
-        unsigned va[4], vb[4], sa = 0, sb = 0;
+    for (unsigned base = 0; base < n; base += kScanPer * kBlock) {
+        const unsigned i0 = base + kScanPer * threadIdx.x;
+        unsigned va[kScanPer], vb[kScanPer], sa = 0, sb = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kScanPer; ++k) {
             va[k] = i0 + k < n ? __ldcg(a + i0 + k) : 0u;
             vb[k] = (b && i0 + k < n) ? __ldcg(b + i0 + k) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
             sa += va[k];
             sb += vb[k];
         }
@@ -104,7 +109,7 @@ __device__ void cta_scan2(unsigned *a, unsigned *b, unsigned n) {
         pa += ia - sa;
         pb += ib - sb;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kScanPer; ++k) {
             if (i0 + k < n) {
                 a[i0 + k] = pa;
                 if (b) b[i0 + k] = pb;
@@ -123,7 +128,7 @@ __device__ void cta_scan2(unsigned *a, unsigned *b, unsigned n) {
     __syncthreads();
 }
 
-// CTA 0, after the compaction: the chunk prefix of the passes over the rows
+// CTA 0, after the compaction: the chunk prefix of the pass over the rows
 // (ceil(degree / kTailChunk) warp items per local vertex).
 __device__ __noinline__ void tail_chunk_prefix(const Params &p, unsigned nT) {
     for (unsigned i = threadIdx.x; i < nT; i += blockDim.x)
@@ -134,19 +139,39 @@ __device__ __noinline__ void tail_chunk_prefix(const Params &p, unsigned nT) {
     __syncthreads();
 }
 
-// CTA 0, after the count pass: per local vertex its W-neighbours (tcnt), the
+// CTA 0, after the row pass: per local vertex its W-neighbours (tcnt), the
 // ones below it (tlow) and the start of its run (its count rounded up to 8,
 // so that every run starts on 16 bytes); per chunk (in place) the exclusive
 // prefix of the counts.  Sets tail_fail if the runs exceed tail_cap.
 __device__ __noinline__ void tail_run_prefix(const Params &p, unsigned nT) {
     const unsigned nch = __ldcg(p.tcp + nT);
     cta_scan2(p.tcc, p.tcl, nch);
-    for (unsigned i = threadIdx.x; i < nT; i += blockDim.x) {
-        const unsigned q0 = __ldcg(p.tcp + i), q1 = __ldcg(p.tcp + i + 1);
-        const unsigned c = __ldcg(p.tcc + q1) - __ldcg(p.tcc + q0);
-        p.tcnt[i] = c;
-        p.tlow[i] = __ldcg(p.tcl + q1) - __ldcg(p.tcl + q0);
-        p.toff[i] = (c + 7u) & ~7u;
+    constexpr int kPer = (kTailMax + kBlock - 1) / kBlock;
+    unsigned q0[kPer], q1[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const unsigned i = threadIdx.x + k * blockDim.x;
+        q0[k] = i < nT ? __ldcg(p.tcp + i) : 0u;
+        q1[k] = i < nT ? __ldcg(p.tcp + i + 1) : 0u;
+    }
+    unsigned c0[kPer], c1[kPer], l0[kPer], l1[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const bool in = threadIdx.x + k * blockDim.x < nT;
+        c0[k] = in ? __ldcg(p.tcc + q0[k]) : 0u;
+        c1[k] = in ? __ldcg(p.tcc + q1[k]) : 0u;
+        l0[k] = in ? __ldcg(p.tcl + q0[k]) : 0u;
+        l1[k] = in ? __ldcg(p.tcl + q1[k]) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const unsigned i = threadIdx.x + k * blockDim.x;
+        if (i < nT) {
+            const unsigned c = c1[k] - c0[k];
+            p.tcnt[i] = c;
+            p.tlow[i] = l1[k] - l0[k];
+            p.toff[i] = (c + 7u) & ~7u;
+        }
     }
     __syncthreads();
     cta_scan2(p.toff, nullptr, nT);
@@ -154,13 +179,13 @@ __device__ __noinline__ void tail_run_prefix(const Params &p, unsigned nT) {
     __syncthreads();
 }
 
-// One warp item of a pass over the rows: entries [a, b) of local vertex i's
-// row.  Lane l takes four consecutive 16-byte blocks of each 128-block step
-// (all loads in flight), so lane order is row order.  kFill = false counts
-// the neighbours still on the worklist (color <= 0) and those of them below
-// the vertex into tcc[q] / tcl[q]; kFill = true writes their local ids into
-// the vertex's run, in row order, at the chunk's offset from the count pass.
-template <bool kBatched, bool kFill>
+// One warp item of the pass over the rows: entries [a, b) of local vertex
+// i's row.  Lane l takes four consecutive 16-byte blocks of each 128-block
+// step (all loads in flight), so lane order is row order.  The neighbours
+// still on the worklist (color <= 0) go, as local ids and in row order, to
+// the chunk's slot of kTailChunk entries in tstage; their number and the
+// number of them below the vertex go to tcc[q] / tcl[q].
+template <bool kBatched>
 __device__ __noinline__ void tail_chunk_pass(const Params &p, unsigned nT, unsigned q) {
     const int lane = threadIdx.x & 31;
     const unsigned i = hub_entry(p.tcp, nT, q);
@@ -170,9 +195,8 @@ __device__ __noinline__ void tail_chunk_pass(const Params &p, unsigned nT, unsig
     int32_t vb;
     row_of<kBatched>(p, v, s, e, vb);
     const long long a = s + (long long)j * kTailChunk, b = min(e, a + kTailChunk);
-    unsigned short *out = nullptr;
-    if (kFill) out = p.tadj + __ldcg(p.toff + i) + (__ldcg(p.tcc + q) - __ldcg(p.tcc + __ldcg(p.tcp + i)));
-    unsigned total = 0, below = 0, put = 0;
+    unsigned short *out = p.tstage + (size_t)q * kTailChunk;
+    unsigned put = 0, below = 0;
     for (long long q0 = a >> 2; (q0 << 2) < b; q0 += 128) {
         int4 x[4];
 #pragma unroll
@@ -191,49 +215,47 @@ __device__ __noinline__ void tail_chunk_pass(const Params &p, unsigned nT, unsig
                 in[t][k] = idx >= a && idx < b && (unsigned)u < (unsigned)p.n && u != v;
                 cw[t][k] = in[t][k] ? __ldcg(p.colors + u) : 1;
             }
-        unsigned c = 0, cl = 0;
+        int32_t lu[4][4];
+        unsigned c = 0;
 #pragma unroll
         for (int t = 0; t < 4; ++t)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 in[t][k] = in[t][k] && cw[t][k] <= 0;
                 c += in[t][k] ? 1u : 0u;
-                cl += (in[t][k] && vb + elem(x[t], k) < v) ? 1u : 0u;
+                below += (in[t][k] && vb + elem(x[t], k) < v) ? 1u : 0u;
+                lu[t][k] = in[t][k] ? __ldcg(p.tloc + vb + elem(x[t], k)) : 0;
             }
-        if constexpr (!kFill) {
-            total += c;
-            below += cl;
-        } else {
-            int32_t lu[4][4];
+        unsigned incl = c;
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) lu[t][k] = in[t][k] ? __ldcg(p.tloc + vb + elem(x[t], k)) : 0;
-            unsigned incl = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned tt = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += tt;
-            }
-            unsigned pos = put + incl - c;
-            put += __shfl_sync(kFull, incl, 31);
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (in[t][k]) out[pos++] = (unsigned short)lu[t][k];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned tt = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += tt;
         }
+        unsigned pos = put + incl - c;
+        put += __shfl_sync(kFull, incl, 31);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (in[t][k]) out[pos++] = (unsigned short)lu[t][k];
     }
-    if constexpr (!kFill) {
-        for (int o = 16; o > 0; o >>= 1) {
-            total += __shfl_xor_sync(kFull, total, o);
-            below += __shfl_xor_sync(kFull, below, o);
-        }
-        if (lane == 0) {
-            p.tcc[q] = total;
-            p.tcl[q] = below;
-        }
+    for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(kFull, below, o);
+    if (lane == 0) {
+        p.tcc[q] = put;
+        p.tcl[q] = below;
     }
+}
+
+// Copy of chunk q's staged entries to its place in the run of its vertex.
+__device__ __noinline__ void tail_chunk_copy(const Params &p, unsigned nT, unsigned q) {
+    const int lane = threadIdx.x & 31;
+    const unsigned i = hub_entry(p.tcp, nT, q);
+    const unsigned first = __ldcg(p.tcc + __ldcg(p.tcp + i));
+    const unsigned e0 = __ldcg(p.tcc + q), n = __ldcg(p.tcc + q + 1) - e0;
+    const unsigned short *src = p.tstage + (size_t)q * kTailChunk;
+    unsigned short *dst = p.tadj + __ldcg(p.toff + i) + (e0 - first);
+    for (unsigned k = lane; k < n; k += 32) dst[k] = src[k];
 }
 
 // The grid's part of the hand-over at the top of round r (all CTAs call it
@@ -276,16 +298,16 @@ __device__ __noinline__ int tail_build(const Params &p, unsigned &gen, unsigned 
     if (blockIdx.x == 0) tail_chunk_prefix(p, nT);
     if (!grid_barrier(p, gen)) return -1;
     if (__ldcg(&ctr->tail_fail)) return 0;
-    // (3) count the W-neighbours per chunk
+    // (3) the W-neighbours of every chunk, staged in row order
     const unsigned nch = __ldcg(p.tcp + nT);
-    for (unsigned q = global_warp(); q < nch; q += total_warps()) tail_chunk_pass<kBatched, false>(p, nT, q);
+    for (unsigned q = global_warp(); q < nch; q += total_warps()) tail_chunk_pass<kBatched>(p, nT, q);
     if (!grid_barrier(p, gen)) return -1;
     // (4) CTA 0: run starts and chunk offsets
     if (blockIdx.x == 0) tail_run_prefix(p, nT);
     if (!grid_barrier(p, gen)) return -1;
     if (__ldcg(&ctr->tail_fail)) return 0;
     // (5) the runs, each in row order
-    for (unsigned q = global_warp(); q < nch; q += total_warps()) tail_chunk_pass<kBatched, true>(p, nT, q);
+    for (unsigned q = global_warp(); q < nch; q += total_warps()) tail_chunk_copy(p, nT, q);
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->tail = 1;
     return 1;  // the end of the launch orders these writes before the tail CTA
 }
@@ -322,6 +344,8 @@ struct TailSmem {
     unsigned short *q;       // [T] unsettled vertices of the round (also: full bitmaps)
     unsigned short *lq;      // [T] unsettled vertices whose scan continues past the lane's blocks
     unsigned short *kq;      // [T] keepers of the round
+    unsigned short *al;      // [2][T]: the vertices still on the worklist, by round parity
+    unsigned *lbest;         // [T] per long-queue entry: nearest conflict (distance << 16 | local id)
 };
 
 __device__ __forceinline__ TailSmem tail_smem(unsigned char *raw, int T) {
@@ -338,6 +362,8 @@ __device__ __forceinline__ TailSmem tail_smem(unsigned char *raw, int T) {
     s.q = s.res + T;
     s.lq = s.q + T;
     s.kq = s.lq + T;
+    s.al = s.kq + T;
+    s.lbest = (unsigned *)(s.al + 2 * T);
     return s;
 }
 
@@ -370,53 +396,38 @@ __device__ __forceinline__ bool tail_conflict(const TailSmem &s, int mode, int u
     return tk_color(t) == c && (mode != 2 || tk_rank(t) > mine);
 }
 
-constexpr int kTailLaneBlocks = 8;
+// First scan of an unsettled vertex: a group of kTailGroup lanes, one
+// 16-byte block (8 entries) per lane and step, blocks in scan order by lane,
+// kTailGroupSteps steps at most; a warp scans 32 / kTailGroup vertices at a
+// time.  Vertices whose range goes on past these blocks without a conflict
+// are finished by whole warps, segment by segment (tail_scan_segment).
+constexpr int kTailGroup = 4;
+constexpr int kTailGroupSteps = 2;
+constexpr int kTailGroupBlocks = kTailGroup * kTailGroupSteps;
 
-// Lane scan of the first kTailLaneBlocks blocks of i's range in scan order
-// (all loaded before the checks).  Returns the conflicting winner nearest the
-// start, -1 if the range has none, or -2 if these blocks have none and the
-// range goes on (s.res[i] is where it goes on).
-__device__ __forceinline__ int tail_scan_lane(const Params &p, const TailSmem &s, int mode, int i,
-                                              unsigned &scanned) {
-    const TailRange rg = tail_range(s, mode, i);
-    if (rg.lo >= rg.hi) return -1;
-    const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + s.off[i]);
-    const unsigned long long me = s.tk[i];
+// First conflicting winner of one block in scan order (down: from its top
+// entry), positions restricted to [lo, hi); -1 if none.
+__device__ __forceinline__ int tail_block_hit(const TailSmem &s, int mode, const uint4 &x, int b, int lo, int hi,
+                                              unsigned c, unsigned mine) {
+    int hit = -1;
     const bool down = mode == 0;
-    const int b0 = down ? (rg.hi - 1) >> 3 : rg.lo >> 3;
-    const int bl = rg.lo >> 3, bh = (rg.hi - 1) >> 3;
-    uint4 x[kTailLaneBlocks];
 #pragma unroll
-    for (int j = 0; j < kTailLaneBlocks; ++j) {
-        const int b = down ? b0 - j : b0 + j;
-        x[j] = (b >= bl && b <= bh) ? __ldg(run + b) : make_uint4(0, 0, 0, 0);
+    for (int kk = 0; kk < 8; ++kk) {
+        const int k = down ? kk : 7 - kk;  // visited last wins: the first in scan order
+        const int pos = 8 * b + k;
+        if (pos < lo || pos >= hi) continue;
+        const int u = tail_elem(x, k);
+        if (tail_conflict(s, mode, u, c, mine)) hit = u;
     }
-#pragma unroll
-    for (int j = 0; j < kTailLaneBlocks; ++j) {
-        const int b = down ? b0 - j : b0 + j;
-        if (b < bl || b > bh) break;
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            const int k = down ? 7 - kk : kk;
-            const int pos = 8 * b + k;
-            if (pos < rg.lo || pos >= rg.hi) continue;
-            ++scanned;
-            const int u = tail_elem(x[j], k);
-            if (tail_conflict(s, mode, u, tk_color(me), tk_rank(me))) return u;
-        }
-    }
-    const int nb = down ? b0 - kTailLaneBlocks : b0 + kTailLaneBlocks;  // next block in scan order
-    if (down ? nb < bl : nb > bh) return -1;
-    s.res[i] = (unsigned short)(down ? 8 * (nb + 1) : 8 * nb);  // down: scan [lo, res); up: [res, hi)
-    return -2;
+    return hit;
 }
 
-// Warp scan of the rest of i's range (from s.res[i] on, in scan order): 128
-// blocks per step, four per lane, all loads of the step in flight; the
-// conflicting winner nearest the start of the range (the same on all lanes),
-// or -1.
-__device__ __forceinline__ int tail_scan_warp(const Params &p, const TailSmem &s, int mode, int i,
-                                              unsigned &scanned) {
+// Warp scan of segment j (128 blocks, four per lane, all loads in flight) of
+// the rest of i's range, from s.res[i] on in scan order.  Returns the
+// nearest conflicting winner in the segment as (distance from the start of
+// the rest << 16 | local id), the same on all lanes, or 0xffffffff.
+__device__ __forceinline__ unsigned tail_scan_segment(const Params &p, const TailSmem &s, int mode, int i,
+                                                      int j, unsigned &scanned) {
     const int lane = threadIdx.x & 31;
     const TailRange rg0 = tail_range(s, mode, i);
     const bool down = mode == 0;
@@ -424,35 +435,38 @@ __device__ __forceinline__ int tail_scan_warp(const Params &p, const TailSmem &s
     const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + s.off[i]);
     const unsigned long long me = s.tk[i];
     const int bl = lo >> 3, bh = (hi - 1) >> 3;
-    for (int step = 0; bl + step * 128 <= bh; ++step) {
-        uint4 x[4];
-        int bb[4];
+    uint4 x[4];
+    int bb[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int d = step * 128 + t * 32 + lane;  // distance in blocks from the start
-            bb[t] = down ? bh - d : bl + d;
-            x[t] = (bb[t] >= bl && bb[t] <= bh) ? __ldg(run + bb[t]) : make_uint4(0, 0, 0, 0);
-        }
-        unsigned best = 0xffffffffu;  // distance in entries from the start << 16 | local id
+    for (int t = 0; t < 4; ++t) {
+        const int d = j * 128 + t * 32 + lane;  // distance in blocks from the start
+        bb[t] = down ? bh - d : bl + d;
+        x[t] = (hi > lo && bb[t] >= bl && bb[t] <= bh) ? __ldg(run + bb[t]) : make_uint4(0, 0, 0, 0);
+    }
+    unsigned best = 0xffffffffu;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if (bb[t] < bl || bb[t] > bh) continue;
+    for (int t = 0; t < 4; ++t) {
+        if (hi <= lo || bb[t] < bl || bb[t] > bh) continue;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int pos = 8 * bb[t] + k;
-                if (pos < lo || pos >= hi) continue;
-                const int u = tail_elem(x[t], k);
-                if (tail_conflict(s, mode, u, tk_color(me), tk_rank(me))) {
-                    const unsigned dist = (unsigned)(down ? hi - 1 - pos : pos - lo);
-                    best = min(best, (dist << 16) | (unsigned)u);
-                }
+        for (int k = 0; k < 8; ++k) {
+            const int pos = 8 * bb[t] + k;
+            if (pos < lo || pos >= hi) continue;
+            const int u = tail_elem(x[t], k);
+            if (tail_conflict(s, mode, u, tk_color(me), tk_rank(me))) {
+                const unsigned dist = (unsigned)(down ? hi - 1 - pos : pos - lo);
+                best = min(best, (dist << 16) | (unsigned)u);
             }
         }
-        if (lane == 0) scanned += (unsigned)min(hi - lo - step * 1024, 1024);
-        best = __reduce_min_sync(kFull, best);
-        if (best != 0xffffffffu) return (int)(best & 0xffffu);
     }
-    return -1;
+    if (lane == 0) scanned += (unsigned)max(0, min(hi - lo - j * 1024, 1024));
+    return __reduce_min_sync(kFull, best);
+}
+
+// Blocks of the rest of i's range (from s.res[i] on).
+__device__ __forceinline__ int tail_rest_blocks(const TailSmem &s, int mode, int i) {
+    const TailRange rg0 = tail_range(s, mode, i);
+    const int lo = mode == 0 ? rg0.lo : (int)s.res[i], hi = mode == 0 ? (int)s.res[i] : rg0.hi;
+    return hi > lo ? ((hi - 1) >> 3) - (lo >> 3) + 1 : 0;
 }
 
 template <bool kBatched>
@@ -462,7 +476,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
     extern __shared__ __align__(16) unsigned char s_raw[];
     const int T = p.tail_max;
     const TailSmem s = tail_smem(s_raw, T);
-    __shared__ unsigned s_nq, s_nlq, s_nfb, s_alive, s_nkeep;
+    __shared__ unsigned s_nq, s_nlq, s_nfb, s_alive, s_nkeep, s_nnext;
     __shared__ unsigned long long s_D, s_kdeg, s_work;
     __shared__ int s_kmax;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kTailThreads / 32;
@@ -477,7 +491,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         s_D = 0;
         s_alive = (unsigned)nT;
         s_kmax = 0;
-        s_nq = s_nlq = s_nfb = s_nkeep = 0;
+        s_nq = s_nlq = s_nfb = s_nkeep = s_nnext = 0;
         s_kdeg = s_work = 0;
     }
     __syncthreads();
@@ -496,6 +510,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         // that wins against v: the grid only records those)
         const int32_t w = __ldcg(p.witness + v);
         s.wit[i] = (short)((w >= 0 && w < p.n && __ldcg(p.colors + w) <= 0) ? __ldcg(p.tloc + w) : -1);
+        s.al[i] = (unsigned short)i;
         dsum += d;
     }
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
@@ -522,6 +537,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
     __syncthreads();
     unsigned long long sum_w = 0, sum_d = 0, sum_next = 0, entries = 0, sum_rescan = 0;
     long long trounds = 0;
+    int par = 0;
+    const unsigned short *al = s.al;
     bool ok = true;
     for (;; ++r) {
         const unsigned alive = s_alive;
@@ -537,9 +554,9 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)alive;
         }
         // ---- FirstFit from the bitmaps
-        for (int i = tid; i < nT; i += kTailThreads) {
+        for (unsigned k = tid; k < alive; k += kTailThreads) {
+            const int i = al[k];
             const unsigned long long t = s.tk[i];
-            if (tk_color(t) == 0) continue;
             unsigned c = 0;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -566,9 +583,9 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         if (tid == 0 && r <= kTraceCap)
             p.trace[kTraceFields * (r - 1) + 1] = (long long)(globaltimer() - t0);
         // ---- ConflictResolve: the witness first, a scan of the run if it does not settle
-        for (int i = tid; i < nT; i += kTailThreads) {
+        for (unsigned k = tid; k < alive; k += kTailThreads) {
+            const int i = al[k];
             const unsigned c = tk_color(s.tk[i]);
-            if (c == 0) continue;
             const int w = s.wit[i];
             if (w >= 0 && tk_color(s.tk[w]) == c) continue;  // loses again, to the same neighbour
             s.q[atomicAdd(&s_nq, 1u)] = (unsigned short)i;
@@ -578,29 +595,75 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         unsigned work = 0;
         unsigned long long kdeg = 0;
         int kmax = 0;
-        for (unsigned k = tid; k < nq; k += kTailThreads) {  // first blocks: one lane each
-            const int i = s.q[k];
-            const int u = tail_scan_lane(p, s, mode, i, work);
-            if (u >= 0) {
-                s.wit[i] = (short)u;
-            } else if (u == -2) {
-                s.lq[atomicAdd(&s_nlq, 1u)] = (unsigned short)i;
-            } else {  // keeps its color
-                const unsigned c = tk_color(s.tk[i]);
-                s.kq[atomicAdd(&s_nkeep, 1u)] = (unsigned short)i;
-                __stcg(p.colors + s.vid[i], (int)c);
-                kmax = max(kmax, (int)c);
-                kdeg += (unsigned long long)s.deg[i];
+        {  // first blocks of every unsettled vertex: kTailGroup lanes each
+            constexpr int kPerWarp = 32 / kTailGroup;
+            const int g = lane / kTailGroup, gl = lane % kTailGroup;
+            const unsigned gmask = ((1u << kTailGroup) - 1u) << (g * kTailGroup);
+            for (unsigned base = warp * kPerWarp; base < nq; base += nwarps * kPerWarp) {
+                const unsigned idx = base + g;
+                const bool act = idx < nq;
+                const int i = act ? (int)s.q[idx] : 0;
+                const TailRange rg = act ? tail_range(s, mode, i) : TailRange{0, 0};
+                const bool down = mode == 0;
+                const unsigned long long me = s.tk[i];
+                const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + s.off[i]);
+                const int bl = rg.lo >> 3, bh = rg.hi > rg.lo ? (rg.hi - 1) >> 3 : bl - 1;
+                const int nblk = bh - bl + 1;
+                int found = -1;
+                for (int step = 0; step < kTailGroupSteps; ++step) {
+                    const int d = step * kTailGroup + gl;
+                    const bool have = act && found < 0 && d < nblk;
+                    int hit = -1;
+                    if (have) {
+                        const int b = down ? bh - d : bl + d;
+                        hit = tail_block_hit(s, mode, __ldg(run + b), b, rg.lo, rg.hi, tk_color(me), tk_rank(me));
+                        work += 8;
+                    }
+                    const unsigned gb = __ballot_sync(kFull, hit >= 0) & gmask;
+                    const int src = gb ? __ffs(gb) - 1 : lane;
+                    const int h = __shfl_sync(kFull, hit, src);
+                    if (gb && found < 0) found = h;
+                    if (!__any_sync(kFull, act && found < 0 && (step + 1) * kTailGroup < nblk)) break;
+                }
+                if (act && gl == 0) {
+                    if (found >= 0) {
+                        s.wit[i] = (short)found;
+                    } else if (nblk <= kTailGroupBlocks) {  // no winner with its color: keeps it
+                        const unsigned c = tk_color(me);
+                        s.kq[atomicAdd(&s_nkeep, 1u)] = (unsigned short)i;
+                        __stcg(p.colors + s.vid[i], (int)c);
+                        kmax = max(kmax, (int)c);
+                        kdeg += (unsigned long long)s.deg[i];
+                    } else {  // the range goes on: a warp finishes it
+                        s.res[i] = (unsigned short)(down ? 8 * (bh - kTailGroupBlocks + 1) : 8 * (bl + kTailGroupBlocks));
+                        const unsigned k = atomicAdd(&s_nlq, 1u);
+                        s.lq[k] = (unsigned short)i;
+                        s.lbest[k] = 0xffffffffu;
+                    }
+                }
             }
         }
         __syncthreads();
         const unsigned nlq = s_nlq;
-        for (unsigned k = warp; k < nlq; k += nwarps) {  // the rest of long scans: one warp each
-            const int i = s.lq[k];
-            const int u = tail_scan_warp(p, s, mode, i, work);
-            if (lane == 0) {
-                if (u >= 0) {
-                    s.wit[i] = (short)u;
+        if (nlq) {  // the rest of long scans: segments of 1024 entries, 32 / nlq warps per vertex
+            const unsigned wpe = max(1u, (unsigned)nwarps / nlq), stride = (unsigned)nwarps / wpe;
+            for (unsigned k = warp / wpe; k < nlq && warp / wpe < stride; k += stride) {
+                const int i = s.lq[k];
+                const int nb = tail_rest_blocks(s, mode, i);
+                for (int j = warp % wpe; j * 128 < nb; j += wpe) {
+                    const unsigned b = tail_scan_segment(p, s, mode, i, j, work);
+                    if (b != 0xffffffffu) {  // the nearer segments are other warps' or scanned already
+                        if (lane == 0) atomicMin(s.lbest + k, b);
+                        break;
+                    }
+                }
+            }
+            __syncthreads();
+            for (unsigned k = tid; k < nlq; k += kTailThreads) {
+                const int i = s.lq[k];
+                const unsigned b = s.lbest[k];
+                if (b != 0xffffffffu) {
+                    s.wit[i] = (short)(b & 0xffffu);
                 } else {
                     const unsigned c = tk_color(s.tk[i]);
                     s.kq[atomicAdd(&s_nkeep, 1u)] = (unsigned short)i;
@@ -611,33 +674,36 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             }
         }
         __syncthreads();
-        // ---- keepers record their colors at their W-neighbours: one warp
-        // per keeper, four blocks per lane and step, all loads in flight
+        // ---- keepers record their colors at their W-neighbours: segments of
+        // 128 blocks (four per lane, all loads in flight), 32 / nk warps per keeper
         const unsigned nk = s_nkeep;
-        for (unsigned k = warp; k < nk; k += nwarps) {
-            const int i = s.kq[k];
-            const unsigned c = tk_color(s.tk[i]);
-            if (c > 256) continue;
-            unsigned *plane = s.bits + (size_t)((c - 1) >> 5) * T;
-            const unsigned bit = 1u << ((c - 1) & 31);
-            const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + s.off[i]);
-            const int n = s.cnt[i], nb = (n + 7) >> 3;
-            for (int b0 = 0; b0 < nb; b0 += 128) {
-                uint4 x[4];
+        if (nk) {
+            const unsigned wpk = max(1u, (unsigned)nwarps / nk), stride = (unsigned)nwarps / wpk;
+            for (unsigned k = warp / wpk; k < nk && warp / wpk < stride; k += stride) {
+                const int i = s.kq[k];
+                const unsigned c = tk_color(s.tk[i]);
+                if (c > 256) continue;
+                unsigned *plane = s.bits + (size_t)((c - 1) >> 5) * T;
+                const unsigned bit = 1u << ((c - 1) & 31);
+                const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + s.off[i]);
+                const int n = s.cnt[i], nb = (n + 7) >> 3;
+                for (int b0 = (int)(warp % wpk) * 128; b0 < nb; b0 += (int)wpk * 128) {
+                    uint4 x[4];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int b = b0 + t * 32 + lane;
-                    x[t] = b < nb ? __ldg(run + b) : make_uint4(0, 0, 0, 0);
+                    for (int t = 0; t < 4; ++t) {
+                        const int b = b0 + t * 32 + lane;
+                        x[t] = b < nb ? __ldg(run + b) : make_uint4(0, 0, 0, 0);
+                    }
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int b = b0 + t * 32 + lane;
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk)
+                            if (b < nb && 8 * b + kk < n) atomicOr(plane + tail_elem(x[t], kk), bit);
+                    }
                 }
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int b = b0 + t * 32 + lane;
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk)
-                        if (b < nb && 8 * b + kk < n) atomicOr(plane + tail_elem(x[t], kk), bit);
-                }
+                if (lane == 0 && warp % wpk == 0) work += (unsigned)n;
             }
-            if (lane == 0) work += (unsigned)n;
         }
         for (int o = 16; o > 0; o >>= 1) {
             work += __shfl_xor_sync(kFull, work, o);
@@ -655,6 +721,16 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             const int i = s.kq[k];
             s.tk[i] = (unsigned long long)tk_rank(s.tk[i]);
         }
+        __syncthreads();
+        if (nk) {  // the next round's list: the vertices still on the worklist
+            unsigned short *nal = s.al + (par ^ 1) * T;
+            for (unsigned k = tid; k < alive; k += kTailThreads) {
+                const int i = al[k];
+                if (tk_color(s.tk[i]) != 0) nal[atomicAdd(&s_nnext, 1u)] = (unsigned short)i;
+            }
+            par ^= 1;
+            al = s.al + par * T;
+        }
         __syncthreads();  // every thread has read the round's counters
         if (tid == 0) {
             const unsigned left = s_alive - nk;
@@ -666,6 +742,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             s_nkeep = 0;
             s_kdeg = s_work = 0;
             s_nq = s_nlq = 0;
+            s_nnext = 0;
             if (r <= kTraceCap) {
                 p.trace[kTraceFields * (r - 1) + 2] = (long long)(globaltimer() - t0);
                 p.trace[kTraceFields * (r - 1) + 3] = (long long)nq;
