@@ -35,6 +35,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 #include <mutex>
 
@@ -65,7 +66,15 @@ constexpr size_t tail_smem_bytes(int t) { return (size_t)t * (8 + 8 * 4 + 4 * 4 
 constexpr int kErrNoConvergence = SGR_ERR_NO_CONVERGENCE;
 constexpr int kErrTimeout = SGR_ERR_TIMEOUT;
 
+// The first kHotBytes of Counters are the fields every CTA reads after a
+// grid barrier; one warp per CTA copies them into shared memory at each
+// barrier (hot_counters() in sgr_kernels.cu), so that the grid's reads do
+// not all go to the same L2 line.  The barrier's arrival counter has a line
+// of its own.
+constexpr int kHotBytes = 256;
+
 struct Counters {
+    // ---- hot block (read through the per-CTA snapshot)
     unsigned int nl[2];             // light list sizes by round parity
     unsigned int nm[2];             // medium list sizes
     unsigned long long h64[2];      // hub lists: (entries << 32) | total chunks
@@ -75,6 +84,15 @@ struct Counters {
     unsigned long long ah64[2];     // det: activated hubs (entries << 32 | chunks)
     unsigned long long adeg[2];     // det: degree sum of the activated vertices
     unsigned long long wcount;      // det: |W_r|, vertices not yet committed
+    unsigned long long sc64;        // hub scatter list: (entries << 32) | total chunks
+    unsigned long long dcur;        // det: degree sum of the current worklist
+    int kmax;                       // largest committed color
+    int err;                        // 0 or a negative status
+    unsigned long long hot_pad[14];
+    // ---- grid barrier: arrivals (bits 0..62), error flag (bit 63)
+    unsigned long long bar;
+    unsigned long long bar_pad[15];
+    // ---- the rest
     unsigned long long nroots;      // det: vertices with no entry below them (round-1 keepers on ascending rows)
     unsigned long long t_start;     // globaltimer at the start of the launch that ran init
     int handoff;                    // det: init handed the rounds to the activation-list kernel
@@ -86,21 +104,18 @@ struct Counters {
     unsigned long long sum_dep;     // det: row entries read to find witness dependents
     unsigned long long tail_entries;  // det: W-adjacency entries the tail CTA read
     unsigned long long tail_build;  // det: row entries the tail hand-over scanned
-    unsigned long long bar;         // grid barrier: arrivals (bits 0..62), error flag (bit 63)
     unsigned int nslots;            // hub slots handed out
     unsigned int hwords;            // hub bitmap words handed out
-    int kmax;                       // largest committed color
-    int err;                        // 0 or a negative status
     unsigned long long unsorted_pairs;   // adjacent col_idx pairs with a[i] >= a[i+1]
     unsigned long long boundary_pairs;   // ... of them across row boundaries
     unsigned long long sum_w, sum_d, sum_dscan, sum_next, sum_scatter, sum_rescan;
-    unsigned long long sc64;        // hub scatter list: (entries << 32) | total chunks
-    unsigned long long dcur;        // det: degree sum of the current worklist
     unsigned long long nslow;       // det: worklist vertices that rescanned their row this round
     long long rounds;
     long long round;                // resumable launches: the next round to run
     long long t_init_ns;            // globaltimer: end of the init pass (after its barrier)
 };
+static_assert(offsetof(Counters, err) + sizeof(int) <= kHotBytes, "hot fields fit the snapshot");
+static_assert(offsetof(Counters, bar) == kHotBytes, "the barrier counter starts its own line");
 
 struct Params {
     const int32_t *ro;

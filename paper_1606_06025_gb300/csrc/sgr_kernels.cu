@@ -88,10 +88,37 @@ __device__ __forceinline__ void raise_error(const Params &p, int code) {
     atomicOr(&p.ctr->bar, kBarErr);
 }
 
+// The CTA's copy of the hot block of Counters (see kHotBytes), taken at the
+// last grid barrier or by load_hot_counters.
+__device__ __forceinline__ unsigned long long *hot_words() {
+    __shared__ __align__(16) unsigned long long s_hot[kHotBytes / 8];
+    return s_hot;
+}
+
+__device__ __forceinline__ const Counters &hot_counters() {
+    return *reinterpret_cast<const Counters *>(hot_words());
+}
+
+// Warp 0 copies the hot block (one 8-byte word per lane).
+__device__ __forceinline__ void copy_hot_block(const Params &p) {
+    static_assert(kHotBytes / 8 == 32, "one word per lane");
+    if (threadIdx.x < 32)
+        hot_words()[threadIdx.x] = __ldcg(reinterpret_cast<const unsigned long long *>(p.ctr) + threadIdx.x);
+}
+
+// Snapshot of the hot block for a launch that enters its round loop without
+// a barrier (all threads call it).
+__device__ __forceinline__ void load_hot_counters(const Params &p) {
+    __syncthreads();
+    copy_hot_block(p);
+    __syncthreads();
+}
+
 // Bounded grid barrier on a monotone arrival counter: barrier number `gen`
 // (per CTA, counted from 1) is passed once gen * nblocks CTAs have arrived.
 // The arrival is a release and the poll an acquire, so every write the CTA
-// made before the barrier is visible to every CTA after it.  Returns false
+// made before the barrier is visible to every CTA after it.  On the way out
+// warp 0 refreshes the CTA's snapshot of the hot counters.  Returns false
 // if this CTA must stop (timeout, or an error flagged by any CTA).
 __device__ bool grid_barrier(const Params &p, unsigned &gen) {
     __shared__ int s_ok;
@@ -116,6 +143,10 @@ __device__ bool grid_barrier(const Params &p, unsigned &gen) {
         }
         if (seen & kBarErr) ok = 0;
         s_ok = ok;
+    }
+    if (threadIdx.x < 32) {
+        __syncwarp();  // lane 0's acquire orders the other lanes' loads
+        copy_hot_block(p);
     }
     __syncthreads();
     return s_ok != 0;
@@ -1949,18 +1980,20 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
     }
     const bool prefix = sorted && p.rule == 0;
     const long long r_end = p.resume ? r + p.rounds_per_launch : LLONG_MAX;
+    if (kFront || p.resume) load_hot_counters(p);  // no barrier since the last writes
+    const Counters &hc = hot_counters();
     bool ok = true;
     bool tail_try = !kFast && p.tail_max > 0 && !p.resume;
     for (;; ++r) {
         if (r == r_end) break;
         const int par = (int)(r & 1), pn = par ^ 1;
-        const unsigned nl = __ldcg(&ctr->nl[par]);
-        const unsigned nm = __ldcg(&ctr->nm[par]);
-        const unsigned long long h64 = __ldcg(&ctr->h64[par]);
+        const unsigned nl = hc.nl[par];
+        const unsigned nm = hc.nm[par];
+        const unsigned long long h64 = hc.h64[par];
         // |W_r|: the list sizes, or (activation lists: not every loser is
         // pushed) the count of uncommitted vertices
         const unsigned long long wsize =
-            kFront ? __ldcg(&ctr->wcount)
+            kFront ? hc.wcount
                    : (unsigned long long)nl + nm + (unsigned long long)(h64 >> 32);
         if (wsize == 0) {
             if (recorder && !kFast) ctr->sc64 = 0;  // nobody is left to read those bitmaps
@@ -1972,7 +2005,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
         }
         const bool front = kFront && r >= 2;  // this round runs on A_r
         if (!kFast) {  // colors of hubs committed last round go to their neighbours' bitmaps
-            const unsigned long long sc64 = __ldcg(&ctr->sc64);
+            const unsigned long long sc64 = hc.sc64;
             if (sc64 >> 32) {
                 det_hub_scatter<kBatched>(p, sc64, kFront ? (int)r : 0, ListSet{1, par});
                 if (kFront) flush_push<kBatched>(p, ListSet{1, par});
@@ -1982,7 +2015,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
         // few vertices left: the tail CTA takes the remaining rounds (the
         // bitmaps are complete here, deferred hub scatters included)
         if (!kFast && tail_try && wsize <= (unsigned long long)p.tail_max &&
-            __ldcg(&ctr->dcur) <= (unsigned long long)p.tail_cap) {
+            hc.dcur <= (unsigned long long)p.tail_cap) {
             const int rc = tail_build<kBatched>(p, gen, (unsigned)wsize);
             if (rc < 0) {
                 ok = false;
@@ -1991,7 +2024,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             if (rc > 0) {
                 if (recorder) {
                     if (kFront && r >= 2) ctr->sum_next += wsize;  // |W_r|, losers of round r-1
-                    ctr->tail_build += __ldcg(&ctr->dcur);
+                    ctr->tail_build += hc.dcur;
                 }
                 break;
             }
@@ -2000,9 +2033,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
         unsigned anl = 0, anm = 0;
         unsigned long long ah = 0;
         if (front) {  // A_r is complete now
-            anl = __ldcg(&ctr->nal[par]);
-            anm = __ldcg(&ctr->nam[par]);
-            ah = __ldcg(&ctr->ah64[par]);
+            anl = hc.nal[par];
+            anm = hc.nam[par];
+            ah = hc.ah64[par];
             if ((unsigned long long)anl + anm + (ah >> 32) == 0) {
                 // nothing can change: only a non-symmetric input gets here
                 if (recorder) raise_error(p, kErrNoConvergence);
@@ -2017,7 +2050,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             } else {  // det: W_{r+1}'s counters were cleared during the last phase B
                 ctr->sc64 = 0;
                 ctr->sum_w += wsize;                       // |W_r|
-                ctr->sum_d += __ldcg(&ctr->dcur);          // D_r: degrees of W_r
+                ctr->sum_d += hc.dcur;                     // D_r: degrees of W_r
                 if (kFront && r >= 2) ctr->sum_next += wsize;  // |W_r| = losers of round r-1
             }
             if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)wsize;
@@ -2026,14 +2059,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
         if (!kFast && recorder) {  // worklist entries phase A visits
             if (front) {
                 ctr->sum_touch += (unsigned long long)anl + anm + (ah >> 32);
-                ctr->sum_dep += __ldcg(&ctr->adeg[par]);
+                ctr->sum_dep += hc.adeg[par];
             } else if (!shortcut) {
                 ctr->sum_touch += wsize;
             }
         }
         // ---- phase A: FirstFit over W_r (det round 1: every tentative color is 1)
         if (kFast) {
-            const int kmax = __ldcg(&ctr->kmax);
+            const int kmax = hc.kmax;
             fast_hub_assign<kBatched>(p, par, h64, kmax, acc);
             fast_medium_assign<kBatched>(p, p.mw[par], nm, acc);
             fast_light_assign<kBatched>(p, p.lw[par], nl, sbuf, acc);
@@ -2062,9 +2095,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             // A_r and its dependents).  On the activation lists every commit
             // activates its stale neighbours for round r+1 and no loser is
             // pushed: the ones not activated stay as they are.
-            const unsigned bnl = shortcut ? nl : __ldcg(&ctr->nul[par]);
-            const unsigned bnm = shortcut ? nm : __ldcg(&ctr->num[par]);
-            const unsigned long long bh = shortcut ? h64 : __ldcg(&ctr->uh64[par]);
+            const unsigned bnl = shortcut ? nl : hc.nul[par];
+            const unsigned bnm = shortcut ? nm : hc.num[par];
+            const unsigned long long bh = shortcut ? h64 : hc.uh64[par];
             const int act_r = kFront ? (int)(r + 1) : 0;
             if (recorder) {  // W_r's counters are in registers; U_{r+1} must start empty
                 ctr->sum_touch += (unsigned long long)bnl + bnm + (bh >> 32);
