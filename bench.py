@@ -417,7 +417,10 @@ def run_ours(args, rank, world, local):
                      "paper_model": {"bytes_per_launch": pb, "equivalent_gbs": pb / (kmean * 1e-3) / 1e9,
                                      "frac": pb / (kmean * 1e-3) / 1e9 / peak,
                                      "what": "Algorithms 4/5 as printed: rows re-read every round"},
-                     "kernel": "sgr_color_kernel", "peak_source": peak_src + " of measured"
+                     "kernel": ("the coloring launches of one call, timed together on their stream: "
+                                "sgr_color_kernel (init, rounds on the grid), its activation-list "
+                                "variant, sgr_tail_kernel (last rounds in one CTA)"),
+                     "peak_source": peak_src + " of measured"
                      if peak_src.startswith("measured") else peak_src},
     }
     if not args.no_cpu_baseline and world == 1:
