@@ -483,20 +483,33 @@ __device__ __forceinline__ long long vertex_degree(const Params &p, int32_t v) {
     return e - s;
 }
 
-// Append one vertex to its bin of L (one lane, global atomics).
+// Append one vertex to its bin of L (global atomics).  The lanes of a warp
+// that get here together and push to the same light or medium list share one
+// atomic; hubs take one each.
 template <bool kBatched>
 __device__ void list_push_one(const Params &p, ListSet L, int32_t v) {
     const int32_t bin = __ldcg(p.vslot + v);
     const long long d = (L.kind || bin >= 0) ? vertex_degree<kBatched>(p, v) : 0;
-    if (bin == -1) {
-        ls_l(p, L)[atomicAdd(ls_nl(p, L), 1u)] = v;
-    } else if (bin == -2) {
-        ls_m(p, L)[atomicAdd(ls_nm(p, L), 1u)] = v;
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, bin < 0 ? bin : 0);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    if (bin < 0) {
+        unsigned *cnt = bin == -1 ? ls_nl(p, L) : ls_nm(p, L);
+        int32_t *list = bin == -1 ? ls_l(p, L) : ls_m(p, L);
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        list[base + __popc(peers & lanemask_lt())] = v;
     } else {
         hub_list_push(ls_h64(p, L), ls_h(p, L), ls_hcb(p, L), bin,
                       (unsigned)((d + p.chunk - 1) / p.chunk));
     }
-    if (L.kind) atomicAdd(ls_deg(p, L), (unsigned long long)d);
+    if (L.kind) {  // the first active lane adds up the others' degrees
+        unsigned long long dsum = 0;
+        for (unsigned m = act; m; m &= m - 1)
+            dsum += __shfl_sync(act, (unsigned long long)d, __ffs(m) - 1);
+        if (lane == __ffs(act) - 1) atomicAdd(ls_deg(p, L), dsum);
+    }
 }
 
 // Vertices pushed by lanes on divergent paths are staged in shared memory and
@@ -1966,9 +1979,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
         sorted = __ldcg(&ctr->unsorted_pairs) == __ldcg(&ctr->boundary_pairs);
         r = 1;
         if (!kFast && p.front_ok && p.front_policy != 1) {
-            // hand the rounds to the activation-list kernel when few vertices
-            // commit in round 1 (every CTA decides alike from the counters)
-            const bool few = sorted && p.rule == 0 && 8 * __ldcg(&ctr->nroots) < (unsigned long long)p.n;
+            // hand the rounds to the activation-list kernel when the commits of
+            // round 1 can only stale few vertices: at most (round-1 keepers) x
+            // (average degree) activations, under n / 16 (a mesh in natural
+            // order; on random graphs most of W_2 would be activated and the
+            // whole-list rounds are faster).  Every CTA decides alike.
+            const unsigned long long roots = __ldcg(&ctr->nroots);
+            const bool few = sorted && p.rule == 0 && p.n > 0 &&
+                             16.0 * (double)roots * ((double)p.m / (double)p.n) < (double)p.n;
             if (p.front_policy == 2 || few) {
                 if (recorder) ctr->handoff = 1;
                 return;

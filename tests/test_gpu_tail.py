@@ -112,3 +112,15 @@ def test_tail_in_batches(tuning, tv):
             ref = oracle.det_sgr(g, rule)
             assert np.array_equal(got[b.vtx_off[i]:b.vtx_off[i + 1]], ref.colors), f"graph {i}"
             assert k[i] == ref.num_colors
+
+
+def test_activation_lists_past_the_push_buffer(tuning):
+    # forced onto the activation lists, a uniform graph this size activates
+    # about 8,000 vertices per CTA in round 2, more than a CTA's push buffer
+    # holds: the rest go to the lists through warp-aggregated global appends
+    g = gg.uniform(4_000_000, 10.0, seed=3)
+    ref = oracle.det_sgr(g)
+    tuning.sgr_set_tuning(active_lists=2)
+    check(tuning, g, "low_keeps", ref)
+    tuning.sgr_set_tuning(active_lists=2, tail_vertices=-1)
+    check(tuning, g, "low_keeps", ref)
