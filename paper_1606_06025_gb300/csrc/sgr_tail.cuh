@@ -370,6 +370,11 @@ __device__ __forceinline__ TailSmem tail_smem(unsigned char *raw, int T) {
 __device__ __forceinline__ unsigned tk_color(unsigned long long x) { return (unsigned)(x >> 32); }
 __device__ __forceinline__ unsigned tk_rank(unsigned long long x) { return (unsigned)x; }
 
+// A block of a run.  The tail CTA compacts the runs in place, so they are
+// read through the coherent path (plain global loads, cached in L1, which
+// sees the CTA's own writes after a __syncthreads), not the read-only one.
+__device__ __forceinline__ uint4 ld_run(const uint4 *q) { return *q; }
+
 // Entry k of a 16-byte block of eight 16-bit local ids.
 __device__ __forceinline__ int tail_elem(const uint4 &x, int k) {
     const unsigned w = k < 2 ? x.x : (k < 4 ? x.y : (k < 6 ? x.z : x.w));
@@ -441,7 +446,7 @@ __device__ __forceinline__ unsigned tail_scan_segment(const Params &p, const Tai
     for (int t = 0; t < 4; ++t) {
         const int d = j * 128 + t * 32 + lane;  // distance in blocks from the start
         bb[t] = down ? bh - d : bl + d;
-        x[t] = (hi > lo && bb[t] >= bl && bb[t] <= bh) ? __ldg(run + bb[t]) : make_uint4(0, 0, 0, 0);
+        x[t] = (hi > lo && bb[t] >= bl && bb[t] <= bh) ? ld_run(run + bb[t]) : make_uint4(0, 0, 0, 0);
     }
     unsigned best = 0xffffffffu;
 #pragma unroll
@@ -469,6 +474,48 @@ __device__ __forceinline__ int tail_rest_blocks(const TailSmem &s, int mode, int
     return hi > lo ? ((hi - 1) >> 3) - (lo >> 3) + 1 : 0;
 }
 
+// Drop the final vertices from i's run, in place and in order (one warp, 32
+// blocks a step; every write lands below every later read), and recount the
+// entries below the vertex.
+__device__ __forceinline__ void tail_compact_run(const Params &p, const TailSmem &s, int i) {
+    const int lane = threadIdx.x & 31;
+    unsigned short *run = p.tadj + s.off[i];
+    const int n = s.cnt[i], lo_old = s.low[i], nb = (n + 7) >> 3;
+    unsigned put = 0, low = 0;
+    for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int b = b0 + lane;
+        const uint4 x = b < nb ? ld_run(reinterpret_cast<const uint4 *>(run) + b) : make_uint4(0, 0, 0, 0);
+        unsigned keep = 0, kl = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int pos = 8 * b + k;
+            if (b < nb && pos < n && tk_color(s.tk[tail_elem(x, k)]) != 0) {
+                keep |= 1u << k;
+                kl += pos < lo_old ? 1u : 0u;
+            }
+        }
+        const unsigned c = __popc(keep);
+        unsigned incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        unsigned at = put + incl - c;
+        __syncwarp();  // every lane has read its block before any write
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if ((keep >> k) & 1u) run[at++] = (unsigned short)tail_elem(x, k);
+        put += __shfl_sync(kFull, incl, 31);
+        low += __reduce_add_sync(kFull, kl);
+        __syncwarp();
+    }
+    if (lane == 0) {
+        s.cnt[i] = (unsigned short)put;
+        s.low[i] = (unsigned short)low;
+    }
+}
+
 template <bool kBatched>
 __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params p) {
     Counters *ctr = p.ctr;
@@ -476,7 +523,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
     extern __shared__ __align__(16) unsigned char s_raw[];
     const int T = p.tail_max;
     const TailSmem s = tail_smem(s_raw, T);
-    __shared__ unsigned s_nq, s_nlq, s_nfb, s_alive, s_nkeep, s_nnext;
+    __shared__ unsigned s_nq, s_nlq, s_nfb, s_alive, s_nkeep, s_nnext, s_compact_at;
     __shared__ unsigned long long s_D, s_kdeg, s_work;
     __shared__ int s_kmax;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kTailThreads / 32;
@@ -492,6 +539,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         s_alive = (unsigned)nT;
         s_kmax = 0;
         s_nq = s_nlq = s_nfb = s_nkeep = s_nnext = 0;
+        s_compact_at = (unsigned)nT / 8;
         s_kdeg = s_work = 0;
     }
     __syncthreads();
@@ -543,6 +591,11 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
     for (;; ++r) {
         const unsigned alive = s_alive;
         if (alive == 0) break;
+        if (alive <= s_compact_at) {  // most of the worklist has gone: drop it from the runs
+            for (unsigned k = warp; k < alive; k += nwarps) tail_compact_run(p, s, al[k]);
+            __syncthreads();
+            if (tid == 0) s_compact_at = alive / 2;
+        }
         if (r > p.max_rounds) {
             if (tid == 0) raise_error(p, kErrNoConvergence);
             ok = false;
@@ -616,7 +669,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
                     int hit = -1;
                     if (have) {
                         const int b = down ? bh - d : bl + d;
-                        hit = tail_block_hit(s, mode, __ldg(run + b), b, rg.lo, rg.hi, tk_color(me), tk_rank(me));
+                        hit = tail_block_hit(s, mode, ld_run(run + b), b, rg.lo, rg.hi, tk_color(me), tk_rank(me));
                         work += 8;
                     }
                     const unsigned gb = __ballot_sync(kFull, hit >= 0) & gmask;
@@ -692,7 +745,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int b = b0 + t * 32 + lane;
-                        x[t] = b < nb ? __ldg(run + b) : make_uint4(0, 0, 0, 0);
+                        x[t] = b < nb ? ld_run(run + b) : make_uint4(0, 0, 0, 0);
                     }
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
