@@ -115,7 +115,7 @@ typedef struct {
     int32_t tail_vertices; /* deterministic mode: once at most this many
                               vertices are left on the worklist, the remaining
                               rounds run in one CTA on the subgraph they
-                              induce; 0 = library default (3072), -1 = never,
+                              induce; 0 = library default (2048), -1 = never,
                               else 1..3072.  The colors are the same. */
 } sgr_tuning;
 

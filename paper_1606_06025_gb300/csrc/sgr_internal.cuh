@@ -57,7 +57,7 @@ constexpr int kTraceFields = 4;                  // |W_r|, ns at end of phase A 
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;  // bounded device waits
 constexpr int kTailThreads = 1024;               // threads of the tail CTA
 constexpr int kTailMax = 3072;                   // largest |W_r| the tail CTA takes
-constexpr int kTailDefault = 3072;               // default hand-over size
+constexpr int kTailDefault = 2048;               // default hand-over size
 constexpr int kTailChunk = 1024;                 // row entries per warp item of the tail build
 constexpr long long kTailCapEntries = 24ll << 20;  // largest W-adjacency (16-bit entries)
 // dynamic shared memory of the tail CTA for t local vertices
