@@ -303,3 +303,15 @@ def test_full_size_det_active_list_policies(tuning, policy, name):
     assert st["sum_w"] == gold["det_sum_w"] and st["sum_d"] == gold["det_sum_d"]
     assert st["sum_next"] == gold["det_sum_next"]
     assert digest(got) == gold["det_colors_sha256"]
+
+
+def test_host_entry_large_upload_matches_device_entry(lib):
+    # col_idx of 38 MB through the host entry, twice in a row (the second
+    # upload reuses the library's device buffers of the first call)
+    g = gg.uniform(600_000, 16.0, seed=12)
+    assert g.m * 4 > (16 << 20)
+    dev, kd, _ = run(lib, g)
+    out = np.zeros(g.n, dtype=np.int32)
+    for _ in range(2):
+        kh = lib.sgr_color_host(g.n, g.row_offsets, g.col_idx, out, "det")
+        assert kh == kd and np.array_equal(out, dev)
