@@ -437,6 +437,12 @@ __device__ __forceinline__ unsigned hub_entry(const unsigned *cb, unsigned cnt, 
     return lo;
 }
 
+// Work items of a hub's ConflictResolve when only the entries below it are
+// read: one per chunk of them, at least one (the item that decides).
+__device__ __forceinline__ unsigned lower_chunks(int lowdeg, int chunk) {
+    return lowdeg > 0 ? (unsigned)((lowdeg + chunk - 1) / chunk) : 1u;
+}
+
 // Append a hub slot with its chunk count to a (count << 32 | chunks) list.
 __device__ __forceinline__ void hub_list_push(unsigned long long *ctr64, int32_t *slots,
                                               unsigned *cb, int32_t slot, unsigned nchunks) {
@@ -702,7 +708,7 @@ __device__ void det_assign_medium(const Params &p, int par, unsigned cnt, Acc &a
 // Hub list: one lane per entry (entries are slots; chunk counts come from
 // the chunk bases).
 template <bool kBatched>
-__device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64, Acc &acc) {
+__device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64, bool prefix, Acc &acc) {
     const int pn = par ^ 1;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const unsigned NW = total_warps();
@@ -720,7 +726,10 @@ __device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64
                 hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
                 acc.next += 1;
             } else {
-                hub_list_push(&p.ctr->uh64[par], p.uh[par], p.ucb[par], slot, nchunks);
+                // with ascending rows and lower ids keeping, ConflictResolve
+                // only reads the entries below the hub: one item per chunk of them
+                const unsigned nu = prefix ? lower_chunks(__ldcg(p.lowdeg + v[0]), p.chunk) : nchunks;
+                hub_list_push(&p.ctr->uh64[par], p.uh[par], p.ucb[par], slot, nu);
             }
         }
     }
@@ -1349,10 +1358,12 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
     }
 }
 
+// lower_only: the list's items cover only the entries below each hub
+// (lower_chunks); otherwise its whole row.
 template <bool kBatched>
 __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsigned *cbs,
                                unsigned long long h64, int pn, bool prefix, bool push_losers,
-                               Acc &acc) {
+                               bool lower_only, Acc &acc) {
     const int lane = threadIdx.x & 31;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const long long CH = p.chunk;
@@ -1381,7 +1392,8 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
                 if (lane == 0) __stcg(p.witness + v, found);
             }
         }
-        const unsigned nchunks = (unsigned)((deg + CH - 1) / CH);
+        const unsigned nchunks =
+            lower_only ? lower_chunks(__ldcg(p.lowdeg + v), p.chunk) : (unsigned)((deg + CH - 1) / CH);
         if (lane == 0) {
             // hconf stops the other items early; the decision travels in the
             // completion counter itself (conflicts in the high word).  The
@@ -1399,7 +1411,9 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
                 __stcg(p.hconf + slot, 0u);
                 __stcg(p.hdone + slot, 0ull);
                 if (lost) {
-                    if (push_losers) hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
+                    if (push_losers)
+                        hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot,
+                                      (unsigned)((deg + CH - 1) / CH));
                     acc.next += 1;
                 } else {
                     __stcg(p.colors + v, c);
@@ -2094,7 +2108,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             front_assign_light<kBatched>(p, par, anl, (int)r, prefix, ListSet{0, par});
             flush_push<kBatched>(p, ListSet{0, par});
         } else if (!shortcut) {
-            det_assign_hubs<kBatched>(p, par, h64, acc);
+            det_assign_hubs<kBatched>(p, par, h64, prefix, acc);
             det_assign_medium<kBatched>(p, par, nm, acc);
             det_assign_light<kBatched>(p, par, nl, acc);
         }
@@ -2133,7 +2147,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
                 }
             }
             det_hub_detect<kBatched>(p, shortcut ? p.hw[par] : p.uh[par],
-                                     shortcut ? p.hcb[par] : p.ucb[par], bh, pn, prefix, !kFront, b);
+                                     shortcut ? p.hcb[par] : p.ucb[par], bh, pn, prefix, !kFront,
+                                     prefix && !shortcut && !kFront, b);
             det_medium_detect<kBatched>(p, shortcut ? p.mw[par] : p.um[par], bnm,
                                         kFront ? nullptr : p.mw[pn], &ctr->nm[pn], prefix, act_r,
                                         ListSet{1, pn}, b);
