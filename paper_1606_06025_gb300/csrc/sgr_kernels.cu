@@ -1304,9 +1304,46 @@ __device__ __forceinline__ int32_t det_scan_warp(const Params &p, int32_t v, int
     return -1;
 }
 
+// Lane scan of the (at most) 16 entries of [s, hi) nearest below hi, all
+// loads in flight (ascending row, lower ids win): the nearest one holding
+// magnitude c, or -1; *rest = the part still unscanned ([s, *rest)).
+__device__ __forceinline__ int32_t scan_below_16(const Params &p, int c, long long s, long long hi, int32_t vb,
+                                                 long long *rest, unsigned long long &scanned) {
+    const long long qt = (hi - 1) >> 2, qs = s >> 2;
+    int4 x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = qt - k >= qs ? load4(p.ci, qt - k, p.m) : make_int4(0, 0, 0, 0);
+    int cw[4][4];
+    bool ok[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long i = ((qt - k) << 2) + j;
+            const int32_t w = vb + elem(x[k], j);
+            ok[k][j] = qt - k >= qs && i >= s && i < hi && (unsigned)w < (unsigned)p.n;
+            cw[k][j] = ok[k][j] ? __ldcg(p.colors + w) : 0;
+        }
+    *rest = max(s, (qt - 3) << 2);
+    for (int k = 0; k < 4; ++k)
+        for (int j = 3; j >= 0; --j) {
+            if (!ok[k][j]) continue;
+            scanned++;
+            if (mag(cw[k][j]) == c) return vb + elem(x[k], j);
+        }
+    return -1;
+}
+
+// Medium vertices (light_max < degree <= chunk), a batch of up to 32 per warp.
+// The witness first; then, with ascending rows and lower ids keeping, each
+// lane scans the entries nearest below its vertex (in round 1, when every
+// tentative color is 1, a vertex loses iff it has a lower neighbour, the
+// nearest of which becomes its witness); the rest are scanned by the whole
+// warp one vertex at a time, and keepers record their color in their
+// neighbours' bitmaps with the whole warp.
 template <bool kBatched>
 __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
-                                  unsigned *out_cnt, bool prefix, int act_r, ListSet A,
+                                  unsigned *out_cnt, bool prefix, bool round1, int act_r, ListSet A,
                                   Acc &acc) {
     const int lane = threadIdx.x & 31;
     const unsigned NW = total_warps(), B = warp_batch(cnt);
@@ -1314,37 +1351,60 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
         const unsigned i = b + lane;
         const int nb = (int)min(B, cnt - b);
         int32_t vl = 0, vbl = 0, wl = -1;
-        long long sl = 0, el = 0;
+        long long sl = 0, el = 0, restl = 0;
         int cl = 0;
-        bool settled = false;
+        bool settled = false, found = false, resolved = false;
         if (lane < nb) {
             vl = __ldcg(list + i);
-            wl = __ldcg(p.witness + vl);
-            cl = -__ldcg(p.colors + vl);
+            wl = round1 ? -1 : __ldcg(p.witness + vl);
+            cl = round1 ? 1 : -__ldcg(p.colors + vl);
             row_of<kBatched>(p, vl, sl, el, vbl);
+            const int ld = prefix ? __ldcg(p.lowdeg + vl) : 0;
             if (wl >= 0) settled = mag(__ldcg(p.colors + wl)) == cl;
+            restl = el;
+            if (prefix && !settled) {
+                const long long split = sl + ld;
+                if (round1) {  // every tentative color is 1: any lower neighbour wins
+                    found = ld > 0;
+                    if (found) __stcg(p.witness + vl, vbl + __ldg(p.ci + split - 1));
+                    resolved = true;
+                } else if (ld == 0) {
+                    resolved = true;  // nothing below: keeps its color
+                } else {
+                    const int32_t f = scan_below_16(p, cl, sl, split, vbl, &restl, acc.dscan);
+                    found = f >= 0;
+                    if (found) __stcg(p.witness + vl, f);
+                    resolved = found || restl <= sl;
+                }
+            }
         }
-        unsigned lost = __ballot_sync(kFull, settled);
-        for (int j = 0; j < nb; ++j) {
-            if ((lost >> j) & 1u) continue;
+        unsigned lost = __ballot_sync(kFull, settled || found);
+        const unsigned keep = __ballot_sync(kFull, lane < nb && resolved && !found && !settled);
+        const unsigned open = __ballot_sync(kFull, lane < nb && !settled && !resolved);
+        for (unsigned m = keep | open; m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
             const int32_t v = __shfl_sync(kFull, vl, j), vb = __shfl_sync(kFull, vbl, j);
             const long long s = __shfl_sync(kFull, sl, j), e = __shfl_sync(kFull, el, j);
+            const long long rest = __shfl_sync(kFull, restl, j);
             const int c = __shfl_sync(kFull, cl, j);
-            const int32_t found = det_scan_warp<kBatched>(p, v, c, (int32_t)(e - s), s, s, e, vb,
-                                                          prefix, nullptr, acc.dscan);
-            if (found >= 0) {
-                lost |= 1u << j;
-                if (lane == 0) __stcg(p.witness + v, found);
-            } else {
-                if (lane == 0) {
-                    __stcg(p.colors + v, c);
-                    acc.kmax = max(acc.kmax, c);
-                    acc.keep++;
-                    acc.kdeg += (unsigned long long)(e - s);
-                    acc.scatter += (unsigned long long)(e - s);
+            if ((open >> j) & 1u) {
+                // prefix: the part below the lane's entries; otherwise the whole row
+                const int32_t f = det_scan_warp<kBatched>(p, v, c, (int32_t)(e - s), s, s,
+                                                          prefix ? rest : e, vb, prefix, nullptr, acc.dscan);
+                if (f >= 0) {
+                    lost |= 1u << j;
+                    if (lane == 0) __stcg(p.witness + v, f);
+                    continue;
                 }
-                scatter_color<kBatched>(p, c, s, e, vb, lane, 32, act_r, A);
             }
+            if (lane == 0) {
+                __stcg(p.colors + v, c);
+                acc.kmax = max(acc.kmax, c);
+                acc.keep++;
+                acc.kdeg += (unsigned long long)(e - s);
+                acc.scatter += (unsigned long long)(e - s);
+            }
+            scatter_color<kBatched>(p, c, s, e, vb, lane, 32, act_r, A);
         }
         if (lost) {
             if (lane == 0) acc.next += (unsigned long long)__popc(lost);
@@ -2150,8 +2210,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
                                      shortcut ? p.hcb[par] : p.ucb[par], bh, pn, prefix, !kFront,
                                      prefix && !shortcut && !kFront, b);
             det_medium_detect<kBatched>(p, shortcut ? p.mw[par] : p.um[par], bnm,
-                                        kFront ? nullptr : p.mw[pn], &ctr->nm[pn], prefix, act_r,
-                                        ListSet{1, pn}, b);
+                                        kFront ? nullptr : p.mw[pn], &ctr->nm[pn], prefix, shortcut,
+                                        act_r, ListSet{1, pn}, b);
             det_light_detect<kBatched>(p, shortcut ? p.lw[par] : p.ul[par], bnl,
                                        kFront ? nullptr : p.lw[pn], &ctr->nl[pn], prefix, shortcut,
                                        act_r, ListSet{1, pn}, b);
