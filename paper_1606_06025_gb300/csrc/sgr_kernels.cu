@@ -1419,11 +1419,13 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
 }
 
 // lower_only: the list's items cover only the entries below each hub
-// (lower_chunks); otherwise its whole row.
+// (lower_chunks); otherwise its whole row.  round1 with prefix: every
+// tentative color is 1, so a hub loses iff it has an entry below it (the
+// nearest of which becomes its witness) and no item scans.
 template <bool kBatched>
 __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsigned *cbs,
                                unsigned long long h64, int pn, bool prefix, bool push_losers,
-                               bool lower_only, Acc &acc) {
+                               bool lower_only, bool round1, Acc &acc) {
     const int lane = threadIdx.x & 31;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const long long CH = p.chunk;
@@ -1440,11 +1442,15 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
         const long long a = s + (long long)j * CH, b = min(e, a + CH);
         const int c = -__ldcg(p.colors + v);
         bool conf = false;
-        if (j == 0) {  // the first item tries the witness
+        if (round1 && prefix) {
+            const int ld = __ldcg(p.lowdeg + v);
+            conf = ld > 0;
+            if (conf && j == 0 && lane == 0) __stcg(p.witness + v, vb + __ldg(p.ci + s + ld - 1));
+        } else if (j == 0) {  // the first item tries the witness
             const int32_t w = __ldcg(p.witness + v);
             conf = w >= 0 && mag(__ldcg(p.colors + w)) == c;
         }
-        if (!conf && !__ldcg(p.hconf + slot)) {
+        if (!conf && !(round1 && prefix) && !__ldcg(p.hconf + slot)) {
             const int32_t found = det_scan_warp<kBatched>(p, v, c, (int32_t)deg, s, a, b, vb, prefix,
                                                           p.hconf + slot, acc.dscan);
             if (found >= 0) {
@@ -2208,7 +2214,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             }
             det_hub_detect<kBatched>(p, shortcut ? p.hw[par] : p.uh[par],
                                      shortcut ? p.hcb[par] : p.ucb[par], bh, pn, prefix, !kFront,
-                                     prefix && !shortcut && !kFront, b);
+                                     prefix && !shortcut && !kFront, shortcut, b);
             det_medium_detect<kBatched>(p, shortcut ? p.mw[par] : p.um[par], bnm,
                                         kFront ? nullptr : p.mw[pn], &ctr->nm[pn], prefix, shortcut,
                                         act_r, ListSet{1, pn}, b);
