@@ -706,8 +706,10 @@ def run_serve(args, rank, world, local):
                    "mean_vertices": float(np.mean(sizes))},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "server_p50_ms": st["p50_ms"], "server_p99_ms": st["p99_ms"],
+        # open loop: value follows the arrival rate while the server keeps up,
+        # so capacity is compared with capacity
         "burst_capacity_graphs_per_s": capacity, "sequential_graphs_per_s": seq_gps,
-        "speedup_vs_sequential": value / seq_gps,
+        "capacity_vs_sequential": capacity / seq_gps,
         "launches": st["launches"], "rounds": st["rounds"],
     }
     print(json.dumps(line), flush=True)
