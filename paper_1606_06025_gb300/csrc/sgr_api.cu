@@ -212,6 +212,10 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     int32_t *ul0 = (int32_t *)take(un * 4), *ul1 = (int32_t *)take(un * 4);
     int32_t *um0 = (int32_t *)take(un * 4), *um1 = (int32_t *)take(un * 4);
     int32_t *uh0 = (int32_t *)take(uhub * 4), *uh1 = (int32_t *)take(uhub * 4);
+    // item -> hub entry map of the unsettled hubs' lower-part work items
+    const size_t uitems = j.fast ? 1 : (size_t)(j.m / t.chunk) + sp.hub_max + 1;
+    unsigned *ui0 = (unsigned *)take(uitems * 4), *ui1 = (unsigned *)take(uitems * 4);
+    int32_t *uv0 = (int32_t *)take(uhub * 4), *uv1 = (int32_t *)take(uhub * 4);
     unsigned *ucb0 = (unsigned *)take(uhub * 4), *ucb1 = (unsigned *)take(uhub * 4);
     const size_t an = front ? (size_t)j.n : 1, ahub = front ? sp.hub_max : 1;
     int32_t *vslot = (int32_t *)take(j.fast ? 4 : (size_t)j.n * 4);
@@ -251,6 +255,10 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         p->ul[0] = ul0; p->ul[1] = ul1;
         p->um[0] = um0; p->um[1] = um1;
         p->uh[0] = uh0; p->uh[1] = uh1;
+        if (!j.fast) {
+            p->uitem[0] = ui0; p->uitem[1] = ui1;
+            p->uvert[0] = uv0; p->uvert[1] = uv1;
+        }
         p->ucb[0] = ucb0; p->ucb[1] = ucb1;
         p->al[0] = al0; p->al[1] = al1;
         p->am[0] = am0; p->am[1] = am1;

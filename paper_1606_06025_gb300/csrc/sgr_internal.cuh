@@ -134,6 +134,8 @@ struct Params {
     int32_t *ul[2];            // det: light vertices the witness did not settle (parity of r)
     int32_t *um[2];            // det: medium vertices the witness did not settle
     int32_t *uh[2];            // det: hub slots the witness did not settle
+    unsigned *uitem[2];        // det (optional): ConflictResolve work item -> entry of uh (lower-part items)
+    int32_t *uvert[2];         // det (optional): entry of uh -> vertex
     unsigned int *ucb[2];      // det: their chunk bases
     int32_t *hvert;
     unsigned int *hbase;

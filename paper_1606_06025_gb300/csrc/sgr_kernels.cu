@@ -729,7 +729,15 @@ __device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64
                 // with ascending rows and lower ids keeping, ConflictResolve
                 // only reads the entries below the hub: one item per chunk of them
                 const unsigned nu = prefix ? lower_chunks(__ldcg(p.lowdeg + v[0]), p.chunk) : nchunks;
-                hub_list_push(&p.ctr->uh64[par], p.uh[par], p.ucb[par], slot, nu);
+                const unsigned long long old =
+                    atomicAdd(&p.ctr->uh64[par], (1ull << 32) | (unsigned long long)nu);
+                const unsigned k = (unsigned)(old >> 32), cbu = (unsigned)old;
+                p.uh[par][k] = slot;
+                p.ucb[par][k] = cbu;
+                if (prefix && p.uitem[par]) {  // ConflictResolve finds its hub without a search
+                    p.uvert[par][k] = v[0];
+                    for (unsigned t = 0; t < nu; ++t) p.uitem[par][cbu + t] = k;
+                }
             }
         }
     }
@@ -1422,8 +1430,11 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
 // (lower_chunks); otherwise its whole row.  round1 with prefix: every
 // tentative color is 1, so a hub loses iff it has an entry below it (the
 // nearest of which becomes its witness) and no item scans.
+//   items / verts (lower_only lists, may be null): the entry of each work item
+// and the vertex of each entry, written when the list was built.
 template <bool kBatched>
 __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsigned *cbs,
+                               const unsigned *items, const int32_t *verts,
                                unsigned long long h64, int pn, bool prefix, bool push_losers,
                                bool lower_only, bool round1, Acc &acc) {
     const int lane = threadIdx.x & 31;
@@ -1431,10 +1442,11 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
     const long long CH = p.chunk;
     const unsigned NW = total_warps();
     for (unsigned q = global_warp(); q < nch; q += NW) {
-        const unsigned i = hub_entry(cbs, cnt, q);
+        const bool direct = items != nullptr;
+        const unsigned i = direct ? __ldcg(items + q) : hub_entry(cbs, cnt, q);
         const int32_t slot = __ldcg(slots + i);
         const unsigned j = q - __ldcg(cbs + i);
-        const int32_t v = __ldcg(p.hvert + slot);
+        const int32_t v = direct ? __ldcg(verts + i) : __ldcg(p.hvert + slot);
         long long s, e;
         int32_t vb;
         row_of<kBatched>(p, v, s, e, vb);
@@ -2212,9 +2224,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
                     ctr->adeg[par] = 0;
                 }
             }
+            const bool lower_only = prefix && !shortcut && !kFront;
             det_hub_detect<kBatched>(p, shortcut ? p.hw[par] : p.uh[par],
-                                     shortcut ? p.hcb[par] : p.ucb[par], bh, pn, prefix, !kFront,
-                                     prefix && !shortcut && !kFront, shortcut, b);
+                                     shortcut ? p.hcb[par] : p.ucb[par],
+                                     lower_only ? p.uitem[par] : nullptr,
+                                     lower_only ? p.uvert[par] : nullptr, bh, pn, prefix, !kFront,
+                                     lower_only, shortcut, b);
             det_medium_detect<kBatched>(p, shortcut ? p.mw[par] : p.um[par], bnm,
                                         kFront ? nullptr : p.mw[pn], &ctr->nm[pn], prefix, shortcut,
                                         act_r, ListSet{1, pn}, b);
