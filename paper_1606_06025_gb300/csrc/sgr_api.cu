@@ -81,7 +81,7 @@ std::mutex g_ctx_mu;
 std::vector<DevCtx *> g_ctx;
 
 std::mutex g_tune_mu;
-sgr_tuning g_tune = {32, 512, 0, 0, 0};
+sgr_tuning g_tune = {32, 1024, 0, 0, 0};
 
 thread_local sgr_stats t_stats;
 
