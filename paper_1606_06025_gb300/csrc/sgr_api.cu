@@ -232,8 +232,8 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     unsigned *tdeg = tmax ? (unsigned *)take((size_t)tmax * 4) : nullptr;
     unsigned *tcp = tmax ? (unsigned *)take((size_t)(tmax + 1) * 4) : nullptr;
     const long long tch = tmax ? tcap / sgr::kTailChunk + tmax + 1 : 0;  // chunks of the row passes
-    unsigned *tcc = tmax ? (unsigned *)take((size_t)(tch + 1) * 4) : nullptr;
-    unsigned *tcl = tmax ? (unsigned *)take((size_t)(tch + 1) * 4) : nullptr;
+    unsigned *tcc = tmax ? (unsigned *)take((size_t)tch * 4) : nullptr;
+    unsigned *tcm = tmax ? (unsigned *)take((size_t)tch * 4) : nullptr;
     unsigned short *tstage = tmax ? (unsigned short *)take((size_t)tch * sgr::kTailChunk * 2) : nullptr;
     int32_t *tloc = tmax ? (int32_t *)take((size_t)j.n * 4) : nullptr;
     unsigned short *tadj = tmax ? (unsigned short *)take((size_t)tcap * 2 + 16) : nullptr;
@@ -292,7 +292,7 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         p->tdeg = tdeg;
         p->tcp = tcp;
         p->tcc = tcc;
-        p->tcl = tcl;
+        p->tcm = tcm;
         p->tail_chunks = (int)tch;
         p->tstage = tstage;
         p->tloc = tloc;

@@ -163,9 +163,9 @@ struct Params {
     unsigned *tlow;            // det tail: W-neighbours below the vertex (tail_max)
     unsigned *tdeg;            // det tail: degree (tail_max)
     unsigned *tcp;             // det tail: chunk prefix of the build (tail_max + 1)
-    unsigned *tcc;             // det tail: per chunk, W-neighbours, then their prefix (tail_chunks + 1)
-    unsigned *tcl;             // det tail: per chunk, W-neighbours below the vertex, then their prefix
-    int tail_chunks;           // det tail: capacity of tcc / tcl, less one
+    unsigned *tcc;             // det tail: per chunk, its W-neighbours (tail_chunks)
+    unsigned *tcm;             // det tail: per chunk, its local vertex (tail_chunks)
+    int tail_chunks;           // det tail: capacity of tcc / tcm
     unsigned short *tadj;      // det tail: W-neighbours as local ids, 16-byte aligned runs
     unsigned short *tstage;    // det tail: the same per chunk, kTailChunk entries a chunk
     int32_t *sw;               // det: hub scatter list slots

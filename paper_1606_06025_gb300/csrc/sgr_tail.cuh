@@ -129,50 +129,28 @@ __device__ void cta_scan2(unsigned *a, unsigned *b, unsigned n) {
 }
 
 // CTA 0, after the compaction: the chunk prefix of the pass over the rows
-// (ceil(degree / kTailChunk) warp items per local vertex).
+// (ceil(degree / kTailChunk) warp items per local vertex) and the map from a
+// chunk to its local vertex.
 __device__ __noinline__ void tail_chunk_prefix(const Params &p, unsigned nT) {
     for (unsigned i = threadIdx.x; i < nT; i += blockDim.x)
         p.tcp[i] = (__ldcg(p.tdeg + i) + kTailChunk - 1) / kTailChunk;
     __syncthreads();
     cta_scan2(p.tcp, nullptr, nT);
-    if (threadIdx.x == 0 && __ldcg(p.tcp + nT) > (unsigned)p.tail_chunks) p.ctr->tail_fail = 1;
+    const bool fits = __ldcg(p.tcp + nT) <= (unsigned)p.tail_chunks;
+    if (threadIdx.x == 0 && !fits) p.ctr->tail_fail = 1;
+    if (fits)
+        for (unsigned i = threadIdx.x; i < nT; i += blockDim.x) {
+            const unsigned q1 = __ldcg(p.tcp + i + 1);
+            for (unsigned q = __ldcg(p.tcp + i); q < q1; ++q) p.tcm[q] = i;
+        }
     __syncthreads();
 }
 
-// CTA 0, after the row pass: per local vertex its W-neighbours (tcnt), the
-// ones below it (tlow) and the start of its run (its count rounded up to 8,
-// so that every run starts on 16 bytes); per chunk (in place) the exclusive
-// prefix of the counts.  Sets tail_fail if the runs exceed tail_cap.
+// CTA 0, after the row pass (which added every chunk's counts into tcnt and
+// tlow): the start of every run, its count rounded up to 8 so that every run
+// starts on 16 bytes.  Sets tail_fail if the runs exceed tail_cap.
 __device__ __noinline__ void tail_run_prefix(const Params &p, unsigned nT) {
-    const unsigned nch = __ldcg(p.tcp + nT);
-    cta_scan2(p.tcc, p.tcl, nch);
-    constexpr int kPer = (kTailMax + kBlock - 1) / kBlock;
-    unsigned q0[kPer], q1[kPer];
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const unsigned i = threadIdx.x + k * blockDim.x;
-        q0[k] = i < nT ? __ldcg(p.tcp + i) : 0u;
-        q1[k] = i < nT ? __ldcg(p.tcp + i + 1) : 0u;
-    }
-    unsigned c0[kPer], c1[kPer], l0[kPer], l1[kPer];
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const bool in = threadIdx.x + k * blockDim.x < nT;
-        c0[k] = in ? __ldcg(p.tcc + q0[k]) : 0u;
-        c1[k] = in ? __ldcg(p.tcc + q1[k]) : 0u;
-        l0[k] = in ? __ldcg(p.tcl + q0[k]) : 0u;
-        l1[k] = in ? __ldcg(p.tcl + q1[k]) : 0u;
-    }
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const unsigned i = threadIdx.x + k * blockDim.x;
-        if (i < nT) {
-            const unsigned c = c1[k] - c0[k];
-            p.tcnt[i] = c;
-            p.tlow[i] = l1[k] - l0[k];
-            p.toff[i] = (c + 7u) & ~7u;
-        }
-    }
+    for (unsigned i = threadIdx.x; i < nT; i += blockDim.x) p.toff[i] = (__ldcg(p.tcnt + i) + 7u) & ~7u;
     __syncthreads();
     cta_scan2(p.toff, nullptr, nT);
     if (threadIdx.x == 0 && (long long)__ldcg(p.toff + nT) > p.tail_cap) p.ctr->tail_fail = 1;
@@ -183,12 +161,13 @@ __device__ __noinline__ void tail_run_prefix(const Params &p, unsigned nT) {
 // i's row.  Lane l takes four consecutive 16-byte blocks of each 128-block
 // step (all loads in flight), so lane order is row order.  The neighbours
 // still on the worklist (color <= 0) go, as local ids and in row order, to
-// the chunk's slot of kTailChunk entries in tstage; their number and the
-// number of them below the vertex go to tcc[q] / tcl[q].
+// the chunk's slot of kTailChunk entries in tstage; their number goes to
+// tcc[q] and is added, with the number of them below the vertex, into the
+// vertex's tcnt / tlow.
 template <bool kBatched>
 __device__ __noinline__ void tail_chunk_pass(const Params &p, unsigned nT, unsigned q) {
     const int lane = threadIdx.x & 31;
-    const unsigned i = hub_entry(p.tcp, nT, q);
+    const unsigned i = __ldcg(p.tcm + q);
     const int32_t v = __ldcg(p.tlist + i);
     const unsigned j = q - __ldcg(p.tcp + i);
     long long s, e;
@@ -243,18 +222,23 @@ __device__ __noinline__ void tail_chunk_pass(const Params &p, unsigned nT, unsig
     for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(kFull, below, o);
     if (lane == 0) {
         p.tcc[q] = put;
-        p.tcl[q] = below;
+        if (put) atomicAdd(p.tcnt + i, put);
+        if (below) atomicAdd(p.tlow + i, below);
     }
 }
 
-// Copy of chunk q's staged entries to its place in the run of its vertex.
-__device__ __noinline__ void tail_chunk_copy(const Params &p, unsigned nT, unsigned q) {
+// Copy of chunk q's staged entries to its place in the run of its vertex:
+// after the entries of the vertex's earlier chunks (their counts summed by
+// the warp).
+__device__ __noinline__ void tail_chunk_copy(const Params &p, unsigned q) {
     const int lane = threadIdx.x & 31;
-    const unsigned i = hub_entry(p.tcp, nT, q);
-    const unsigned first = __ldcg(p.tcc + __ldcg(p.tcp + i));
-    const unsigned e0 = __ldcg(p.tcc + q), n = __ldcg(p.tcc + q + 1) - e0;
+    const unsigned i = __ldcg(p.tcm + q);
+    const unsigned n = __ldcg(p.tcc + q);
+    unsigned before = 0;
+    for (unsigned k = __ldcg(p.tcp + i) + lane; k < q; k += 32) before += __ldcg(p.tcc + k);
+    before = __reduce_add_sync(kFull, before);
     const unsigned short *src = p.tstage + (size_t)q * kTailChunk;
-    unsigned short *dst = p.tadj + __ldcg(p.toff + i) + (e0 - first);
+    unsigned short *dst = p.tadj + __ldcg(p.toff + i) + before;
     for (unsigned k = lane; k < n; k += 32) dst[k] = src[k];
 }
 
@@ -292,9 +276,12 @@ __device__ __noinline__ int tail_build(const Params &p, unsigned &gen, unsigned 
         if (blockIdx.x == 0 && threadIdx.x == 0) ctr->tail_fail = 1;
         return 0;  // every CTA sees the same nT and returns alike
     }
-    // (2) local ids; CTA 0: chunk prefix
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += gridDim.x * blockDim.x)
+    // (2) local ids, counts cleared; CTA 0: chunk prefix and chunk map
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += gridDim.x * blockDim.x) {
         p.tloc[__ldcg(p.tlist + i)] = (int32_t)i;
+        p.tcnt[i] = 0;
+        p.tlow[i] = 0;
+    }
     if (blockIdx.x == 0) tail_chunk_prefix(p, nT);
     if (!grid_barrier(p, gen)) return -1;
     if (__ldcg(&ctr->tail_fail)) return 0;
@@ -302,12 +289,12 @@ __device__ __noinline__ int tail_build(const Params &p, unsigned &gen, unsigned 
     const unsigned nch = __ldcg(p.tcp + nT);
     for (unsigned q = global_warp(); q < nch; q += total_warps()) tail_chunk_pass<kBatched>(p, nT, q);
     if (!grid_barrier(p, gen)) return -1;
-    // (4) CTA 0: run starts and chunk offsets
+    // (4) CTA 0: run starts
     if (blockIdx.x == 0) tail_run_prefix(p, nT);
     if (!grid_barrier(p, gen)) return -1;
     if (__ldcg(&ctr->tail_fail)) return 0;
     // (5) the runs, each in row order
-    for (unsigned q = global_warp(); q < nch; q += total_warps()) tail_chunk_copy(p, nT, q);
+    for (unsigned q = global_warp(); q < nch; q += total_warps()) tail_chunk_copy(p, q);
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->tail = 1;
     return 1;  // the end of the launch orders these writes before the tail CTA
 }
@@ -543,23 +530,45 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         s_kdeg = s_work = 0;
     }
     __syncthreads();
+    // every thread's vertices (kLoadPer at most) load together, one step of
+    // the chain vertex -> bitmaps, witness -> its color -> its local id at a
+    // time, so that each step has all of its loads in flight
+    constexpr int kLoadPer = (kTailMax + kTailThreads - 1) / kTailThreads;
     unsigned long long dsum = 0;
-    for (int i = tid; i < nT; i += kTailThreads) {
-        const int32_t v = __ldcg(p.tlist + i);
-        const unsigned d = __ldcg(p.tdeg + i);
-        s.vid[i] = v;
-        s.deg[i] = (int32_t)d;
-        s.off[i] = __ldcg(p.toff + i);
-        s.cnt[i] = (unsigned short)__ldcg(p.tcnt + i);
-        s.low[i] = (unsigned short)__ldcg(p.tlow + i);
+    int32_t lv[kLoadPer], lw[kLoadPer];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) s.bits[j * T + i] = __ldcg(p.bm + (size_t)j * p.np + v);
-        // the last witness, if it is still on the worklist (it is a neighbour
-        // that wins against v: the grid only records those)
-        const int32_t w = __ldcg(p.witness + v);
-        s.wit[i] = (short)((w >= 0 && w < p.n && __ldcg(p.colors + w) <= 0) ? __ldcg(p.tloc + w) : -1);
-        s.al[i] = (unsigned short)i;
-        dsum += d;
+    for (int k = 0; k < kLoadPer; ++k) {
+        const int i = tid + k * kTailThreads;
+        lv[k] = i < nT ? __ldcg(p.tlist + i) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kLoadPer; ++k) {
+        const int i = tid + k * kTailThreads;
+        lw[k] = -1;
+        if (i < nT) {
+            const int32_t v = lv[k];
+            const unsigned d = __ldcg(p.tdeg + i);
+            s.vid[i] = v;
+            s.deg[i] = (int32_t)d;
+            s.off[i] = __ldcg(p.toff + i);
+            s.cnt[i] = (unsigned short)__ldcg(p.tcnt + i);
+            s.low[i] = (unsigned short)__ldcg(p.tlow + i);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s.bits[j * T + i] = __ldcg(p.bm + (size_t)j * p.np + v);
+            lw[k] = __ldcg(p.witness + v);
+            s.al[i] = (unsigned short)i;
+            dsum += d;
+        }
+    }
+    // the last witness, if it is still on the worklist (it is a neighbour
+    // that wins against v: the grid only records those)
+    bool wl[kLoadPer];
+#pragma unroll
+    for (int k = 0; k < kLoadPer; ++k) wl[k] = lw[k] >= 0 && lw[k] < p.n && __ldcg(p.colors + lw[k]) <= 0;
+#pragma unroll
+    for (int k = 0; k < kLoadPer; ++k) {
+        const int i = tid + k * kTailThreads;
+        if (i < nT) s.wit[i] = (short)(wl[k] ? __ldcg(p.tloc + lw[k]) : -1);
     }
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
     if (lane == 0 && dsum) atomicAdd(&s_D, dsum);
