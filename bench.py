@@ -150,7 +150,14 @@ def alg_bytes(st, n, m, mode):
     writes) plus 4 B per entry FirstFit gathers (sum of D_r) and per entry
     ConflictResolve inspects.  Both: the init pass reads col_idx once (4 B per
     entry) and 24 B per vertex.  Neighbour color and bitmap accesses that hit
-    the L2-resident arrays are not counted."""
+    the L2-resident arrays are not counted.  Topology-driven schedule
+    (Algorithm 6), per iteration: the own color of all n vertices in both
+    passes (8n), and per vertex colored tentatively its row offsets in both
+    passes (16 B), its tentative write and its commit (8 B) and its row in
+    both passes (8 B per entry); the last iteration only reads the n colors
+    once."""
+    if mode == "topo":
+        return 8 * n * st["rounds"] + 4 * n + 24 * st["sum_w"] + 8 * st["sum_d"]
     if mode == "det":
         tail = 4 * st["tail_build"] + 4 * n if st["tail_rounds"] else 0
         return (24 * st["sum_touch"] + 4 * (st["sum_dscan"] + st["sum_scatter"] + st["sum_dep"])
@@ -408,7 +415,8 @@ def run_ours(args, rank, world, local):
                 "h2d_bytes_per_step": 4 * (n + 1) + 4 * m, "d2h_bytes_per_step": 4 * n},
         # per step: the round kernel, then (det) the activation-list kernel and
         # the tail kernel, each of which returns at once when not handed over
-        "gpu_launches": args.steps * (1 if args.mode == "fast" else 3),
+        # (topology-driven: two kernels per iteration, and the final one that finds nothing)
+        "gpu_launches": args.steps * {"fast": 1, "det": 3}.get(args.mode, 2 * (st["rounds"] + 1)),
         "step_ms": {"min": min(step_ms), "max": max(step_ms)},
         "tail_rounds": st["tail_rounds"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -419,7 +427,9 @@ def run_ours(args, rank, world, local):
                                      "what": "Algorithms 4/5 as printed: rows re-read every round"},
                      "kernel": ("the coloring launches of one call, timed together on their stream: "
                                 "sgr_color_kernel (init, rounds on the grid), its activation-list "
-                                "variant, sgr_tail_kernel (last rounds in one CTA)"),
+                                "variant, sgr_tail_kernel (last rounds in one CTA)") if args.mode != "topo" else
+                               ("the topology-driven iterations of one call (topo_assign_kernel and "
+                                "topo_resolve_kernel per iteration, host loop on a flag), event to event"),
                      "peak_source": peak_src + " of measured"
                      if peak_src.startswith("measured") else peak_src},
     }
@@ -724,7 +734,9 @@ def main():
     ap.add_argument("--workload", default="rmat20",
                     help="rmat20 | stencil192 | er20k | stencil128 | batch512 | batch64 | serve | "
                          "serve512 | er:N:D | rmat:S")
-    ap.add_argument("--mode", choices=["det", "fast"], default="det")
+    ap.add_argument("--mode", choices=["det", "fast", "topo"], default="det",
+                    help="det: the worklist rounds; fast: racy in place; topo: the deterministic "
+                         "rounds on the topology-driven schedule of Algorithm 6 (comparison)")
     ap.add_argument("--rule", choices=["low_keeps", "low_loses", "degree"], default="low_keeps",
                     help="loser rule (Sect. 3.2 heuristic = degree; Alg. 5 as printed = low_loses)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

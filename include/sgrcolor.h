@@ -28,6 +28,14 @@
  *     place while other vertices of the round do the same, as the paper's GPU
  *     code does (Sect. 3.1, "Color Clearing").  Always a valid coloring; the
  *     exact colors may change from run to run.
+ *   SGR_MODE_TOPO: the deterministic rounds on the topology-driven schedule of
+ *     Algorithm 6 (Sect. 3.1, the paper's baseline design): every iteration
+ *     visits all n vertices, FirstFit for those not final and
+ *     ConflictResolve for those holding a tentative color, and the host
+ *     relaunches the two passes while an iteration found a vertex to color.
+ *     Same colors, k and rounds as SGR_MODE_DETERMINISTIC; it is there to
+ *     compare the schedules.  sgr_color and sgr_color_host only; the other
+ *     entry points refuse it (SGR_ERR_INVALID_ARG).
  *   SGR_RULE_LOW_KEEPS (default): of two neighbours with the same color, the
  *     lower vertex id keeps it.
  *   SGR_RULE_LOW_LOSES: the lower id is recolored, as printed in Algorithm 2
@@ -72,6 +80,7 @@ typedef enum {
 
 #define SGR_MODE_DETERMINISTIC 0
 #define SGR_MODE_FAST 1
+#define SGR_MODE_TOPO 2
 #define SGR_MODE_MASK 0x3
 #define SGR_RULE_LOW_KEEPS (0 << 4)
 #define SGR_RULE_LOW_LOSES (1 << 4)

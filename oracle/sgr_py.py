@@ -72,3 +72,44 @@ def serial_greedy_py(g):
             c += 1
         colors[v] = c
     return colors, (max(colors) if colors else 0)
+
+
+def topo_sgr_py(g, rule=0):
+    """The same deterministic rounds on the topology-driven schedule of
+    Algorithm 6 (Sect. 3.1): every iteration visits every vertex, FirstFit for
+    the ones not colored yet (reading the colors final at the start of the
+    iteration), then ConflictResolve for them (judged on the iteration's
+    tentative colors), which marks the non-conflicting ones colored; the loop
+    stops when an iteration finds nothing to color.  Returns (colors list, k,
+    rounds, [vertices colored tentatively per iteration], [their degree sums]).
+    """
+    adj = _adj(g)
+    n = len(adj)
+    key = _priority_key(rule, adj)
+    color = [0] * n
+    colored = [False] * n
+    rounds, tw, td = 0, [], []
+    while True:
+        changed = False
+        final = [color[w] if colored[w] else 0 for w in range(n)]
+        open_now = [not colored[v] for v in range(n)]
+        tent = [0] * n
+        for v in range(n):
+            if open_now[v]:
+                used = {final[w] for w in adj[v]}
+                c = 1
+                while c in used:
+                    c += 1
+                tent[v] = c
+                changed = True
+        if not changed:
+            break
+        rounds += 1
+        tw.append(sum(open_now))
+        td.append(sum(len(adj[v]) for v in range(n) if open_now[v]))
+        for v in range(n):
+            if open_now[v] and not any(open_now[w] and tent[w] == tent[v] and key(w) > key(v) for w in adj[v]):
+                color[v] = tent[v]
+                colored[v] = True
+    k = max(color) if color else 0
+    return color, k, rounds, tw, td

@@ -132,10 +132,11 @@ int ensure_host_small(DevCtx *c, size_t count) {
     return SGR_OK;
 }
 
-bool valid_mode(int mode) {
+// topo: the entry point also takes SGR_MODE_TOPO (single graphs only).
+bool valid_mode(int mode, bool topo = false) {
     if (mode & ~(SGR_MODE_MASK | SGR_RULE_MASK)) return false;
     const int md = mode & SGR_MODE_MASK, rule = (mode & SGR_RULE_MASK) >> 4;
-    return (md == SGR_MODE_DETERMINISTIC || md == SGR_MODE_FAST) && rule <= 2;
+    return (md == SGR_MODE_DETERMINISTIC || md == SGR_MODE_FAST || (topo && md == SGR_MODE_TOPO)) && rule <= 2;
 }
 
 bool is_device_ptr(const void *p) {
@@ -353,9 +354,65 @@ cudaError_t launch_rounds(Params p, bool fast, bool batched, int per_sm_full, in
     return cudaSuccess;
 }
 
+// The topology-driven schedule (Algorithm 6) for a single graph: a FirstFit
+// pass and a ConflictResolve pass over all vertices per iteration, relaunched
+// by this host loop while an iteration found a vertex to color (one flag read
+// back per iteration, as in the paper's baseline).  Caller holds the device
+// mutex.
+int run_topo(DevCtx *c, const Job &j, int rule, cudaStream_t st, int32_t *k_out) {
+    static_assert(sizeof(sgr::TopoCounters) <= 4 * sizeof(int64_t), "read back through host_small");
+    int rc = ensure_host_small(c, 4);
+    if (rc != SGR_OK) return rc;
+    cudaError_t e = c->scratch.ensure(align_up(sizeof(sgr::TopoCounters)));
+    if (e != cudaSuccess) return map_cuda(e);
+    sgr::TopoCounters *tc = (sgr::TopoCounters *)c->scratch.ptr;
+    int grid = 0;
+    if (sgr::topo_grid(&grid) != 0) return SGR_ERR_CUDA;
+    unsigned *flag = (unsigned *)c->host_small;  // pinned
+    if ((e = cudaMemsetAsync(tc, 0, sizeof(*tc), st)) != cudaSuccess) return map_cuda(e);
+    if ((e = cudaMemsetAsync(j.colors, 0, (size_t)j.n * 4, st)) != cudaSuccess) return map_cuda(e);
+    if ((e = cudaEventRecord(c->ev0, st)) != cudaSuccess) return map_cuda(e);
+    long long rounds = 0;
+    for (;;) {
+        if ((e = cudaMemsetAsync(&tc->changed, 0, sizeof(unsigned), st)) != cudaSuccess) return map_cuda(e);
+        if ((e = sgr::launch_topo_iteration(j.ro, j.ci, j.colors, j.n, rule, tc, grid, st)) != cudaSuccess)
+            return map_cuda(e);
+        if ((e = cudaMemcpyAsync(flag, &tc->changed, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess)
+            return map_cuda(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);
+        if (*flag == 0) break;
+        if (++rounds > (long long)j.n + 1) return SGR_ERR_NO_CONVERGENCE;
+    }
+    if ((e = cudaEventRecord(c->ev1, st)) != cudaSuccess) return map_cuda(e);
+    sgr::TopoCounters h;
+    if ((e = cudaMemcpyAsync(c->host_small, tc, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);
+    std::memcpy(&h, c->host_small, sizeof(h));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    sgr_stats s;
+    std::memset(&s, 0, sizeof(s));
+    s.rounds = rounds;
+    s.sum_w = (int64_t)h.nw;
+    s.sum_d = (int64_t)h.dsum;
+    s.sum_next = (int64_t)h.nw - (int64_t)j.n;  // every vertex but the first-round ones came back
+    s.num_colors = h.kmax;
+    s.grid_blocks = grid;
+    s.block_threads = 256;
+    s.device_ms = ms;
+    t_stats = s;
+    c->last_trace = nullptr;  // no per-round timeline on this schedule
+    c->last_rounds = 0;
+    if (k_out) *k_out = h.kmax;
+    return SGR_OK;
+}
+
 // Run the coloring launches for a job (single graph or batch) and read back
 // the counters.  Caller holds the device mutex.
 int run_job(DevCtx *c, Job &j, int mode, cudaStream_t st, int32_t *k_out) {
+    if ((mode & SGR_MODE_MASK) == SGR_MODE_TOPO) return run_topo(c, j, (mode & SGR_RULE_MASK) >> 4, st, k_out);
     const sgr_tuning t = current_tuning();
     const bool fast = (mode & SGR_MODE_MASK) == SGR_MODE_FAST;
     const int rule = (mode & SGR_RULE_MASK) >> 4;
@@ -509,7 +566,7 @@ int sgr_release_scratch(void) {
 int sgr_color(int32_t n, const int32_t *row_offsets, const int32_t *col_idx, int32_t *colors_out,
               int32_t *num_colors, int mode, sgr_stream_t stream) {
     std::memset(&t_stats, 0, sizeof(t_stats));
-    if (n < 0 || !num_colors || !valid_mode(mode)) return SGR_ERR_INVALID_ARG;
+    if (n < 0 || !num_colors || !valid_mode(mode, true)) return SGR_ERR_INVALID_ARG;
     if (n == 0) {
         *num_colors = 0;
         return SGR_OK;
@@ -544,7 +601,7 @@ int sgr_color(int32_t n, const int32_t *row_offsets, const int32_t *col_idx, int
 int sgr_color_host(int32_t n, const int32_t *ro_h, const int32_t *ci_h, int32_t *colors_h,
                    int32_t *num_colors, int mode, sgr_stream_t stream) {
     std::memset(&t_stats, 0, sizeof(t_stats));
-    if (n < 0 || !num_colors || !valid_mode(mode)) return SGR_ERR_INVALID_ARG;
+    if (n < 0 || !num_colors || !valid_mode(mode, true)) return SGR_ERR_INVALID_ARG;
     if (n == 0) {
         *num_colors = 0;
         return SGR_OK;

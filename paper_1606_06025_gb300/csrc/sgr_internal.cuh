@@ -225,4 +225,16 @@ cudaError_t launch_validate(int32_t n, long long m, const int32_t *ro, const int
 cudaError_t launch_validate_exact(int32_t n, long long m, const int32_t *ro, const int32_t *ci,
                                   unsigned long long *flags_dev, cudaStream_t s);
 
+// The topology-driven schedule (Algorithm 6, sgr_topo.cu): per iteration, a
+// FirstFit pass and a ConflictResolve pass over all n vertices.
+struct TopoCounters {
+    unsigned changed;         // the iteration found a vertex to color (cleared by the host)
+    int kmax;                 // largest final color
+    unsigned long long nw;    // sum over iterations of the vertices colored tentatively (sum |W_r|)
+    unsigned long long dsum;  // ... and of their degrees (sum D_r)
+};
+int topo_grid(int *out);
+cudaError_t launch_topo_iteration(const int32_t *ro, const int32_t *ci, int32_t *colors, int32_t n, int rule,
+                                  TopoCounters *tc, int grid, cudaStream_t s);
+
 }  // namespace sgr

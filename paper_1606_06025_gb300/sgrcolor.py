@@ -27,11 +27,12 @@ SGR_ERR_BUSY = -8
 
 SGR_MODE_DETERMINISTIC = 0
 SGR_MODE_FAST = 1
+SGR_MODE_TOPO = 2
 SGR_RULE_LOW_KEEPS = 0 << 4
 SGR_RULE_LOW_LOSES = 1 << 4
 SGR_RULE_DEGREE = 2 << 4
 
-MODES = {"det": SGR_MODE_DETERMINISTIC, "fast": SGR_MODE_FAST}
+MODES = {"det": SGR_MODE_DETERMINISTIC, "fast": SGR_MODE_FAST, "topo": SGR_MODE_TOPO}
 RULES = {"low_keeps": SGR_RULE_LOW_KEEPS, "low_loses": SGR_RULE_LOW_LOSES,
          "degree": SGR_RULE_DEGREE}
 

@@ -67,3 +67,20 @@ def test_argument_checks_before_any_device_work():
     # n == 0 is a valid empty graph
     assert sgrcolor._lib.sgr_color(0, None, None, None, ctypes.byref(k), 0, None) == 0
     assert k.value == 0
+    # mode 3 is no mode; the topology-driven mode is taken by the single-graph
+    # entry points only (an empty graph needs no device)
+    assert sgrcolor._lib.sgr_color(1, None, None, None, ctypes.byref(k), 3, None) == -1
+    assert sgrcolor._lib.sgr_color(0, None, None, None, ctypes.byref(k), sgrcolor.SGR_MODE_TOPO, None) == 0
+    assert sgrcolor._lib.sgr_color(0, None, None, None, ctypes.byref(k),
+                                   sgrcolor.SGR_MODE_TOPO | sgrcolor.SGR_RULE_DEGREE, None) == 0
+    assert sgrcolor._lib.sgr_color(0, None, None, None, ctypes.byref(k), sgrcolor.SGR_MODE_TOPO | (3 << 4), None) == -1
+
+
+def test_header_mode_constants_match_the_binding():
+    import re
+    from paper_1606_06025_gb300 import sgrcolor
+    text = open(os.path.join(ROOT, "include", "sgrcolor.h")).read()
+    for name in ["SGR_MODE_DETERMINISTIC", "SGR_MODE_FAST", "SGR_MODE_TOPO"]:
+        m = re.search(r"#define\s+" + name + r"\s+(\d+)", text)
+        assert m and int(m.group(1)) == getattr(sgrcolor, name), name
+    assert sgrcolor._mode("topo+degree") == sgrcolor.SGR_MODE_TOPO | sgrcolor.SGR_RULE_DEGREE

@@ -207,6 +207,21 @@ def test_det_matches_python_restatement(rule):
 
 
 @pytest.mark.parametrize("rule", ["low_keeps", "low_loses", "degree"])
+def test_topology_driven_schedule_gives_the_same_rounds(rule):
+    # Algorithm 6 visits every vertex each iteration and marks the
+    # non-conflicting ones colored; under the deterministic readings it colors
+    # exactly W_r per iteration, so colors, k, rounds and the per-round sums
+    # equal the worklist loop's (reading 5: detect over V or over W is the same)
+    graphs = [random_graph(1 + s % 50, 0.1 + 0.05 * (s % 3), 300 + s) for s in range(30)]
+    graphs += [gg.uniform(800, 5.0, seed=8), gg.rmat(9, 8, seed=4), crown(5), petersen(), star(7, center=3)]
+    for g in graphs:
+        r = oracle.det_sgr(g, rule)
+        ct, kt, rt, twt, tdt = sgr_py.topo_sgr_py(g, rule)
+        assert list(r.colors) == ct and r.num_colors == kt and r.rounds == rt
+        assert list(r.trace_w) == twt and list(r.trace_d) == tdt
+
+
+@pytest.mark.parametrize("rule", ["low_keeps", "low_loses", "degree"])
 def test_det_invariants(rule):
     for seed in range(25):
         n = 1 + seed % 12
