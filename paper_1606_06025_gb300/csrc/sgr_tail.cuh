@@ -312,9 +312,9 @@ __device__ __noinline__ int tail_build(const Params &p, unsigned &gen, unsigned 
 // higher ids win): the nearest winner is the likeliest to lose again itself,
 // to stay on the worklist and settle the next round with one read, and a
 // conflict is usually within a few entries.  Otherwise the whole run is
-// scanned with the rank test.  Each unsettled vertex is first scanned by one
-// lane over eight 16-byte blocks (all in flight, so that the CTA keeps many
-// L2 loads outstanding); the few that go on past them are finished by whole
+// scanned with the rank test.  Each unsettled vertex is first scanned by a
+// group of eight lanes over its eight nearest 16-byte blocks, one block a lane,
+// all in flight at once; the few that go on past them are finished by whole
 // warps.  Keepers record their color at their W-neighbours in a separate
 // warp-parallel pass.
 
@@ -393,8 +393,8 @@ __device__ __forceinline__ bool tail_conflict(const TailSmem &s, int mode, int u
 // kTailGroupSteps steps at most; a warp scans 32 / kTailGroup vertices at a
 // time.  Vertices whose range goes on past these blocks without a conflict
 // are finished by whole warps, segment by segment (tail_scan_segment).
-constexpr int kTailGroup = 4;
-constexpr int kTailGroupSteps = 2;
+constexpr int kTailGroup = 8;
+constexpr int kTailGroupSteps = 1;
 constexpr int kTailGroupBlocks = kTailGroup * kTailGroupSteps;
 
 // First conflicting winner of one block in scan order (down: from its top
