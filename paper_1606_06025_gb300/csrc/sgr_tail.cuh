@@ -1,7 +1,7 @@
 // sgr_tail.cuh -- the last deterministic rounds in one CTA.
 //
 // Included by sgr_kernels.cu inside its anonymous namespace, after the
-// helpers it uses (row_of, load4, grid_barrier, hub_entry, warp_first_fit).
+// helpers it uses (row_of, load4, grid_barrier, warp_first_fit).
 //
 // Once few vertices are left on the worklist, a round of Algorithm 7 is a
 // short chain of dependent steps (FirstFit, ConflictResolve, commit), and the
