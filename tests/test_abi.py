@@ -84,3 +84,33 @@ def test_header_mode_constants_match_the_binding():
         m = re.search(r"#define\s+" + name + r"\s+(\d+)", text)
         assert m and int(m.group(1)) == getattr(sgrcolor, name), name
     assert sgrcolor._mode("topo+degree") == sgrcolor.SGR_MODE_TOPO | sgrcolor.SGR_RULE_DEGREE
+
+
+def test_every_params_pointer_is_set_by_both_arenas():
+    # The launch parameters are filled by two arenas: layout() for the
+    # single-graph, batch and no-allocation entry points, and the server's own.
+    # A pointer the kernels use that one of them leaves null faults the
+    # device, so every pointer field must be set by layout(), and by the server
+    # unless the server never runs the code that uses it.
+    src = open(os.path.join(ROOT, "paper_1606_06025_gb300", "csrc", "sgr_internal.cuh")).read()
+    body = src[src.index("struct Params {"):]
+    body = body[:body.index("};")]
+    fields = []
+    for line in body.splitlines():
+        m = re.match(r"\s*(?:const\s+)?[\w:]+(?:\s+[\w:]+)*\s*\*\s*(\w+)(?:\[\d+\])?;", line.split("//")[0])
+        if m:
+            fields.append(m.group(1))
+    assert len(fields) > 30
+    api = open(os.path.join(ROOT, "paper_1606_06025_gb300", "csrc", "sgr_api.cu")).read()
+    srv = open(os.path.join(ROOT, "paper_1606_06025_gb300", "csrc", "sgr_server.cu")).read()
+    # not run by the server: its launches have front_ok = 0 (no activation
+    # lists) and tail_max = 0 (no tail); uitem / uvert are optional (every
+    # write checks for null and ConflictResolve then searches the chunk bases)
+    server_unused = {"uitem", "uvert", "al", "am", "ah", "acb", "astamp", "vslot",
+                     "tlist", "tloc", "toff", "tcnt", "tlow", "tdeg", "tcp", "tcc", "tcm", "tadj", "tstage"}
+    for f in fields:
+        assert re.search(r"p->" + f + r"\b", api), f"layout() leaves Params::{f} unset"
+        if f not in server_unused:
+            assert re.search(r"\bP\." + f + r"\b", srv), f"the server leaves Params::{f} unset"
+    for f in ("front_ok", "tail_max"):
+        assert not re.search(r"\bP\." + f + r"\s*=", srv), f"the server sets {f}: recheck server_unused"
