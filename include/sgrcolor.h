@@ -46,10 +46,15 @@
  * Ownership and memory: the caller owns every input and output buffer.  The
  * library keeps a per-device scratch arena (worklists, counters, bitmaps),
  * grown on demand and never shrunk, released by sgr_release_scratch().
- * Errors: every entry point returns an sgr_status; on error, output
- * parameters other than the status are left unspecified.
- * Threads: calls on different host threads may run concurrently only on
- * different devices; calls on one device are serialised by the library.
+ * Errors: every entry point returns an sgr_status; on error, HOST output
+ * parameters (num_colors, req_id, ...) are left untouched and DEVICE output
+ * buffers hold unspecified values.
+ * Threads: calls on different host threads may run concurrently; the
+ * coloring launches of all entry points on one device (sgr_color,
+ * sgr_color_noalloc, sgr_color_host, sgr_color_batch, sgr_autotune and the
+ * servers' scheduler threads) are serialised by the library, since two
+ * cooperative persistent grids in flight on one device could each wait for
+ * CTAs the other holds.
  */
 #ifndef SGRCOLOR_H
 #define SGRCOLOR_H
@@ -158,8 +163,10 @@ int sgr_color(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
  * fixed share of the GPU and routes every allocation through its own pool, or
  * a latency-sensitive loop in which cudaMalloc / cudaFree would synchronise
  * the device and stall other streams.
- *   Arguments, layout, modes and results are those of sgr_color (device
- *   buffers owned by the caller, colors 1..k, k on the host).
+ *   Arguments, layout and results are those of sgr_color (device buffers
+ *   owned by the caller, colors 1..k, k on the host).  Modes: those of
+ *   sgr_color except SGR_MODE_TOPO, which is refused with
+ *   SGR_ERR_INVALID_ARG.
  *   Scratch: a fixed 16 MiB array inside the library's device image, held by
  *   every GPU that loads the library until the process exits (enough for
  *   graphs of about 200,000 vertices and a few million entries).  A graph
@@ -169,10 +176,12 @@ int sgr_color(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
  *   device current); make that first call before any stream capture.
  *   All calls share the array and it keeps the last call's contents; each call
  *   clears what must start at zero.  Calls whose GPU work overlaps would race
- *   on the array; within one process calls on a device are serialised and
- *   each returns after its work is complete.
+ *   on the array; within one process the calls on a device are serialised
+ *   with each other and with every other coloring entry point (see Threads
+ *   above), and each returns after its work is complete.
  *   The call makes no cudaMalloc, cudaFree or other allocating call.
- *   sgr_last_stats reports device_ms = 0 for it.
+ *   sgr_last_stats reports device_ms = 0 for it; sgr_last_trace then reads
+ *   its timeline from the array (until the next call on the device).
  */
 int sgr_color_noalloc(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
                       int32_t *colors_out, int32_t *num_colors, int mode, sgr_stream_t stream);
@@ -258,7 +267,11 @@ int sgr_server_submit(sgr_server *s, int32_t n, const int32_t *row_offsets_host,
  * SGR_PENDING if not finished yet; SGR_OK with colors_host (HOST, n int32,
  * may be NULL) and *num_colors filled, after which the id is forgotten;
  * SGR_ERR_NOT_FOUND for an unknown or already collected id; or the request's
- * error.  Thread-safe. */
+ * error, after which the id is forgotten too.  Every request ends: a graph
+ * still unfinished after n + 1 of its own rounds (only a CSR that is not
+ * symmetric gets there; the submit checks do not test symmetry) is taken off
+ * the device, its slot and memory are freed, and it fails with
+ * SGR_ERR_NO_CONVERGENCE, as sgr_color would.  Thread-safe. */
 int sgr_server_poll(sgr_server *s, uint64_t req_id, int32_t *colors_host, int32_t *num_colors,
                     int timeout_ms);
 
@@ -309,6 +322,37 @@ int sgr_last_stats(sgr_stats *out);
  * negative status.  Valid until the next call on the device.  out is HOST.
  */
 int sgr_last_trace(int64_t *out, int64_t cap_rounds, int64_t *init_ns);
+
+/*
+ * Limit of every bounded device-side wait (the grid barriers of the
+ * persistent coloring kernels), process-wide, in nanoseconds: 0 restores the
+ * default of 4 s; otherwise 100 us .. 600 s.  A wait that runs out makes
+ * every CTA of the launch leave at its next barrier, and the call returns
+ * SGR_ERR_TIMEOUT; the device stays usable.  A watchdog for callers that
+ * would rather fail fast; the paper has no counterpart.  Returns SGR_OK or
+ * SGR_ERR_INVALID_ARG.
+ */
+int sgr_set_wait_limit(int64_t ns);
+
+/*
+ * Host-side fault injection for tests of the error paths (no counterpart in
+ * the paper).  No GPU fault is ever caused: the failures are made on the host.
+ *   SGR_INJECT_NONE          disarm everything (value ignored).
+ *   SGR_INJECT_FAIL_ALLOC    the value-th next device allocation of the
+ *                            library (scratch arena, host-buffer arena,
+ *                            server budget) fails as out of memory without
+ *                            calling cudaMalloc (value >= 1; 0 disarms).
+ *   SGR_INJECT_BARRIER       the next `value` coloring calls launch their
+ *                            round kernel with a barrier count one CTA larger
+ *                            than the grid, so that its first grid barrier's
+ *                            bounded wait runs out (see sgr_set_wait_limit)
+ *                            and the call returns SGR_ERR_TIMEOUT.
+ * Returns SGR_OK or SGR_ERR_INVALID_ARG (unknown kind, value < 0).
+ */
+#define SGR_INJECT_NONE 0
+#define SGR_INJECT_FAIL_ALLOC 1
+#define SGR_INJECT_BARRIER 2
+int sgr_debug_inject(int what, int64_t value);
 
 /* Get / set the process-wide tuning used by later calls. */
 int sgr_get_tuning(sgr_tuning *out);

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -26,6 +27,12 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
+// Limit of the bounded device-side waits (0: kWaitTimeoutNs) and the host-side
+// fault injection of sgr_debug_inject.
+std::atomic<unsigned long long> g_wait_ns{0};
+std::atomic<long long> g_inject_alloc{0};  // the k-th next device allocation fails (0: none)
+std::atomic<int> g_inject_barrier{0};      // coloring launches whose barriers wait for one CTA more
+
 // A device buffer that only grows (freed by sgr_release_scratch).
 struct Arena {
     char *ptr = nullptr;
@@ -38,6 +45,7 @@ struct Arena {
             cap = 0;
             if (e != cudaSuccess) return e;
         }
+        if (sgr::inject_alloc_failure()) return cudaErrorMemoryAllocation;
         size_t want = std::max(bytes, cap + cap / 4);
         cudaError_t e = cudaMalloc(&ptr, want);
         if (e != cudaSuccess) {
@@ -119,6 +127,14 @@ int get_ctx(DevCtx **out) {
     }
     *out = c;
     return SGR_OK;
+}
+
+// The context record of a device, without the CUDA set-up get_ctx does.
+DevCtx *ctx_struct(int device) {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    if ((int)g_ctx.size() <= device) g_ctx.resize(device + 1, nullptr);
+    if (!g_ctx[device]) g_ctx[device] = new DevCtx();
+    return g_ctx[device];
 }
 
 int ensure_host_small(DevCtx *c, size_t count) {
@@ -338,7 +354,8 @@ cudaError_t launch_rounds(Params p, bool fast, bool batched, int per_sm_full, in
     if (t.blocks_per_sm > 0) per_sm = std::min(per_sm, t.blocks_per_sm);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int grid = per_sm * sms;
-    p.nblocks = (unsigned)grid;
+    p.nblocks = (unsigned)grid + sgr::inject_barrier_extra();  // > grid only under fault injection
+    p.wait_ns = sgr::wait_limit_ns();
     *grid_out = grid;
     cudaError_t e = sgr::launch_color(p, fast, batched, grid, st);
     if (e != cudaSuccess || fast) return e;
@@ -348,6 +365,9 @@ cudaError_t launch_rounds(Params p, bool fast, bool batched, int per_sm_full, in
         if (per_sm_f < 1) return cudaErrorInvalidConfiguration;
         p.nblocks = (unsigned)(per_sm_f * sms);
         if ((e = cudaMemsetAsync(&p.ctr->bar, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        // (a barrier that timed out in the first launch raised the error flag,
+        // which this reset clears: the kernel returns at once, since init did
+        // not hand the rounds over)
         if ((e = sgr::launch_color_front(p, batched, (int)p.nblocks, st)) != cudaSuccess) return e;
     }
     if (p.tail_max > 0) return sgr::launch_color_tail(p, batched, st);
@@ -464,19 +484,31 @@ namespace sgr {
 
 sgr_tuning tuning_snapshot() { return current_tuning(); }
 
+unsigned long long wait_limit_ns() {
+    const unsigned long long w = g_wait_ns.load();
+    return w ? w : kWaitTimeoutNs;
+}
+
+bool inject_alloc_failure() {
+    long long k = g_inject_alloc.load();
+    while (k > 0) {
+        if (g_inject_alloc.compare_exchange_weak(k, k - 1)) return k == 1;
+    }
+    return false;
+}
+
+unsigned inject_barrier_extra() {
+    int k = g_inject_barrier.load();
+    while (k > 0) {
+        if (g_inject_barrier.compare_exchange_weak(k, k - 1)) return 1u;
+    }
+    return 0u;
+}
+
 // Cooperative persistent launches of this process on one device are
 // serialised: two of them in flight could each wait in a grid barrier for
 // CTAs that cannot become resident.
-std::mutex &device_launch_mutex(int device) {
-    DevCtx *c = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_ctx_mu);
-        if ((int)g_ctx.size() <= device) g_ctx.resize(device + 1, nullptr);
-        if (!g_ctx[device]) g_ctx[device] = new DevCtx();
-        c = g_ctx[device];
-    }
-    return c->mu;
-}
+std::mutex &device_launch_mutex(int device) { return ctx_struct(device)->mu; }
 
 }  // namespace sgr
 
@@ -527,6 +559,30 @@ int sgr_set_tuning(const sgr_tuning *in) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune = t;
     return SGR_OK;
+}
+
+int sgr_set_wait_limit(int64_t ns) {
+    if (ns != 0 && (ns < 100000 || ns > 600000000000ll)) return SGR_ERR_INVALID_ARG;
+    g_wait_ns.store((unsigned long long)ns);
+    return SGR_OK;
+}
+
+int sgr_debug_inject(int what, int64_t value) {
+    if (value < 0 || value > (1ll << 30)) return SGR_ERR_INVALID_ARG;
+    switch (what) {
+        case SGR_INJECT_NONE:
+            g_inject_alloc.store(0);
+            g_inject_barrier.store(0);
+            return SGR_OK;
+        case SGR_INJECT_FAIL_ALLOC:
+            g_inject_alloc.store(value);
+            return SGR_OK;
+        case SGR_INJECT_BARRIER:
+            g_inject_barrier.store((int)value);
+            return SGR_OK;
+        default:
+            return SGR_ERR_INVALID_ARG;
+    }
 }
 
 int sgr_last_stats(sgr_stats *out) {
@@ -635,11 +691,13 @@ int sgr_color_host(int32_t n, const int32_t *ro_h, const int32_t *ci_h, int32_t 
     j.colors = co_d;
     j.front = true;
     j.tail = true;
-    rc = run_job(c, j, mode, st, num_colors);
+    int32_t k = 0;
+    rc = run_job(c, j, mode, st, &k);
     if (rc != SGR_OK) return rc;
     if ((e = cudaMemcpyAsync(colors_h, co_d, (size_t)n * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return map_cuda(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);
+    *num_colors = k;
     return SGR_OK;
 }
 
@@ -859,7 +917,13 @@ extern "C" int sgr_color_noalloc(int32_t n, const int32_t *row_offsets, const in
     if (!is_device_ptr(row_offsets) || !is_device_ptr(colors_out)) return SGR_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return SGR_ERR_CUDA;
+    // Lock order: the array's mutex, then the device's launch mutex, which
+    // every other coloring entry point holds around its cooperative launches
+    // (two persistent grids in flight on one device could each wait in a grid
+    // barrier for CTAs that cannot become resident).  Nothing takes them in
+    // the other order.
     std::lock_guard<std::mutex> lk(g_noalloc_mu[dev]);
+    std::lock_guard<std::mutex> dev_lk(sgr::device_launch_mutex(dev));
     if (!g_noalloc_ptr[dev]) {  // set-up, once per device, with that device current
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return SGR_ERR_CUDA;
@@ -907,6 +971,12 @@ extern "C" int sgr_color_noalloc(int32_t n, const int32_t *row_offsets, const in
         return map_cuda(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);
     fill_stats(h, 0.f, grid, h.kmax);
+    {  // sgr_last_trace now reads this call's timeline (in the fixed array)
+        DevCtx *c = ctx_struct(dev);
+        c->last_trace = p.trace;
+        c->last_rounds = h.rounds;
+        c->last_t_init = h.t_init_ns;
+    }
     if (h.err != 0) return h.err;
     *num_colors = h.kmax;
     return SGR_OK;

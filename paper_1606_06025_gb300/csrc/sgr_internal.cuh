@@ -54,7 +54,7 @@ constexpr int kMinBlocks = 3;                    // CTAs per SM the register bud
 constexpr int kLightMaxStage = 32;               // largest light degree (staged rows per lane)
 constexpr int kTraceCap = 1 << 16;               // rounds recorded in the timeline
 constexpr int kTraceFields = 4;                  // |W_r|, ns at end of phase A / phase B, rescans
-constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;  // bounded device waits
+constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;  // default limit of a bounded device wait
 constexpr int kTailThreads = 1024;               // threads of the tail CTA
 constexpr int kTailMax = 3072;                   // largest |W_r| the tail CTA takes
 constexpr int kTailDefault = 2048;               // default hand-over size
@@ -176,6 +176,7 @@ struct Params {
     int chunk;                 // hub chunk edges; medium degree bound
     int rule;                  // 0 low keeps, 1 low loses, 2 degree
     long long max_rounds;
+    unsigned long long wait_ns;  // limit of every bounded device-side wait (grid barriers)
     unsigned int nblocks;
     int resume;                // 1: skip init and continue from Counters::round
     int resume_sorted;         // resume: every resident graph has ascending rows
@@ -201,6 +202,12 @@ inline ScratchPlan plan_scratch(long long n, long long m, int chunk) {
 // Host-side shared state (implemented in sgr_api.cu).
 sgr_tuning tuning_snapshot();
 std::mutex &device_launch_mutex(int device);
+unsigned long long wait_limit_ns();  // sgr_set_wait_limit, or kWaitTimeoutNs
+// Host-side fault injection (sgr_debug_inject): true when this device
+// allocation must fail as out of memory; the extra CTAs the next coloring
+// launch's grid barriers wait for (0 normally; consumed by the call).
+bool inject_alloc_failure();
+unsigned inject_barrier_extra();
 
 // Launches (implemented in sgr_kernels.cu).
 int occupancy_blocks_per_sm(bool fast, bool batched, int *out);
@@ -214,6 +221,8 @@ cudaError_t launch_color_front(const Params &p, bool batched, int grid, cudaStre
 cudaError_t launch_color_tail(const Params &p, bool batched, cudaStream_t s);
 cudaError_t launch_admit(const Params &p, int g, long long vb, int32_t n, int par, int grid,
                          cudaStream_t s);
+// Server: take graph [lo, hi)'s vertices off the worklists of parity par.
+cudaError_t launch_purge(const Params &p, long long lo, long long hi, int par, cudaStream_t s);
 cudaError_t launch_slot_status(const int32_t *colors, const long long *vbase, const int32_t *nv,
                                int G, int32_t *rem, int32_t *kmax, cudaStream_t s);
 cudaError_t launch_fill_gid(int32_t *gid, const long long *vbase_dev, int G, int32_t n,

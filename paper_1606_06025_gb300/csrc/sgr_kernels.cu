@@ -134,7 +134,7 @@ __device__ bool grid_barrier(const Params &p, unsigned &gen) {
                 seen = ld_acquire64(&p.ctr->bar);
                 if ((seen & ~kBarErr) >= target || (seen & kBarErr)) break;
                 __nanosleep(32);
-                if (globaltimer() - t0 > kWaitTimeoutNs) {
+                if (globaltimer() - t0 > p.wait_ns) {
                     raise_error(p, kErrTimeout);
                     seen |= kBarErr;
                     break;
@@ -2342,6 +2342,103 @@ __global__ void __launch_bounds__(kBlock) admit_kernel(const Params p, int g, lo
     if ((threadIdx.x & 31) == 0 && dsum) atomicAdd(&p.ctr->dcur, dsum);
 }
 
+// Exclusive scan of one value per thread over the whole CTA (blockDim.x a
+// multiple of 32, at most 1024); *total receives the sum.  Begins and ends
+// with a __syncthreads().
+__device__ unsigned cta_excl_scan(unsigned x, unsigned *total) {
+    __shared__ unsigned s_w[32], s_tot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    __syncthreads();
+    unsigned incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned v = lane < nw ? s_w[lane] : 0u;
+        unsigned vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(kFull, vi, o);
+            if (lane >= o) vi += t;
+        }
+        if (lane < nw) s_w[lane] = vi - v;
+        if (lane == 31) s_tot = vi;
+    }
+    __syncthreads();
+    *total = s_tot;
+    return s_w[warp] + incl - x;
+}
+
+// Server: take the vertices of one resident graph (global ids [lo, hi)) off
+// the worklists of parity `par` (the next round's W_in), in place and in
+// order, with their degrees off the worklist's degree sum.  One CTA; runs
+// between two resumable launches, when the graph is retired before it
+// finished (its round cap passed).  Writes land at or below every entry still
+// to be read (kept entries only move down), and each tile's reads precede its
+// writes (the scans' barriers).
+__global__ void __launch_bounds__(1024) purge_kernel(const Params p, long long lo, long long hi, int par) {
+    unsigned long long dsum = 0;
+    for (int which = 0; which < 2; ++which) {  // light, then medium list
+        int32_t *list = which ? p.mw[par] : p.lw[par];
+        unsigned *cnt = which ? &p.ctr->nm[par] : &p.ctr->nl[par];
+        const unsigned n = *cnt;
+        unsigned put = 0;
+        for (unsigned base = 0; base < n; base += blockDim.x) {
+            const unsigned i = base + threadIdx.x;
+            int32_t v = 0;
+            bool keep = false;
+            if (i < n) {
+                v = list[i];
+                keep = v < lo || v >= hi;
+                if (!keep) dsum += (unsigned long long)vertex_degree<true>(p, v);
+            }
+            unsigned tot;
+            const unsigned pos = cta_excl_scan(keep ? 1u : 0u, &tot);
+            if (keep) list[put + pos] = v;
+            put += tot;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *cnt = put;
+    }
+    {  // hub list: entries (slot, chunk base); kept entries get new chunk bases
+        const unsigned long long h = p.ctr->h64[par];
+        const unsigned n = (unsigned)(h >> 32), nch = (unsigned)h;
+        int32_t *slots = p.hw[par];
+        unsigned *cbs = p.hcb[par];
+        unsigned put = 0, cput = 0;
+        for (unsigned base = 0; base < n; base += blockDim.x) {
+            const unsigned i = base + threadIdx.x;
+            int32_t slot = 0;
+            unsigned nc = 0;
+            bool keep = false;
+            if (i < n) {
+                slot = slots[i];
+                nc = (i + 1 < n ? cbs[i + 1] : nch) - cbs[i];
+                const int32_t v = p.hvert[slot];
+                keep = v < lo || v >= hi;
+                if (!keep) dsum += (unsigned long long)vertex_degree<true>(p, v);
+            }
+            unsigned tot, ctot;
+            const unsigned pos = cta_excl_scan(keep ? 1u : 0u, &tot);
+            const unsigned cpos = cta_excl_scan(keep ? nc : 0u, &ctot);
+            if (keep) {
+                slots[put + pos] = slot;
+                cbs[put + pos] = cput + cpos;
+            }
+            put += tot;
+            cput += ctot;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) p.ctr->h64[par] = ((unsigned long long)put << 32) | cput;
+    }
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+    if ((threadIdx.x & 31) == 0 && dsum) atomicAdd(&p.ctr->dcur, 0ull - dsum);
+}
+
 // Per resident graph slot: vertices not yet final and the largest color.
 __global__ void slot_status_kernel(const int32_t *colors, const long long *vbase,
                                    const int32_t *nv, int G, int32_t *rem, int32_t *kmax) {
@@ -2490,6 +2587,11 @@ cudaError_t launch_admit(const Params &p, int g, long long vb, int32_t n, int pa
                          cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     admit_kernel<<<grid, kBlock, 0, s>>>(p, g, vb, n, par);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_purge(const Params &p, long long lo, long long hi, int par, cudaStream_t s) {
+    purge_kernel<<<1, 1024, 0, s>>>(p, lo, hi, par);
     return cudaGetLastError();
 }
 

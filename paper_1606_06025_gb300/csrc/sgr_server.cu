@@ -103,6 +103,7 @@ struct Request {
     int32_t k = 0;
     int slot = -1;
     long long vb = 0, eb = 0, rb = 0;
+    long long r_admit = 0;  // server round at which the graph's round 1 runs
 };
 
 }  // namespace
@@ -212,6 +213,7 @@ int carve(sgr_server *S) {
     take((void **)&ro, (size_t)S->Rcap * 4);
     take((void **)&ci, (size_t)Ecap * 4 + 64);
     for (auto &pr : parts) off += align_up(pr.second);
+    if (sgr::inject_alloc_failure()) return SGR_ERR_OUT_OF_MEMORY;
     cudaError_t e = cudaMalloc(&S->dmem, off);
     if (e != cudaSuccess) {
         S->dmem = nullptr;
@@ -245,7 +247,7 @@ int carve(sgr_server *S) {
     P.light_max = t.light_max;
     P.chunk = t.chunk;
     P.rule = (S->cfg.mode & SGR_RULE_MASK) >> 4;
-    P.max_rounds = LLONG_MAX / 4;
+    P.max_rounds = LLONG_MAX / 4;  // per-graph caps are kept by the scheduler
     P.resume = 1;
     P.resume_sorted = 1;
     S->va.init(Vcap);
@@ -334,6 +336,7 @@ void worker_loop(sgr_server *S) {
                 if (rb < 0) { S->va.release(vb, q->n); S->ea.release(eb, q->m); ++it; continue; }
                 q->slot = S->free_slots.back();
                 S->free_slots.pop_back();
+                q->r_admit = S->round;
                 q->vb = vb;
                 q->eb = eb;
                 q->rb = rb;
@@ -380,6 +383,7 @@ void worker_loop(sgr_server *S) {
         sgr::Params P = S->P;
         P.rounds_per_launch = R;
         P.nblocks = (unsigned)S->grid;
+        P.wait_ns = sgr::wait_limit_ns();
         // fresh barrier and error state for this launch
         if (e == cudaSuccess) e = cudaMemsetAsync(&P.ctr->bar, 0, sizeof(unsigned long long), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(&P.ctr->err, 0, sizeof(int), st);
@@ -414,9 +418,42 @@ void worker_loop(sgr_server *S) {
         S->round = h.round;
         // Retire finished graphs, unless a hub's color still waits to be
         // scattered into neighbour bitmaps (its range must not be reused yet).
-        // A resident graph always finishes: in every round the worklist vertex
-        // that wins against all its neighbours under the rule keeps its color.
+        // A graph with a symmetric CSR finishes within n of its rounds: in
+        // every round the worklist vertex that wins against all its
+        // neighbours under the rule keeps its color.  One that is still
+        // unfinished after n + 1 of its rounds (a non-symmetric CSR, which
+        // the submit checks do not catch) is taken off the worklists and
+        // fails with SGR_ERR_NO_CONVERGENCE, as sgr_color would.
         if (h.sc64 != 0) continue;
+        std::vector<Request *> stuck;
+        for (int g = 0; g < G; ++g) {
+            Request *q = S->slot_req[g];
+            if (q && S->rem_h[g] != 0 && S->round - q->r_admit > (long long)q->n) stuck.push_back(q);
+        }
+        for (Request *q : stuck) {
+            S->nv_h[q->slot] = 0;
+            if (e == cudaSuccess) e = sgr::launch_purge(P, q->vb, q->vb + q->n, (int)(S->round & 1), st);
+        }
+        if (!stuck.empty()) {
+            if (e == cudaSuccess) e = cudaMemcpyAsync(S->nv_d, S->nv_h, (size_t)G * 4, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                const int status = map_err(e);
+                {
+                    std::lock_guard<std::mutex> lk(S->mu);
+                    S->fatal = status;
+                }
+                fail_all_resident(S, status);
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->stop = true;
+                break;
+            }
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (Request *q : stuck) {
+                release_slot(S, q);
+                finish(S, q, SGR_ERR_NO_CONVERGENCE);
+            }
+        }
         std::vector<Request *> retiring;
         for (int g = 0; g < G; ++g) {
             Request *q = S->slot_req[g];

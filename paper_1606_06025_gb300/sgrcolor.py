@@ -40,7 +40,8 @@ RULES = {"low_keeps": SGR_RULE_LOW_KEEPS, "low_loses": SGR_RULE_LOW_LOSES,
 EXPORTS = ["sgr_color", "sgr_color_noalloc", "sgr_color_host", "sgr_autotune", "sgr_color_batch", "sgr_validate_csr",
            "sgr_last_stats", "sgr_last_trace", "sgr_get_tuning", "sgr_set_tuning", "sgr_release_scratch",
            "sgr_status_string", "sgr_version", "sgr_server_create", "sgr_server_submit",
-           "sgr_server_poll", "sgr_server_stats", "sgr_server_destroy"]
+           "sgr_server_poll", "sgr_server_stats", "sgr_server_destroy", "sgr_set_wait_limit",
+           "sgr_debug_inject"]
 
 
 class SgrError(RuntimeError):
@@ -112,6 +113,8 @@ def _load():
     lib.sgr_server_poll.argtypes = [vp, ctypes.c_uint64, vp, pi32, ctypes.c_int]
     lib.sgr_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     lib.sgr_server_destroy.argtypes = [vp]
+    lib.sgr_set_wait_limit.argtypes = [i64]
+    lib.sgr_debug_inject.argtypes = [ctypes.c_int, i64]
     for name in EXPORTS:
         if name != "sgr_status_string":
             getattr(lib, name).restype = ctypes.c_int
@@ -258,6 +261,21 @@ def sgr_set_tuning(light_max=0, chunk=0, blocks_per_sm=0, active_lists=0, tail_v
 
 def sgr_release_scratch() -> None:
     _check(_lib.sgr_release_scratch(), "sgr_release_scratch")
+
+
+def sgr_set_wait_limit(ns: int) -> None:
+    """Limit of every bounded device-side wait in ns (0: the 4 s default)."""
+    _check(_lib.sgr_set_wait_limit(int(ns)), "sgr_set_wait_limit")
+
+
+SGR_INJECT_NONE = 0
+SGR_INJECT_FAIL_ALLOC = 1
+SGR_INJECT_BARRIER = 2
+
+
+def sgr_debug_inject(what: int, value: int = 0) -> None:
+    """Host-side fault injection for tests (see sgrcolor.h)."""
+    _check(_lib.sgr_debug_inject(int(what), int(value)), "sgr_debug_inject")
 
 
 def sgr_version() -> int:

@@ -114,3 +114,32 @@ def test_every_params_pointer_is_set_by_both_arenas():
             assert re.search(r"\bP\." + f + r"\b", srv), f"the server leaves Params::{f} unset"
     for f in ("front_ok", "tail_max"):
         assert not re.search(r"\bP\." + f + r"\s*=", srv), f"the server sets {f}: recheck server_unused"
+
+
+def test_wait_limit_and_injection_arguments_without_gpu():
+    from paper_1606_06025_gb300 import sgrcolor
+    lib = sgrcolor._lib
+    assert lib.sgr_set_wait_limit(0) == 0
+    assert lib.sgr_set_wait_limit(1_000_000) == 0
+    assert lib.sgr_set_wait_limit(99_999) == sgrcolor.SGR_ERR_INVALID_ARG  # under 100 us
+    assert lib.sgr_set_wait_limit(-5) == sgrcolor.SGR_ERR_INVALID_ARG
+    assert lib.sgr_set_wait_limit(0) == 0
+    assert lib.sgr_debug_inject(99, 1) == sgrcolor.SGR_ERR_INVALID_ARG
+    assert lib.sgr_debug_inject(sgrcolor.SGR_INJECT_FAIL_ALLOC, -1) == sgrcolor.SGR_ERR_INVALID_ARG
+    assert lib.sgr_debug_inject(sgrcolor.SGR_INJECT_BARRIER, 2) == 0
+    assert lib.sgr_debug_inject(sgrcolor.SGR_INJECT_NONE, 0) == 0
+    for name in ("SGR_INJECT_NONE", "SGR_INJECT_FAIL_ALLOC", "SGR_INJECT_BARRIER"):
+        m = re.search(r"#define\s+" + name + r"\s+(\d+)", open(HEADER).read())
+        assert m and int(m.group(1)) == getattr(sgrcolor, name), name
+
+
+def test_noalloc_refuses_topo_mode_before_any_device_work():
+    import ctypes
+    from paper_1606_06025_gb300 import sgrcolor
+    k = ctypes.c_int32(-7)
+    buf = (ctypes.c_int32 * 8)()
+    rc = sgrcolor._lib.sgr_color_noalloc(2, ctypes.addressof(buf), ctypes.addressof(buf), ctypes.addressof(buf),
+                                         ctypes.byref(k), sgrcolor.SGR_MODE_TOPO, None)
+    assert rc == sgrcolor.SGR_ERR_INVALID_ARG and k.value == -7
+    # the single-graph entry takes the same mode (an empty graph needs no device)
+    assert sgrcolor._lib.sgr_color(0, None, None, None, ctypes.byref(k), sgrcolor.SGR_MODE_TOPO, None) == 0

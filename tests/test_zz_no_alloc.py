@@ -68,3 +68,68 @@ def test_noalloc_refuses_graphs_beyond_its_scratch(gpu_lib):
     ro, ci = _dev(h)
     rc, got, k = _call(gpu_lib, "sgr_color_noalloc", h, ro, ci, "det")
     assert rc == 0 and np.array_equal(got, oracle.det_sgr(h).colors)
+
+
+def test_noalloc_allocates_no_device_memory(gpu_lib):
+    """The entry point's defining property: with the library's own scratch
+    released, repeated calls leave the device's free memory unchanged (the
+    fixed array is part of the loaded image, counted before the first call's
+    measurement)."""
+    import torch
+    g = gg.rmat(14, 16, seed=4)
+    ro, ci = _dev(g)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    ref = oracle.det_sgr(g)
+    gpu_lib.sgr_release_scratch()
+    k = gpu_lib.sgr_color_noalloc(g.n, ro, ci, out, "det")  # first call: looks up the array
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        k = gpu_lib.sgr_color_noalloc(g.n, ro, ci, out, "det")
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert gpu_lib.sgr_last_stats()["device_ms"] == 0.0
+    assert k == ref.num_colors and np.array_equal(out.cpu().numpy(), ref.colors)
+    # the timeline of the last call is that of this call
+    tl = gpu_lib.sgr_last_trace()
+    assert len(tl["w"]) == gpu_lib.sgr_last_stats()["rounds"] > 0
+
+
+def test_noalloc_refuses_the_topology_driven_mode(gpu_lib):
+    g = gg.uniform(500, 6.0, seed=2)
+    ro, ci = _dev(g)
+    rc, _, _ = _call(gpu_lib, "sgr_color_noalloc", g, ro, ci, "topo")
+    assert rc == gpu_lib.SGR_ERR_INVALID_ARG
+
+
+def test_noalloc_and_sgr_color_concurrently_on_one_device(gpu_lib):
+    """Two host threads color at the same time, one through sgr_color and one
+    through sgr_color_noalloc, each on its own stream.  The library serialises
+    their cooperative launches on the device; both results equal the oracle."""
+    import threading
+
+    import torch
+    ga, gb = gg.rmat(15, 16, seed=8), gg.uniform(30000, 12.0, seed=9)
+    ra, rb = oracle.det_sgr(ga), oracle.det_sgr(gb)
+    da, db = _dev(ga), _dev(gb)
+    errors = []
+
+    def worker(fn, g, d, ref):
+        try:
+            s = torch.cuda.Stream()
+            out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+            for _ in range(6):
+                k = fn(g.n, d[0], d[1], out, "det", s)
+                s.synchronize()
+                if k != ref.num_colors or not np.array_equal(out.cpu().numpy(), ref.colors):
+                    errors.append(fn.__name__)
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    ta = threading.Thread(target=worker, args=(gpu_lib.sgr_color, ga, da, ra))
+    tb = threading.Thread(target=worker, args=(gpu_lib.sgr_color_noalloc, gb, db, rb))
+    ta.start()
+    tb.start()
+    ta.join()
+    tb.join()
+    assert not errors, errors
