@@ -232,6 +232,7 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     // item -> hub entry map of the unsettled hubs' lower-part work items
     const size_t uitems = j.fast ? 1 : (size_t)(j.m / t.chunk) + sp.hub_max + 1;
     unsigned *ui0 = (unsigned *)take(uitems * 4), *ui1 = (unsigned *)take(uitems * 4);
+    unsigned *ur0 = (unsigned *)take(uitems * 32), *ur1 = (unsigned *)take(uitems * 32);
     int32_t *uv0 = (int32_t *)take(uhub * 4), *uv1 = (int32_t *)take(uhub * 4);
     unsigned *ucb0 = (unsigned *)take(uhub * 4), *ucb1 = (unsigned *)take(uhub * 4);
     const size_t an = front ? (size_t)j.n : 1, ahub = front ? sp.hub_max : 1;
@@ -275,6 +276,7 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         if (!j.fast) {
             p->uitem[0] = ui0; p->uitem[1] = ui1;
             p->uvert[0] = uv0; p->uvert[1] = uv1;
+            p->urec[0] = ur0; p->urec[1] = ur1;
         }
         p->ucb[0] = ucb0; p->ucb[1] = ucb1;
         p->al[0] = al0; p->al[1] = al1;

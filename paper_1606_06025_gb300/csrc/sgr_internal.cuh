@@ -136,6 +136,8 @@ struct Params {
     int32_t *uh[2];            // det: hub slots the witness did not settle
     unsigned *uitem[2];        // det (optional): ConflictResolve work item -> entry of uh (lower-part items)
     int32_t *uvert[2];         // det (optional): entry of uh -> vertex
+    unsigned *urec[2];         // det (optional): per lower-part work item of uh, a 32-byte record
+                               //   {v, slot, tentative color, vb | start (64-bit), length, items}
     unsigned int *ucb[2];      // det: their chunk bases
     int32_t *hvert;
     unsigned int *hbase;

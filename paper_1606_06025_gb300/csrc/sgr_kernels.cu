@@ -73,6 +73,14 @@ __device__ __forceinline__ unsigned long long atom_add_release64(unsigned long l
     return old;
 }
 
+__device__ __forceinline__ unsigned long long atom_add_acq_rel64(unsigned long long *p,
+                                                                 unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;"
+                 : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -706,17 +714,29 @@ __device__ void det_assign_medium(const Params &p, int par, unsigned cnt, Acc &a
 }
 
 // Hub list: one lane per entry (entries are slots; chunk counts come from
-// the chunk bases).
+// the chunk bases).  With ascending rows and lower ids keeping, an unsettled
+// hub's ConflictResolve reads only the entries below it, one work item per
+// chunk of them, nearest chunk first; when the launch has room for them
+// (p.urec), each item gets a 32-byte record {v, slot, c, vb | start, length,
+// items of the hub}, so that ConflictResolve starts scanning after one load.
 template <bool kBatched>
 __device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64, bool prefix, Acc &acc) {
     const int pn = par ^ 1;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const unsigned NW = total_warps();
+    const bool records = prefix && p.urec[par] != nullptr;
     for (unsigned base = global_warp() * 32; base < cnt; base += NW * 32) {
         const unsigned idx = base + (threadIdx.x & 31);
         bool act[1] = {idx < cnt}, settled[1];
         int32_t slot = act[0] ? __ldcg(p.hw[par] + idx) : 0;
         int32_t v[1] = {act[0] ? __ldcg(p.hvert + slot) : 0};
+        long long rs = 0, re = 0;
+        int32_t vb = 0;
+        int ld = 0;
+        if (act[0] && prefix) {  // issued before the bitmap chain
+            row_of<kBatched>(p, v[0], rs, re, vb);
+            ld = __ldcg(p.lowdeg + v[0]);
+        }
         int c[1];
         det_assign_lane<kBatched, 1>(p, act, v, c, settled);
         if (act[0]) {
@@ -726,17 +746,23 @@ __device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64
                 hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
                 acc.next += 1;
             } else {
-                // with ascending rows and lower ids keeping, ConflictResolve
-                // only reads the entries below the hub: one item per chunk of them
-                const unsigned nu = prefix ? lower_chunks(__ldcg(p.lowdeg + v[0]), p.chunk) : nchunks;
+                const unsigned nu = prefix ? lower_chunks(ld, p.chunk) : nchunks;
                 const unsigned long long old =
                     atomicAdd(&p.ctr->uh64[par], (1ull << 32) | (unsigned long long)nu);
                 const unsigned k = (unsigned)(old >> 32), cbu = (unsigned)old;
                 p.uh[par][k] = slot;
                 p.ucb[par][k] = cbu;
-                if (prefix && p.uitem[par]) {  // ConflictResolve finds its hub without a search
-                    p.uvert[par][k] = v[0];
-                    for (unsigned t = 0; t < nu; ++t) p.uitem[par][cbu + t] = k;
+                if (records) {
+                    const long long split = rs + ld;
+                    uint4 *rec = reinterpret_cast<uint4 *>(p.urec[par]) + 2 * (size_t)cbu;
+                    for (unsigned t = 0; t < nu; ++t) {  // item t: the t-th chunk below the split
+                        const long long hi = split - (long long)t * p.chunk;
+                        const long long lo = max(rs, hi - (long long)p.chunk);
+                        __stcg(rec + 2 * t, make_uint4((unsigned)v[0], (unsigned)slot, (unsigned)c[0], (unsigned)vb));
+                        __stcg(rec + 2 * t + 1, make_uint4((unsigned)(unsigned long long)lo,
+                                                           (unsigned)((unsigned long long)lo >> 32),
+                                                           (unsigned)max(0ll, hi - lo), nu));
+                    }
                 }
             }
         }
@@ -1312,6 +1338,45 @@ __device__ __forceinline__ int32_t det_scan_warp(const Params &p, int32_t v, int
     return -1;
 }
 
+// Warp scan of entries [a, hi) of an ascending row, all below the vertex,
+// from the top down (128 entries a step); returns the nearest neighbour
+// holding magnitude c, or -1.  The stop flag is read with each step's loads
+// and ends the scan after that step.
+__device__ __forceinline__ int32_t scan_range_down_warp(const Params &p, int c, long long a, long long hi,
+                                                        int32_t vb, const unsigned *stop,
+                                                        unsigned long long &scanned) {
+    const int lane = threadIdx.x & 31;
+    for (long long top = (hi - 1) >> 2; hi > a && top >= (a >> 2); top -= 32) {
+        const long long q = top - lane;
+        const bool in = q >= (a >> 2);
+        const int4 x = in ? load4(p.ci, q, p.m) : make_int4(0, 0, 0, 0);
+        const unsigned halt = __ldcg(stop);
+        int32_t my = -1;
+        if (in) {
+            const long long i0 = q << 2;
+            int cw[4];
+            bool ok[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long i = i0 + k;
+                const int32_t w = vb + elem(x, k);
+                ok[k] = i >= a && i < hi && (unsigned)w < (unsigned)p.n;
+                cw[k] = ok[k] ? __ldcg(p.colors + w) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!ok[k]) continue;
+                scanned++;
+                if (mag(cw[k]) == c) my = vb + elem(x, k);
+            }
+        }
+        const unsigned bal = __ballot_sync(kFull, my >= 0);
+        if (bal) return __shfl_sync(kFull, my, __ffs(bal) - 1);
+        if (halt) return -1;
+    }
+    return -1;
+}
+
 // Lane scan of the (at most) 16 entries of [s, hi) nearest below hi, all
 // loads in flight (ascending row, lower ids win): the nearest one holding
 // magnitude c, or -1; *rest = the part still unscanned ([s, *rest)).
@@ -1434,13 +1499,60 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
 // and the vertex of each entry, written when the list was built.
 template <bool kBatched>
 __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsigned *cbs,
-                               const unsigned *items, const int32_t *verts,
+                               const unsigned *items, const int32_t *verts, const unsigned *recs,
                                unsigned long long h64, int pn, bool prefix, bool push_losers,
                                bool lower_only, bool round1, Acc &acc) {
     const int lane = threadIdx.x & 31;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const long long CH = p.chunk;
     const unsigned NW = total_warps();
+    if (recs) {  // lower-part items with records: one load, then the scan
+        for (unsigned q = global_warp(); q < nch; q += NW) {
+            const uint4 *rp = reinterpret_cast<const uint4 *>(recs) + 2 * (size_t)q;
+            const uint4 r0 = __ldcg(rp), r1 = __ldcg(rp + 1);
+            const int32_t v = (int32_t)r0.x, slot = (int32_t)r0.y, vb = (int32_t)r0.w;
+            const int c = (int)r0.z;
+            const long long a = (long long)(((unsigned long long)r1.y << 32) | r1.x);
+            const unsigned nchunks = r1.w;
+            const int32_t found = scan_range_down_warp(p, c, a, a + (long long)r1.z, vb, p.hconf + slot, acc.dscan);
+            const bool conf = found >= 0;
+            if (lane == 0) {
+                if (conf) {
+                    __stcg(p.witness + v, found);
+                    atomicOr(p.hconf + slot, 1u);  // stops the hub's other items early
+                }
+                // the decision travels in the completion counter (conflicts in
+                // the high word); release orders this item's writes before its
+                // count, acquire orders the last item's resets after all counts
+                const unsigned long long old =
+                    atom_add_acq_rel64(p.hdone + slot, conf ? (1ull << 32) + 1ull : 1ull);
+                if ((unsigned)old == nchunks - 1) {
+                    const bool lost = conf || (old >> 32) != 0;
+                    __stcg(p.hconf + slot, 0u);
+                    __stcg(p.hdone + slot, 0ull);
+                    long long s, e;
+                    int32_t vb2;
+                    row_of<kBatched>(p, v, s, e, vb2);
+                    const long long deg = e - s;
+                    if (lost) {
+                        if (push_losers)
+                            hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot,
+                                          (unsigned)((deg + CH - 1) / CH));
+                        acc.next += 1;
+                    } else {
+                        __stcg(p.colors + v, c);
+                        acc.kmax = max(acc.kmax, c);
+                        acc.keep++;
+                        acc.kdeg += (unsigned long long)deg;
+                        acc.scatter += (unsigned long long)deg;
+                        hub_list_push(&p.ctr->sc64, p.sw, p.scb, slot,
+                                      (unsigned)((deg + kScatterChunk - 1) / kScatterChunk));
+                    }
+                }
+            }
+        }
+        return;
+    }
     for (unsigned q = global_warp(); q < nch; q += NW) {
         const bool direct = items != nullptr;
         const unsigned i = direct ? __ldcg(items + q) : hub_entry(cbs, cnt, q);
@@ -2228,7 +2340,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             det_hub_detect<kBatched>(p, shortcut ? p.hw[par] : p.uh[par],
                                      shortcut ? p.hcb[par] : p.ucb[par],
                                      lower_only ? p.uitem[par] : nullptr,
-                                     lower_only ? p.uvert[par] : nullptr, bh, pn, prefix, !kFront,
+                                     lower_only ? p.uvert[par] : nullptr,
+                                     lower_only ? p.urec[par] : nullptr, bh, pn, prefix, !kFront,
                                      lower_only, shortcut, b);
             det_medium_detect<kBatched>(p, shortcut ? p.mw[par] : p.um[par], bnm,
                                         kFront ? nullptr : p.mw[pn], &ctr->nm[pn], prefix, shortcut,

@@ -104,9 +104,9 @@ def test_every_params_pointer_is_set_by_both_arenas():
     api = open(os.path.join(ROOT, "paper_1606_06025_gb300", "csrc", "sgr_api.cu")).read()
     srv = open(os.path.join(ROOT, "paper_1606_06025_gb300", "csrc", "sgr_server.cu")).read()
     # not run by the server: its launches have front_ok = 0 (no activation
-    # lists) and tail_max = 0 (no tail); uitem / uvert are optional (every
+    # lists) and tail_max = 0 (no tail); uitem / uvert / urec are optional (every
     # write checks for null and ConflictResolve then searches the chunk bases)
-    server_unused = {"uitem", "uvert", "al", "am", "ah", "acb", "astamp", "vslot",
+    server_unused = {"uitem", "uvert", "urec", "al", "am", "ah", "acb", "astamp", "vslot",
                      "tlist", "tloc", "toff", "tcnt", "tlow", "tdeg", "tcp", "tcc", "tcm", "tadj", "tstage"}
     for f in fields:
         assert re.search(r"p->" + f + r"\b", api), f"layout() leaves Params::{f} unset"
