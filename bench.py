@@ -16,6 +16,16 @@ on the stream the library launches on; the L2 cache is flushed (a 512 MiB
 write) before every step, outside the events.  SM clocks and throttle reasons
 are sampled with nvidia-smi during the timed steps.
 
+The default run (rmat20, one GPU) also measures the other configurations and
+puts them in the same JSON line under "configs": the 192^3 stencil and the
+20k uniform graph, the 512-graph batch (graphs/s against one sgr_color call
+per graph), the same 512 graphs submitted at once to the server, and an open
+Poisson stream of served requests (1k-4M vertices, 64 GB budget) at 0.7 x the
+server's burst capacity and at the sequential path's capacity.  Every
+deterministic result is checked against the oracle (its colors, or digests
+the oracle wrote into tests/golden).  roofline.frac is section 8(d)'s model:
+the bytes Algorithms 4/5 as printed would move, over the device time.
+
 --impl reference times the CPU oracle (the only reference this method has:
 the paper publishes no code) on the host cores, on the same workload, metric
 and unit.
@@ -302,6 +312,154 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def golden(name):
+    """Oracle-written expected values (tests/golden, written by scripts that
+    call only oracle/ and graphgen/)."""
+    path = os.path.join(ROOT, "tests", "golden", name)
+    with open(path) as f:
+        return json.load(f)
+
+
+def digest(a) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
+
+
+GOLDEN_SINGLE = {"rmat20": "rmat20", "stencil192": "stencil27_192", "er20k": "er20k"}
+
+
+def roofline_record(st, n, m, mode, kmean, workload, rule):
+    """Section 8(d)'s roofline: the bytes of the printed Algorithms 4/5 per
+    call (20 B per worklist vertex and round, 8 B per FirstFit edge visit, 4 B
+    per pushed loser, from the device's own counts) over the call's device
+    time, against the measured copy bandwidth.  The implementation's own byte
+    model is kept beside it as frac_impl."""
+    peak, peak_src = read_peaks()
+    pb = paper_bytes(st)
+    ab = alg_bytes(st, n, m, mode)
+    achieved = pb / (kmean * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": read_traffic(workload, mode) if rule == "low_keeps" else None,
+            "model": "paper: 20*sum|W_r| + 8*sum D_r + 4*sum L_r bytes per call (Algorithms 4/5 as printed)",
+            "bytes_per_launch": pb, "kernel_ms": kmean,
+            "frac_impl": ab / (kmean * 1e-3) / 1e9 / peak,
+            "impl_model": {"bytes_per_launch": ab, "achieved_gbs": ab / (kmean * 1e-3) / 1e9,
+                           "what": "bytes this implementation moves by its own model (bitmaps, "
+                                   "witnesses, tail CTA; see alg_bytes)"},
+            "kernel": ("the coloring launches of one call, timed together on their stream: "
+                       "sgr_color_kernel (init, rounds on the grid), its activation-list variant, "
+                       "sgr_tail_kernel (last rounds in one CTA)") if mode != "topo" else
+                      ("the topology-driven iterations of one call (topo_assign_kernel and "
+                       "topo_resolve_kernel per iteration, host loop on a flag), event to event"),
+            "peak_source": peak_src + " of measured" if peak_src.startswith("measured") else peak_src}
+
+
+def measure_single(lib, dev, stream, name, g, args, steps, warmup, flush, world=1, e2e=True,
+                   cpu="det", check=True):
+    """One workload graph on the device: K timed steps (L2 flushed before each),
+    the section 8(d) roofline, end to end through the host-buffer entry, the
+    CPU oracle beside it, and bit-exactness against the oracle."""
+    import torch
+    n, m = g.n, g.m
+    ro = torch.from_numpy(g.row_offsets).to(dev)
+    ci = torch.from_numpy(g.col_idx).to(dev)
+    colors = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    mode = args.mode + "+" + args.rule
+    for _ in range(max(warmup, 0)):
+        flush.fill_(1)
+        lib.sgr_color(n, ro, ci, colors, mode, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    step_ms, kern_ms, stats = [], [], []
+    k = 0
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        k = lib.sgr_color(n, ro, ci, colors, mode, stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = lib.sgr_last_stats()
+        stats.append(st)
+        kern_ms.append(st["device_ms"])
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    if world > 1:
+        torch.distributed.barrier()
+    st = stats[-1]
+    timeline = lib.sgr_last_trace() if args.timeline else None
+    got = colors[:n].cpu().numpy()
+    rec = {
+        "workload": name, "value": st["sum_d"] * steps * world / (total_ms * 1e-3) / 1e9, "unit": "GTEPS",
+        "ms_per_step": total_ms / steps, "n": n, "m": m, "num_colors": k, "rounds": st["rounds"],
+        "sum_d": st["sum_d"], "useful_gteps": m / (total_ms / steps * 1e-3) / 1e9, "clocks": clocks,
+        "step_ms": {"min": min(step_ms), "max": max(step_ms)}, "tail_rounds": st["tail_rounds"],
+        "roofline": roofline_record(st, n, m, args.mode, statistics.mean(kern_ms), name, args.rule),
+        "gpu_launches": steps * {"fast": 1, "det": 3}.get(args.mode, 2 * (st["rounds"] + 1)),
+    }
+    if e2e:
+        ro_h = torch.from_numpy(g.row_offsets).pin_memory().numpy()
+        ci_h = torch.from_numpy(g.col_idx).pin_memory().numpy()
+        col_h = torch.empty(max(n, 1), dtype=torch.int32).pin_memory().numpy()
+        e2e_ms = []
+        for i in range(warmup + steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lib.sgr_color_host(n, ro_h, ci_h, col_h, mode, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= warmup:
+                e2e_ms.append(e0.elapsed_time(e1))
+        e2e_total = max_over_ranks(sum(e2e_ms), dev)
+        rec["e2e"] = {"value": st["sum_d"] * steps * world / (e2e_total * 1e-3) / 1e9, "unit": "GTEPS",
+                      "ms_per_step": e2e_total / steps, "h2d_bytes_per_step": 4 * (n + 1) + 4 * m,
+                      "d2h_bytes_per_step": 4 * n}
+    det = args.mode == "det" and args.rule == "low_keeps"
+    if cpu and world == 1:
+        model, ncpu = cpu_info()
+        if cpu == "det":
+            r, t_det, runs, t_serial, k_serial = oracle_baseline(g)
+            rec["cpu_baseline"] = {
+                "value": r.sum_d / t_det / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                "sample": f"{runs} full det-SGR runs of the workload (median), single thread",
+                "cpu": model, "host_cpus": ncpu, "serial_greedy_ms": t_serial * 1e3,
+                "serial_greedy_colors": k_serial}
+            if det:
+                rec["det_matches_oracle"] = bool(np.array_equal(got, r.colors))
+        else:  # serial greedy only: the det oracle takes minutes on the largest graphs
+            import oracle
+            ts = []
+            k_serial = 0
+            while sum(ts) < 3.0 and len(ts) < 10:
+                t0 = time.perf_counter()
+                _, k_serial = oracle.serial_greedy(g)
+                ts.append(time.perf_counter() - t0)
+            t_serial = statistics.median(ts)
+            rec["cpu_baseline"] = {
+                "value": m / t_serial / 1e9, "unit": "GTEPS (m / time: one pass)", "cores": 1,
+                "kind": "oracle", "sample": f"{len(ts)} serial first-fit greedy runs (median), single thread",
+                "cpu": model, "host_cpus": ncpu, "serial_greedy_ms": t_serial * 1e3,
+                "serial_greedy_colors": k_serial}
+        rec["serial_greedy_colors"] = k_serial
+        rec["colors_vs_serial"] = k / k_serial if k_serial else None
+        rec["speedup_vs_serial_greedy"] = t_serial * 1e3 / (total_ms / steps)
+    if det and check and "det_matches_oracle" not in rec and name in GOLDEN_SINGLE:
+        gold = golden("configs.json")[GOLDEN_SINGLE[name]]
+        rec["det_matches_oracle"] = bool(digest(got) == gold["det_colors_sha256"]
+                                         and k == gold["det_num_colors"])
+        rec["det_oracle_source"] = "tests/golden/configs.json (written by make_golden.py from the oracle)"
+    return rec, timeline
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -321,151 +479,88 @@ def run_ours(args, rank, world, local):
                            tail_vertices=tv)
     desc, make = workload(args.workload)
     g = make()
-    n, m = g.n, g.m
-    ro = torch.from_numpy(g.row_offsets).to(dev)
-    ci = torch.from_numpy(g.col_idx).to(dev)
-    colors = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    mode = args.mode + "+" + args.rule
     tuned = None
     if args.autotune:
-        tuned, tuned_ms = lib.sgr_autotune(n, ro, ci, colors, mode, 3000, stream)
-
-    def step():
-        return lib.sgr_color(n, ro, ci, colors, mode, stream)
-
-    for _ in range(max(args.warmup, 0)):
-        flush.fill_(1)
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    step_ms, kern_ms, stats = [], [], []
-    k = 0
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        k = step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        st = lib.sgr_last_stats()
-        stats.append(st)
-        kern_ms.append(st["device_ms"])
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    total_ms = max_over_ranks(sum(step_ms), dev)
-    if world > 1:
-        torch.distributed.barrier()
-    st = stats[-1]
-    work = st["sum_d"] * args.steps * world
-    value = work / (total_ms * 1e-3) / 1e9
-    # end to end through the host-buffer entry: H2D of the CSR, coloring, D2H of colors
-    ro_h = torch.from_numpy(g.row_offsets).pin_memory().numpy()
-    ci_h = torch.from_numpy(g.col_idx).pin_memory().numpy()
-    col_h = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
-    if args.timeline and rank == 0:
-        tl = lib.sgr_last_trace()
+        ro = torch.from_numpy(g.row_offsets).to(dev)
+        ci = torch.from_numpy(g.col_idx).to(dev)
+        colors = torch.empty(g.n, dtype=torch.int32, device=dev)
+        tuned, tuned_ms = lib.sgr_autotune(g.n, ro, ci, colors, args.mode + "+" + args.rule, 3000, stream)
+        del ro, ci, colors
+    rec, timeline = measure_single(lib, dev, stream, args.workload, g, args, args.steps, args.warmup, flush,
+                                   world=world, e2e=not args.no_e2e,
+                                   cpu=None if args.no_cpu_baseline else "det")
+    if args.timeline and rank == 0 and timeline is not None:
         with open(args.timeline, "w") as f:
-            json.dump({"workload": args.workload, "mode": mode, "init_ns": tl["init_ns"],
-                       **{k: v.tolist() for k, v in tl.items() if k != "init_ns"}}, f)
-    e2e_ms = []
-    for i in range(0 if args.no_e2e else args.warmup + args.steps):
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        lib.sgr_color_host(n, ro_h, ci_h, col_h, mode, stream)
-        e1.record(stream)
-        e1.synchronize()
-        if i >= args.warmup:
-            e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = max_over_ranks(sum(e2e_ms) if e2e_ms else float("nan"), dev)
-    e2e_value = st["sum_d"] * args.steps * world / (e2e_total * 1e-3) / 1e9
+            json.dump({"workload": args.workload, "mode": args.mode, "init_ns": timeline["init_ns"],
+                       **{k: v.tolist() for k, v in timeline.items() if k != "init_ns"}}, f)
+    suite = (world == 1 and not args.no_suite and args.workload == "rmat20" and args.mode == "det"
+             and args.rule == "low_keeps" and not args.tune and not args.autotune)
+    configs = {}
+    if suite:
+        del g
+        configs = run_suite(lib, dev, stream, args, flush)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    peak, peak_src = read_peaks()
-    kmean = statistics.mean(kern_ms)
-    ab = alg_bytes(st, n, m, args.mode)
-    achieved = ab / (kmean * 1e-3) / 1e9
-    pb = paper_bytes(st)
     line = {
-        "metric": METRIC_SINGLE, "value": value, "unit": "GTEPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "metric": METRIC_SINGLE, "value": rec["value"], "unit": "GTEPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "n": n, "m": m,
+        "config": {"workload": args.workload, "description": desc, "n": rec["n"], "m": rec["m"],
                    "mode": args.mode, "rule": args.rule, "tuning": lib.sgr_get_tuning(),
                    "tuning_source": "autotuned" if tuned else ("--tune" if args.tune else "default"),
                    "l2": "flushed (512 MiB write) before every step",
                    "parallelism": f"replicas x{world}"},
-        "num_colors": k, "rounds": st["rounds"], "sum_d": st["sum_d"],
-        "useful_gteps": m / (total_ms / args.steps * 1e-3) / 1e9,
-        "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": "GTEPS", "ms_per_step": e2e_total / args.steps,
-                "h2d_bytes_per_step": 4 * (n + 1) + 4 * m, "d2h_bytes_per_step": 4 * n},
-        # per step: the round kernel, then (det) the activation-list kernel and
-        # the tail kernel, each of which returns at once when not handed over
-        # (topology-driven: two kernels per iteration, and the final one that finds nothing)
-        "gpu_launches": args.steps * {"fast": 1, "det": 3}.get(args.mode, 2 * (st["rounds"] + 1)),
-        "step_ms": {"min": min(step_ms), "max": max(step_ms)},
-        "tail_rounds": st["tail_rounds"],
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": read_traffic(args.workload, args.mode) if args.rule == "low_keeps" else None,
-                     "alg_bytes_per_launch": ab, "kernel_ms": kmean,
-                     "paper_model": {"bytes_per_launch": pb, "equivalent_gbs": pb / (kmean * 1e-3) / 1e9,
-                                     "frac": pb / (kmean * 1e-3) / 1e9 / peak,
-                                     "what": "Algorithms 4/5 as printed: rows re-read every round"},
-                     "kernel": ("the coloring launches of one call, timed together on their stream: "
-                                "sgr_color_kernel (init, rounds on the grid), its activation-list "
-                                "variant, sgr_tail_kernel (last rounds in one CTA)") if args.mode != "topo" else
-                               ("the topology-driven iterations of one call (topo_assign_kernel and "
-                                "topo_resolve_kernel per iteration, host loop on a flag), event to event"),
-                     "peak_source": peak_src + " of measured"
-                     if peak_src.startswith("measured") else peak_src},
     }
-    if not args.no_cpu_baseline and world == 1:
-        r, t_det, runs, t_serial, k_serial = oracle_baseline(g)
-        model, ncpu = cpu_info()
-        line["cpu_baseline"] = {
-            "value": r.sum_d / t_det / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"{runs} full det-SGR runs of the workload (median), single thread",
-            "cpu": model, "host_cpus": ncpu,
-            "serial_greedy_ms": t_serial * 1e3, "serial_greedy_colors": k_serial,
-        }
-        line["serial_greedy_colors"] = k_serial
-        line["colors_vs_serial"] = k / k_serial if k_serial else None
-        line["speedup_vs_serial_greedy"] = t_serial * 1e3 / (total_ms / args.steps)
-        if args.mode == "det" and args.rule == "low_keeps":
-            line["det_matches_oracle"] = bool(
-                np.array_equal(colors.cpu().numpy(), r.colors))
+    for key in ("num_colors", "rounds", "sum_d", "useful_gteps", "clocks", "e2e", "gpu_launches", "step_ms",
+                "tail_rounds", "roofline", "cpu_baseline", "serial_greedy_colors", "colors_vs_serial",
+                "speedup_vs_serial_greedy", "det_matches_oracle"):
+        if key in rec:
+            line[key] = rec[key]
+    if configs:
+        line["configs"] = configs
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def run_batch(args, rank, world, local):
+def run_suite(lib, dev, stream, args, flush):
+    """The other configurations, each as a sub-record of the headline line:
+    the 192^3 stencil and the 20k uniform graph (single graphs), the 512-graph
+    batch, the same 512 graphs submitted at once to the server, and the open
+    Poisson stream of served requests at two arrival rates."""
+    out = {}
+    t0 = time.time()
+    steps = max(3, min(args.steps, 10))
+    g = gg.stencil27(192)
+    out["stencil192"], _ = measure_single(lib, dev, stream, "stencil192", g, args, steps, args.warmup, flush,
+                                          cpu="serial")
+    out["stencil192"]["description"] = WORKLOADS["stencil192"][0]
+    del g
+    g = gg.er20k(0)
+    out["er20k"], _ = measure_single(lib, dev, stream, "er20k", g, args, args.steps, args.warmup, flush, cpu="det")
+    out["er20k"]["description"] = WORKLOADS["er20k"][0]
+    del g
+    out["batch512"] = measure_batch(lib, dev, stream, "batch512", steps, args.warmup, flush)
+    out["serve512"] = measure_serve_burst(lib, args.budget_gb, steps, max(args.warmup, 1))
+    out["serve"] = measure_serve(lib, args.requests, args.pool, args.rate, args.budget_gb)
+    if args.rate == 0:  # also at the sequential path's capacity
+        out["serve_at_sequential_rate"] = measure_serve(lib, max(1, args.requests // 2), args.pool,
+                                                        -1.0, args.budget_gb)
+    out["suite_wall_s"] = time.time() - t0
+    return out
+
+
+def measure_batch(lib, dev, stream, name, steps, warmup, flush, rank=0, world=1):
     """Batched workload: graphs/s of one sgr_color_batch call over the whole mix,
-    against the same graphs colored by one sgr_color call each (the plain path)."""
+    against the same graphs colored by one sgr_color call each (the plain path),
+    with every graph's colors checked against the oracle's digest."""
     import torch
-
-    from paper_1606_06025_gb300 import sgrcolor as lib
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    desc, make = BATCH_WORKLOADS[args.workload]
+    desc, make = BATCH_WORKLOADS[name]
     b = make()
     if world > 1:  # shard the graphs by rank: no exchange on the data path
         b = gg.pack(shard(b.graphs, rank, world))
@@ -474,23 +569,21 @@ def run_batch(args, rank, world, local):
     ci = torch.from_numpy(b.col_idx).to(dev)
     colors = torch.empty(n, dtype=torch.int32, device=dev)
     kk = np.zeros(G, dtype=np.int32)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    mode = args.mode
+    mode = "det"
 
     def step():
         lib.sgr_color_batch(G, b.vtx_off, b.edge_off, ro, ci, colors, kk, mode, stream)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.fill_(1)
         step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(dev.index)
     sampler.start()
-    ms = []
-    for _ in range(args.steps):
+    ms, kms = [], []
+    for _ in range(steps):
         flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -499,12 +592,13 @@ def run_batch(args, rank, world, local):
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
+        kms.append(lib.sgr_last_stats()["device_ms"])
     clocks = sampler.stop()
     st = lib.sgr_last_stats()
     total = max_over_ranks(sum(ms), dev)
-    value = G * world * args.steps / (total * 1e-3)
+    value = G * world * steps / (total * 1e-3)
+    got = colors.cpu().numpy()
     # the plain path: one sgr_color per graph, same graphs, same device buffers
-    seq_ms = []
     offs = [(int(b.vtx_off[i]), int(b.vtx_off[i + 1]), int(b.edge_off[i]), int(b.edge_off[i + 1]))
             for i in range(G)]
     dev_graphs = []
@@ -514,6 +608,8 @@ def run_batch(args, rank, world, local):
             4, dtype=torch.int32, device=dev)
         dev_graphs.append((v1 - v0, r, c))
     out = torch.empty(max(x[0] for x in dev_graphs) + 1, dtype=torch.int32, device=dev)
+    seq_ms = []
+    same_as_alone = True
     for rep in range(2):
         flush.fill_(1)
         torch.cuda.synchronize()
@@ -526,39 +622,78 @@ def run_batch(args, rank, world, local):
         e1.synchronize()
         if rep == 1:
             seq_ms.append(e0.elapsed_time(e1))
+    for i in range(0, G, max(1, G // 16)):  # a sample of graphs, alone, against their batch slice
+        nn, r, c = dev_graphs[i]
+        lib.sgr_color(nn, r, c, out, mode, stream)
+        same_as_alone &= bool(np.array_equal(out[:nn].cpu().numpy(), got[offs[i][0]:offs[i][1]]))
     seq_value = G / (seq_ms[0] * 1e-3)
-    if rank != 0:
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return
-    line = {
-        "metric": "batched graphs/s", "value": value, "unit": "graphs/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "graphs": G, "n": n, "m": m,
-                   "mode": mode, "l2": "flushed (512 MiB write) before every step",
-                   "parallelism": f"graphs sharded by rank x{world}"},
-        "rounds": st["rounds"], "sum_d": st["sum_d"], "kernel_ms": st["device_ms"],
-        "sequential_graphs_per_s": seq_value, "speedup_vs_sequential": value / seq_value,
-        "clocks": clocks, "gpu_launches": args.steps * 5,
-    }
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    rec = {"workload": name, "description": desc, "metric": "batched graphs/s", "value": value,
+           "unit": "graphs/s", "ms_per_step": total / steps, "graphs": G, "n": n, "m": m, "mode": mode,
+           "rounds": st["rounds"], "sum_d": st["sum_d"], "kernel_ms": statistics.mean(kms),
+           "sequential_graphs_per_s": seq_value, "speedup_vs_sequential": value / seq_value,
+           "clocks": clocks, "gpu_launches": steps * 5,
+           "roofline": roofline_record(st, n, m, "det", statistics.mean(kms), name, "low_keeps"),
+           "batch_slices_equal_alone": same_as_alone}
+    if name == "batch512" and world == 1:
+        gold = golden("mix_digests.json")["batch512"]["graphs"]
+        bad = sum(1 for i, gr in enumerate(gold)
+                  if digest(got[offs[i][0]:offs[i][1]]) != gr["det_colors_sha256"]
+                  or kk[i] != gr["det_num_colors"])
+        rec["det_matches_oracle"] = bad == 0
+        rec["det_oracle_source"] = "tests/golden/mix_digests.json (per-graph digests from the oracle)"
+        # the oracle on a bounded sample of the mix, single thread
+        import oracle
+        t0 = time.perf_counter()
+        done = 0
+        for g in b.graphs:
+            oracle.det_sgr(g)
+            done += 1
+            if time.perf_counter() - t0 > 10.0:
+                break
+        el = time.perf_counter() - t0
+        model, ncpu = cpu_info()
+        rec["cpu_baseline"] = {"value": done / el, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                               "sample": f"det-SGR of the first {done} graphs of the mix, single thread",
+                               "cpu": model, "host_cpus": ncpu}
+    return rec
 
 
-def run_serve_burst(args, rank, world, local):
-    """The 512-graph batch mix submitted at once to the server (host buffers in,
-    colors out), against the same graphs colored one at a time through the
-    host-buffer entry point: graphs/s, and p50/p99 request latency."""
+def run_batch(args, rank, world, local):
     import torch
 
     from paper_1606_06025_gb300 import sgrcolor as lib
 
     torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rec = measure_batch(lib, dev, stream, args.workload, args.steps, args.warmup, flush, rank, world)
+    if rank == 0:
+        line = {"metric": rec.pop("metric"), "value": rec.pop("value"), "unit": rec.pop("unit"),
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": rec.pop("ms_per_step"), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": args.workload, "description": rec.pop("description"),
+                           "graphs": rec["graphs"], "n": rec["n"], "m": rec["m"], "mode": "det",
+                           "l2": "flushed (512 MiB write) before every step",
+                           "parallelism": f"graphs sharded by rank x{world}"}, **rec}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_serve_burst(lib, budget_gb, steps, warmup, rank=0, world=1):
+    """The 512-graph batch mix submitted at once to the server (host buffers in,
+    colors out), against the same graphs colored one at a time through the
+    host-buffer entry point: graphs/s, and p50/p99 request latency; every result
+    checked against the oracle's digest."""
     b = gg.batch_mix(512, 1000, 200000, 0)
-    graphs = shard(b.graphs, rank, world)
+    gold = golden("mix_digests.json")["batch512"]["graphs"]
+    idx = shard(range(b.G), rank, world)
+    graphs = [b.graphs[i] for i in idx]
     outs = [np.empty(g.n, dtype=np.int32) for g in graphs]
     for g, o in zip(graphs[:8], outs):  # warm-up
         lib.sgr_color_host(g.n, g.row_offsets, g.col_idx, o, "det")
@@ -568,11 +703,9 @@ def run_serve_burst(args, rank, world, local):
     seq_s = time.perf_counter() - t0
     seq_gps = len(graphs) / seq_s
     runs = []
-    import threading
     clients = 4  # concurrent submitters, each with a share of the graphs
-    with lib.Server(hbm_budget_bytes=int(args.budget_gb * (1 << 30)), mode="det",
-                    staging_bytes=8 << 30) as srv:
-        for rep in range(max(args.warmup, 1) + args.steps):
+    with lib.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)), mode="det", staging_bytes=8 << 30) as srv:
+        for rep in range(warmup + steps):
             got = [None] * len(graphs)
 
             def client(c):
@@ -588,49 +721,53 @@ def run_serve_burst(args, rank, world, local):
             for t in th:
                 t.join()
             dt = time.perf_counter() - t0
-            if rep >= max(args.warmup, 1):
+            if rep >= warmup:
                 runs.append(dt)
         st = srv.stats()
-    ok = all(np.array_equal(c, o) for (c, _), o in zip(got, outs))
+    ok = all(digest(c) == gold[i]["det_colors_sha256"] and k == gold[i]["det_num_colors"]
+             for i, (c, k) in zip(idx, got))
     value = len(graphs) * world / statistics.median(runs)
-    if rank != 0:
-        return
-    line = {
-        "metric": "served graphs/s, p50/p99 latency", "value": value, "unit": "graphs/s",
-        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 1),
-        "ms_per_step": statistics.median(runs) * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "serve512", "graphs": len(graphs),
-                   "submission": "all at once from 4 client threads",
-                   "description": BATCH_WORKLOADS["batch512"][0], "mode": "det",
-                   "hbm_budget_gb": args.budget_gb},
-        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-        "sequential_host_graphs_per_s": seq_gps, "speedup_vs_sequential": value / seq_gps,
-        "results_equal_sequential": ok, "launches": st["launches"], "rounds": st["rounds"],
-    }
-    print(json.dumps(line), flush=True)
+    return {"workload": "serve512", "metric": "served graphs/s, p50/p99 latency", "value": value,
+            "unit": "graphs/s", "ms_per_step": statistics.median(runs) * 1e3, "graphs": len(graphs),
+            "submission": "all at once from 4 client threads", "description": BATCH_WORKLOADS["batch512"][0],
+            "mode": "det", "hbm_budget_gb": budget_gb, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "sequential_host_graphs_per_s": seq_gps, "speedup_vs_sequential": value / seq_gps,
+            "det_matches_oracle": ok, "launches": st["launches"], "rounds": st["rounds"],
+            "colored_alone": st["direct"], "latency": "submit to completion, host buffers (H2D and D2H included)"}
 
 
-def run_serve(args, rank, world, local):
-    """Served workload: an open-loop Poisson stream of requests drawn from a
-    pool of distinct-seed graphs (sizes log-uniform in [1k, 4M], the batch
-    mix's kinds), through the continuous-batching server with its HBM budget,
-    against the same requests colored one at a time by sgr_color_host (both
-    include the host-device copies)."""
-    import threading
-
+def run_serve_burst(args, rank, world, local):
     import torch
 
     from paper_1606_06025_gb300 import sgrcolor as lib
 
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    specs = gg.mix_specs(args.pool, 1000, 4000000, 7 + rank)
+    rec = measure_serve_burst(lib, args.budget_gb, args.steps, max(args.warmup, 1), rank, world)
+    if rank != 0:
+        return
+    line = {"metric": rec.pop("metric"), "value": rec.pop("value"), "unit": rec.pop("unit"), "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": rec.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": "serve512", "graphs": rec["graphs"],
+                                            "hbm_budget_gb": args.budget_gb}, **rec}
+    print(json.dumps(line), flush=True)
+
+
+def measure_serve(lib, requests, pool_size, rate, budget_gb, rank=0):
+    """Served workload: an open-loop Poisson stream of requests drawn from a
+    pool of distinct-seed graphs (sizes log-uniform in [1k, 4M], the batch
+    mix's kinds), through the continuous-batching server with its HBM budget,
+    against the same requests colored one at a time by sgr_color_host (both
+    include the host-device copies).  rate > 0: arrivals per second; 0: 0.7 x
+    the server's measured burst capacity; < 0: the sequential path's
+    capacity."""
+    specs = gg.mix_specs(pool_size, 1000, 4000000, 7 + rank)
     pool = [gg.mix_graph(s) for s in specs]
+    gold = None
+    if pool_size == 24 and rank == 0:
+        gold = golden("mix_digests.json")["serve_pool"]["graphs"]
     rnd = np.random.default_rng(11 + rank)
-    picks = rnd.integers(0, len(pool), size=args.requests)
+    picks = rnd.integers(0, len(pool), size=requests)
     # sequential plain path: mean time per request over the pick distribution
     seq = []
     for g in pool:
@@ -641,8 +778,7 @@ def run_serve(args, rank, world, local):
         seq.append(time.perf_counter() - t0)
     seq_mean = float(np.mean([seq[j] for j in picks]))
     seq_gps = 1.0 / seq_mean
-    budget = int(args.budget_gb * (1 << 30))
-    results = {}
+    budget = int(budget_gb * (1 << 30))
 
     def drain(srv, ids, done):
         for i, rid in ids:
@@ -651,15 +787,20 @@ def run_serve(args, rank, world, local):
 
     with lib.Server(hbm_budget_bytes=budget, mode="det") as srv:
         # capacity: a burst of requests submitted at once
-        burst = min(args.requests, 64)
+        burst = min(requests, 64)
         t0 = time.perf_counter()
-        bids = [(i, srv.submit(pool[picks[i]].row_offsets, pool[picks[i]].col_idx))
-                for i in range(burst)]
+        bids = [(i, srv.submit(pool[picks[i]].row_offsets, pool[picks[i]].col_idx)) for i in range(burst)]
         bdone = {}
         drain(srv, bids, bdone)
         capacity = burst / (time.perf_counter() - t0)
-    rate = args.rate if args.rate > 0 else 0.7 * capacity
-    gaps = rnd.exponential(1.0 / rate, size=args.requests)
+    if rate > 0:
+        lam, rate_src = rate, "stated"
+    elif rate == 0:
+        lam, rate_src = 0.7 * capacity, "0.7 x measured burst capacity"
+    else:
+        lam, rate_src = seq_gps, "the sequential path's capacity"
+    gaps = rnd.exponential(1.0 / lam, size=requests)
+    bad = []
     with lib.Server(hbm_budget_bytes=budget, mode="det") as srv:
         sub_t = {}
         ids = []
@@ -670,7 +811,7 @@ def run_serve(args, rank, world, local):
 
         def poller():  # non-blocking sweeps, so each completion is seen when it happens
             outstanding = []
-            while len(done) < args.requests:
+            while len(done) < requests:
                 with lock:
                     outstanding.extend(ids)
                     ids.clear()
@@ -681,12 +822,16 @@ def run_serve(args, rank, world, local):
                         still.append((i, rid))
                     else:
                         done[i] = (time.perf_counter(), got[1])
+                        if gold is not None:
+                            gr = gold[picks[i]]
+                            if digest(got[0]) != gr["det_colors_sha256"] or got[1] != gr["det_num_colors"]:
+                                bad.append(i)
                 outstanding = still
                 time.sleep(0.0002)
 
         th = threading.Thread(target=poller, daemon=True)
         th.start()
-        for i in range(args.requests):
+        for i in range(requests):
             t_next += gaps[i]
             delay = t_next - time.perf_counter()
             if delay > 0:
@@ -699,29 +844,45 @@ def run_serve(args, rank, world, local):
         th.join()
         t_end = max(t for t, _ in done.values())
         st = srv.stats()
-    lat = np.array([(done[i][0] - sub_t[i]) * 1e3 for i in range(args.requests)])
-    value = args.requests / (t_end - t_start)
+    lat = np.array([(done[i][0] - sub_t[i]) * 1e3 for i in range(requests)])
+    value = requests / (t_end - t_start)
+    sizes = [pool[j].n for j in picks]
+    rec = {"workload": "serve", "metric": "served graphs/s, p50/p99 latency", "value": value,
+           "unit": "graphs/s", "ms_per_step": 1e3 / value, "requests": requests, "pool": pool_size,
+           "sizes": "log-uniform [1k, 4M] vertices; 1/3 uniform, 1/3 R-MAT, 1/3 stencils",
+           "arrivals": "open-loop Poisson", "arrival_rate_per_s": lam, "arrival_rate": rate_src,
+           "hbm_budget_gb": budget_gb, "mode": "det", "mean_vertices": float(np.mean(sizes)),
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "server_p50_ms": st["p50_ms"], "server_p99_ms": st["p99_ms"],
+           # open loop: value follows the arrival rate while the server keeps up,
+           # so capacity is compared with capacity
+           "burst_capacity_graphs_per_s": capacity, "sequential_graphs_per_s": seq_gps,
+           "capacity_vs_sequential": capacity / seq_gps, "launches": st["launches"], "rounds": st["rounds"],
+           "colored_alone": st["direct"],
+           "latency": "submit to completion, host buffers (H2D and D2H included)"}
+    if gold is not None:
+        rec["det_matches_oracle"] = not bad
+        rec["det_oracle_source"] = "tests/golden/mix_digests.json serve_pool (per-graph digests from the oracle)"
+    return rec
+
+
+def run_serve(args, rank, world, local):
+    import torch
+
+    from paper_1606_06025_gb300 import sgrcolor as lib
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    rec = measure_serve(lib, args.requests, args.pool, args.rate, args.budget_gb, rank)
     if rank != 0:
         return
-    sizes = [pool[j].n for j in picks]
-    line = {
-        "metric": "served graphs/s, p50/p99 latency", "value": value, "unit": "graphs/s",
-        "n_gpus": world, "steps": args.requests, "warmup": burst, "ms_per_step": 1e3 / value,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic",
-        "config": {"workload": "serve", "requests": args.requests, "pool": args.pool,
-                   "sizes": "log-uniform [1k, 4M] vertices; 1/3 uniform, 1/3 R-MAT, 1/3 stencils",
-                   "arrivals": "open-loop Poisson", "arrival_rate_per_s": rate,
-                   "hbm_budget_gb": args.budget_gb, "mode": "det",
-                   "mean_vertices": float(np.mean(sizes))},
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "server_p50_ms": st["p50_ms"], "server_p99_ms": st["p99_ms"],
-        # open loop: value follows the arrival rate while the server keeps up,
-        # so capacity is compared with capacity
-        "burst_capacity_graphs_per_s": capacity, "sequential_graphs_per_s": seq_gps,
-        "capacity_vs_sequential": capacity / seq_gps,
-        "launches": st["launches"], "rounds": st["rounds"],
-    }
+    line = {"metric": rec.pop("metric"), "value": rec.pop("value"), "unit": rec.pop("unit"), "n_gpus": world,
+            "steps": args.requests, "warmup": 64, "ms_per_step": rec.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": "serve", "requests": args.requests, "pool": args.pool,
+                                            "hbm_budget_gb": args.budget_gb}, **rec}
     print(json.dumps(line), flush=True)
 
 
@@ -746,10 +907,13 @@ def main():
                     help="light_max,chunk,blocks_per_sm[,active_lists[,tail_vertices]] (0 = default)")
     ap.add_argument("--autotune", action="store_true",
                     help="measure the tuning candidates on the workload before timing")
-    ap.add_argument("--requests", type=int, default=600, help="serve: requests in the stream")
+    ap.add_argument("--no-suite", action="store_true",
+                    help="headline workload only (by default the rmat20 line also carries the other "
+                         "configurations as sub-records)")
+    ap.add_argument("--requests", type=int, default=10000, help="serve: requests in the stream")
     ap.add_argument("--pool", type=int, default=24, help="serve: distinct graphs drawn from")
     ap.add_argument("--rate", type=float, default=0.0,
-                    help="serve: arrivals per second (0: 0.7 x measured capacity)")
+                    help="serve: arrivals per second (0: 0.7 x measured capacity; < 0: the sequential capacity)")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: server HBM budget")
     args = ap.parse_args()
     rank, world, local = dist_env()

@@ -227,13 +227,20 @@ typedef struct sgr_server sgr_server;
 
 typedef struct {
     int64_t hbm_budget_bytes;  /* device memory the server allocates at creation (0: 1 GiB):
-                                  about 30% for per-vertex state, the rest for col_idx */
+                                  a quarter for the scratch of requests colored alone (when
+                                  direct_min_vertices >= 0), of the rest about 30% for
+                                  per-vertex state and the remainder for col_idx */
     int32_t max_inflight;      /* graphs resident at once (0: 1024) */
     int32_t mode;              /* SGR_MODE_DETERMINISTIC | SGR_RULE_* */
     int32_t device;            /* CUDA device ordinal */
     int32_t rounds_per_launch; /* rounds advanced per launch (0: 8 while requests wait, else 64) */
     int64_t staging_bytes;     /* pinned host memory for request copies (0: 1 GiB, < 0: none);
                                   requests that do not fit use ordinary memory */
+    int32_t direct_min_vertices; /* requests with at least this many vertices are colored
+                                  alone on the single-graph kernels of sgr_color (with its
+                                  activation lists and one-CTA tail), between two batched
+                                  launches, in a scratch region of the budget (0: 262144,
+                                  < 0: never); smaller ones share the batched rounds */
 } sgr_server_config;
 
 typedef struct {
@@ -247,6 +254,7 @@ typedef struct {
     int64_t entry_capacity;    /* col_idx entries that can be resident at once */
     double p50_ms, p99_ms, mean_ms;  /* submit-to-finish latency of completed requests */
     double graphs_per_s;       /* completed / (last completion - first submission) */
+    int64_t direct;            /* requests colored alone on the single-graph kernels */
 } sgr_server_counters;
 
 /* Create a server on cfg->device; allocates its whole budget up front.

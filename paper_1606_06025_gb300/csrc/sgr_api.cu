@@ -486,6 +486,70 @@ namespace sgr {
 
 sgr_tuning tuning_snapshot() { return current_tuning(); }
 
+// Scratch bytes color_single_in needs for a graph (deterministic mode, with
+// the activation lists and the tail arrays of sgr_color).
+size_t single_scratch_bytes(int32_t n, long long m) {
+    Job j;
+    std::memset(&j, 0, sizeof(j));
+    j.n = n;
+    j.m = m;
+    j.front = true;
+    j.tail = true;
+    size_t zero_bytes = 0;
+    return layout(j, current_tuning(), nullptr, nullptr, &zero_bytes);
+}
+
+// The launches of sgr_color (deterministic or fast mode) for one graph in
+// device memory, with the scratch at `base` (cap bytes, 256-byte aligned,
+// owned by the caller).  The caller holds the device's launch mutex.  Writes
+// k to *k_out and the rounds to *rounds_out on success; SGR_ERR_INVALID_ARG
+// if the scratch does not fit.  Used by the server for requests it colors
+// alone between its batched launches.
+int color_single_in(char *base, size_t cap, int32_t n, long long m, const int32_t *ro, const int32_t *ci,
+                    int32_t *colors, int mode, cudaStream_t st, int32_t *k_out, long long *rounds_out) {
+    if (n <= 0) {
+        *k_out = 0;
+        return SGR_OK;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SGR_ERR_CUDA;
+    const sgr_tuning t = current_tuning();
+    const bool fast = (mode & SGR_MODE_MASK) == SGR_MODE_FAST;
+    Job j;
+    std::memset(&j, 0, sizeof(j));
+    j.fast = fast;
+    j.n = n;
+    j.m = m;
+    j.ro = ro;
+    j.ci = ci;
+    j.colors = colors;
+    j.front = true;
+    j.tail = true;
+    size_t zero_bytes = 0;
+    if (layout(j, t, nullptr, nullptr, &zero_bytes) > cap) return SGR_ERR_INVALID_ARG;
+    Params p;
+    layout(j, t, base, &p, nullptr);
+    p.rule = (mode & SGR_RULE_MASK) >> 4;
+    p.max_rounds = (long long)n + 1;
+    int per_sm = 0, per_sm_f = 0, sms = 0;
+    if (occupancy_blocks_per_sm(fast, false, &per_sm) != 0) return SGR_ERR_CUDA;
+    if (occupancy_blocks_per_sm_front(false, &per_sm_f) != 0) return SGR_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SGR_ERR_CUDA;
+    cudaError_t e = cudaMemsetAsync(base, 0, zero_bytes, st);
+    if (e != cudaSuccess) return map_cuda(e);
+    int grid = 0;
+    if ((e = launch_rounds(p, fast, false, per_sm, per_sm_f, sms, t, st, &grid)) != cudaSuccess)
+        return map_cuda(e);
+    Counters h;  // pageable: the copy completes before the synchronisation returns
+    if ((e = cudaMemcpyAsync(&h, p.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return map_cuda(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return map_cuda(e);
+    if (h.err != 0) return h.err;
+    *k_out = h.kmax;
+    *rounds_out = h.rounds;
+    return SGR_OK;
+}
+
 unsigned long long wait_limit_ns() {
     const unsigned long long w = g_wait_ns.load();
     return w ? w : kWaitTimeoutNs;

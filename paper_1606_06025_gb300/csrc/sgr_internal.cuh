@@ -205,6 +205,11 @@ inline ScratchPlan plan_scratch(long long n, long long m, int chunk) {
 sgr_tuning tuning_snapshot();
 std::mutex &device_launch_mutex(int device);
 unsigned long long wait_limit_ns();  // sgr_set_wait_limit, or kWaitTimeoutNs
+// The single-graph launches with caller-owned scratch (caller holds the
+// device launch mutex); used by the server for requests it colors alone.
+size_t single_scratch_bytes(int32_t n, long long m);
+int color_single_in(char *base, size_t cap, int32_t n, long long m, const int32_t *ro, const int32_t *ci,
+                    int32_t *colors, int mode, cudaStream_t st, int32_t *k_out, long long *rounds_out);
 // Host-side fault injection (sgr_debug_inject): true when this device
 // allocation must fail as out of memory; the extra CTAs the next coloring
 // launch's grid barriers wait for (0 normally; consumed by the call).

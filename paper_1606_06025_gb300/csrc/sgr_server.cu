@@ -104,6 +104,8 @@ struct Request {
     int slot = -1;
     long long vb = 0, eb = 0, rb = 0;
     long long r_admit = 0;  // server round at which the graph's round 1 runs
+    long long ealen = 0;    // entries of its col_idx range (m rounded up to 16 bytes)
+    bool direct = false;    // colored alone on the single-graph kernels
 };
 
 }  // namespace
@@ -136,6 +138,13 @@ struct sgr_server {
     int32_t *nv_h = nullptr, *rem_h = nullptr, *kmax_h = nullptr;
     sgr::Counters *ctr_h = nullptr;
     long long round = 1;
+    char *direct_mem = nullptr;   // scratch of requests colored alone (part of the budget)
+    size_t direct_cap = 0;
+    long long direct_min = 0;     // vertices from which a request is colored alone
+    long long direct_count = 0;
+    cudaStream_t copy_stream = nullptr;  // host<->device copies of requests colored alone
+    static constexpr int kDirectPass = 4;  // requests colored alone per pass, at most
+    cudaEvent_t ev_in[kDirectPass] = {}, ev_done[kDirectPass] = {};
     // statistics
     std::vector<double> lat_ms;
     long long submitted = 0, completed = 0, failed = 0, launches = 0, rounds_run = 0;
@@ -151,7 +160,9 @@ namespace {
 constexpr long long kVertexBytes = 4 + 32 + 4 + 4 + 4 + 2 * 4 * 4 + 2 * 4 * 4 + 6 * 4 + 4;
 
 int carve(sgr_server *S) {
-    const long long budget = S->cfg.hbm_budget_bytes;
+    // a quarter of the budget for the scratch of requests colored alone
+    S->direct_cap = S->direct_min > 0 ? align_up((size_t)(S->cfg.hbm_budget_bytes / 4)) : 0;
+    const long long budget = S->cfg.hbm_budget_bytes - (long long)S->direct_cap;
     const int G = S->G;
     const size_t fixed = align_up(sizeof(sgr::Counters)) +
                          align_up(sizeof(long long) * sgr::kTraceCap * sgr::kTraceFields) +
@@ -212,6 +223,7 @@ int carve(sgr_server *S) {
     take((void **)&S->kmax_d, (size_t)G * 4);
     take((void **)&ro, (size_t)S->Rcap * 4);
     take((void **)&ci, (size_t)Ecap * 4 + 64);
+    if (S->direct_cap) take((void **)&S->direct_mem, S->direct_cap);
     for (auto &pr : parts) off += align_up(pr.second);
     if (sgr::inject_alloc_failure()) return SGR_ERR_OUT_OF_MEMORY;
     cudaError_t e = cudaMalloc(&S->dmem, off);
@@ -296,11 +308,16 @@ void host_free(sgr_server *S, HostBuf &b) {
     std::vector<int32_t>().swap(b.vec);
 }
 
-void release_slot(sgr_server *S, Request *q) {
+void release_ranges(sgr_server *S, Request *q) {
     // caller holds S->mu
     S->va.release(q->vb, q->n);
-    S->ea.release(q->eb, q->m);
+    S->ea.release(q->eb, q->ealen);
     S->ra.release(q->rb, (long long)q->n + 1);
+}
+
+void release_slot(sgr_server *S, Request *q) {
+    // caller holds S->mu
+    release_ranges(S, q);
     S->slot_req[q->slot] = nullptr;
     S->free_slots.push_back(q->slot);
     q->slot = -1;
@@ -319,7 +336,7 @@ void fail_all_resident(sgr_server *S, int status) {
 void worker_loop(sgr_server *S) {
     cudaSetDevice(S->device);
     for (;;) {
-        std::vector<Request *> admitted;
+        std::vector<Request *> admitted, direct;
         int resident = 0;
         bool have_pending = false;
         {
@@ -327,26 +344,37 @@ void worker_loop(sgr_server *S) {
             if (S->stop) break;
             for (auto it = S->pending.begin(); it != S->pending.end();) {
                 Request *q = *it;
-                if (S->free_slots.empty()) break;
+                // large graphs are colored alone (one per pass, so that the
+                // resident graphs keep advancing); the others join the rounds
+                const bool alone = S->direct_cap > 0 && q->n >= S->direct_min &&
+                                   sgr::single_scratch_bytes(q->n, q->m) <= S->direct_cap;
+                if (alone && (int)direct.size() >= sgr_server::kDirectPass) { ++it; continue; }  // next pass
+                if (!alone && S->free_slots.empty()) { ++it; continue; }
+                q->ealen = (q->m + 3) & ~3ll;  // every col_idx range starts on 16 bytes
                 const long long vb = S->va.alloc(q->n);
                 if (vb < 0) { ++it; continue; }
-                const long long eb = S->ea.alloc(q->m);
+                const long long eb = S->ea.alloc(q->ealen);
                 if (eb < 0) { S->va.release(vb, q->n); ++it; continue; }
                 const long long rb = S->ra.alloc((long long)q->n + 1);
-                if (rb < 0) { S->va.release(vb, q->n); S->ea.release(eb, q->m); ++it; continue; }
-                q->slot = S->free_slots.back();
-                S->free_slots.pop_back();
-                q->r_admit = S->round;
+                if (rb < 0) { S->va.release(vb, q->n); S->ea.release(eb, q->ealen); ++it; continue; }
                 q->vb = vb;
                 q->eb = eb;
                 q->rb = rb;
-                S->slot_req[q->slot] = q;
-                admitted.push_back(q);
+                if (alone) {
+                    q->direct = true;
+                    direct.push_back(q);
+                } else {
+                    q->slot = S->free_slots.back();
+                    S->free_slots.pop_back();
+                    q->r_admit = S->round;
+                    S->slot_req[q->slot] = q;
+                    admitted.push_back(q);
+                }
                 it = S->pending.erase(it);
             }
             resident = S->G - (int)S->free_slots.size();
             have_pending = !S->pending.empty();
-            if (resident == 0) {
+            if (resident == 0 && direct.empty()) {
                 S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
                 continue;
             }
@@ -354,6 +382,73 @@ void worker_loop(sgr_server *S) {
         std::lock_guard<std::mutex> dev_lk(sgr::device_launch_mutex(S->device));
         cudaStream_t st = S->stream;
         cudaError_t e = cudaSuccess;
+        // Requests colored alone, one after another with the launches of
+        // sgr_color, in the scratch region.  Their CSR copies all go out at
+        // once on the copy stream, and each one's colors come back on it while
+        // the next one is colored, so that the copies overlap the coloring.
+        std::vector<int> status(direct.size(), SGR_OK);
+        for (size_t i = 0; i < direct.size(); ++i) {
+            Request *q = direct[i];
+            cudaError_t ce = cudaMemcpyAsync((int32_t *)S->P.ro + q->rb, q->csr.ptr, ((size_t)q->n + 1) * 4,
+                                             cudaMemcpyHostToDevice, S->copy_stream);
+            if (ce == cudaSuccess && q->m > 0)
+                ce = cudaMemcpyAsync((int32_t *)S->P.ci + q->eb, q->csr.ptr + q->n + 1, (size_t)q->m * 4,
+                                     cudaMemcpyHostToDevice, S->copy_stream);
+            if (ce == cudaSuccess) ce = cudaEventRecord(S->ev_in[i], S->copy_stream);
+            if (ce != cudaSuccess) status[i] = map_err(ce);
+        }
+        for (size_t i = 0; i < direct.size(); ++i) {
+            Request *q = direct[i];
+            int32_t k = 0;
+            long long rr = 0;
+            if (status[i] == SGR_OK) {
+                cudaError_t ce = cudaStreamWaitEvent(st, S->ev_in[i], 0);
+                status[i] = ce == cudaSuccess
+                                ? sgr::color_single_in(S->direct_mem, S->direct_cap, q->n, q->m, S->P.ro + q->rb,
+                                                       S->P.ci + q->eb, S->P.colors + q->vb, S->cfg.mode, st, &k,
+                                                       &rr)
+                                : map_err(ce);
+            }
+            q->k = k;
+            if (status[i] == SGR_OK) {  // (the coloring has finished: color_single_in synchronised st)
+                {
+                    std::lock_guard<std::mutex> lk(S->mu);
+                    host_alloc(S, q->out, q->n);
+                }
+                cudaError_t ce = cudaMemcpyAsync(q->out.ptr, S->P.colors + q->vb, (size_t)q->n * 4,
+                                                 cudaMemcpyDeviceToHost, S->copy_stream);
+                if (ce == cudaSuccess) ce = cudaEventRecord(S->ev_done[i], S->copy_stream);
+                if (ce != cudaSuccess) status[i] = map_err(ce);
+            }
+        }
+        for (size_t i = 0; i < direct.size(); ++i) {  // finish in order as the copies land
+            Request *q = direct[i];
+            if (status[i] == SGR_OK) {
+                const cudaError_t ce = cudaEventSynchronize(S->ev_done[i]);
+                if (ce != cudaSuccess) status[i] = map_err(ce);
+            }
+            std::lock_guard<std::mutex> lk(S->mu);
+            host_free(S, q->csr);
+            release_ranges(S, q);
+            S->direct_count++;
+            S->launches++;
+            finish(S, q, status[i]);
+        }
+        if (!direct.empty()) {  // every copy of the pass has landed before its ranges are reused
+            const cudaError_t ce = cudaStreamSynchronize(S->copy_stream);
+            if (ce != cudaSuccess) {
+                {
+                    std::lock_guard<std::mutex> lk(S->mu);
+                    S->fatal = map_err(ce);
+                }
+                fail_all_resident(S, map_err(ce));
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->stop = true;
+                break;
+            }
+        }
+        e = cudaSuccess;
+        if (resident == 0) continue;
         const int par = (int)(S->round & 1);
         const int G = S->G;
         for (Request *q : admitted) {  // copy the CSR into the arenas (async from pinned staging)
@@ -497,6 +592,7 @@ int sgr_server_create(const sgr_server_config *cfg, sgr_server **out) {
     if (S->cfg.staging_bytes == 0) S->cfg.staging_bytes = 1ll << 30;
     if (S->cfg.staging_bytes < 0) S->cfg.staging_bytes = 0;
     S->G = S->cfg.max_inflight > 0 ? S->cfg.max_inflight : 1024;
+    S->direct_min = S->cfg.direct_min_vertices == 0 ? 262144 : S->cfg.direct_min_vertices;
     S->device = cfg->device;
     int rc = SGR_OK;
     if (cudaSetDevice(S->device) != cudaSuccess) rc = SGR_ERR_INVALID_ARG;
@@ -511,6 +607,12 @@ int sgr_server_create(const sgr_server_config *cfg, sgr_server **out) {
     }
     if (rc == SGR_OK && cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = SGR_ERR_CUDA;
+    if (rc == SGR_OK && cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = SGR_ERR_CUDA;
+    for (int i = 0; rc == SGR_OK && i < sgr_server::kDirectPass; ++i)
+        if (cudaEventCreateWithFlags(&S->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&S->ev_done[i], cudaEventDisableTiming) != cudaSuccess)
+            rc = SGR_ERR_CUDA;
     if (rc == SGR_OK) rc = carve(S);
     if (rc == SGR_OK) {
         const long long words = S->cfg.staging_bytes / 4;
@@ -541,6 +643,11 @@ int sgr_server_create(const sgr_server_config *cfg, sgr_server **out) {
         if (S->pinned) cudaFreeHost(S->pinned);
         if (S->tab_h) cudaFreeHost(S->tab_h);
         if (S->stream) cudaStreamDestroy(S->stream);
+        if (S->copy_stream) cudaStreamDestroy(S->copy_stream);
+        for (int i = 0; i < sgr_server::kDirectPass; ++i) {
+            if (S->ev_in[i]) cudaEventDestroy(S->ev_in[i]);
+            if (S->ev_done[i]) cudaEventDestroy(S->ev_done[i]);
+        }
         delete S;
         return rc;
     }
@@ -573,17 +680,40 @@ int sgr_server_submit(sgr_server *S, int32_t n, const int32_t *ro, const int32_t
         }
         int32_t *hro = q->csr.ptr, *hci = q->csr.ptr + n + 1;
         std::memcpy(hro, ro, ((size_t)n + 1) * 4);
-        // Copy col_idx, then count ids outside [0, n) and adjacent descending
-        // pairs; rows are ascending iff every descending pair sits on a row
-        // boundary.
-        if (m) std::memcpy(hci, ci, (size_t)m * 4);
+        // Copy col_idx, counting ids outside [0, n) and adjacent descending
+        // pairs on the way; rows are ascending iff every descending pair sits
+        // on a row boundary.  Large requests are copied and checked by a few
+        // host threads at once, each over its own stretch of entries (a pair
+        // across two stretches is read from the caller's array).
         long long bad = 0, desc = 0, bnd = 0;
         const uint32_t un = (uint32_t)n;
-        for (long long i = 0; i + 1 < m; ++i) {
-            bad += (uint32_t)hci[i] >= un;
-            desc += hci[i] >= hci[i + 1];
+        auto copy_check = [&](long long i0, long long i1, long long *b_out, long long *d_out) {
+            if (i1 > i0) std::memcpy(hci + i0, ci + i0, (size_t)(i1 - i0) * 4);
+            long long b = 0, d = 0;
+            for (long long i = i0; i < i1; ++i) {
+                b += (uint32_t)ci[i] >= un;
+                if (i + 1 < m) d += ci[i] >= ci[i + 1];
+            }
+            *b_out = b;
+            *d_out = d;
+        };
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int nth = m >= (1ll << 20) ? (int)std::min(8u, std::max(1u, hw / 2)) : 1;
+        if (nth == 1) {
+            copy_check(0, m, &bad, &desc);
+        } else {
+            std::vector<long long> bs(nth, 0), ds(nth, 0);
+            std::vector<std::thread> th;
+            const long long per = (m + nth - 1) / nth;
+            for (int t = 1; t < nth; ++t)
+                th.emplace_back(copy_check, std::min(m, t * per), std::min(m, (t + 1) * per), &bs[t], &ds[t]);
+            copy_check(0, std::min(m, per), &bs[0], &ds[0]);
+            for (auto &x : th) x.join();
+            for (int t = 0; t < nth; ++t) {
+                bad += bs[t];
+                desc += ds[t];
+            }
         }
-        if (m) bad += (uint32_t)hci[m - 1] >= un;
         if (bad) return reject(SGR_ERR_INVALID_GRAPH);
         for (int32_t v = 0; v < n; ++v) {
             const int32_t a = hro[v], b = hro[v + 1];
@@ -653,6 +783,7 @@ int sgr_server_stats(sgr_server *S, sgr_server_counters *out) {
     out->hbm_bytes = (int64_t)S->dbytes;
     out->vertex_capacity = S->Vcap;
     out->entry_capacity = S->Ecap;
+    out->direct = S->direct_count;
     if (!S->lat_ms.empty()) {
         std::vector<double> v = S->lat_ms;
         std::sort(v.begin(), v.end());
@@ -684,10 +815,16 @@ int sgr_server_destroy(sgr_server *S) {
     cudaGetDevice(&prev);
     cudaSetDevice(S->device);
     if (S->stream) cudaStreamSynchronize(S->stream);
+    if (S->copy_stream) cudaStreamSynchronize(S->copy_stream);
     if (S->dmem) cudaFree(S->dmem);
     if (S->pinned) cudaFreeHost(S->pinned);
     if (S->tab_h) cudaFreeHost(S->tab_h);
     if (S->stream) cudaStreamDestroy(S->stream);
+    if (S->copy_stream) cudaStreamDestroy(S->copy_stream);
+    for (int i = 0; i < sgr_server::kDirectPass; ++i) {
+        if (S->ev_in[i]) cudaEventDestroy(S->ev_in[i]);
+        if (S->ev_done[i]) cudaEventDestroy(S->ev_done[i]);
+    }
     cudaSetDevice(prev);
     for (auto &kv : S->reqs) delete kv.second;  // their pinned ranges go with the pool
     delete S;

@@ -69,14 +69,16 @@ class Stats(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("rounds_per_launch", ctypes.c_int32), ("staging_bytes", ctypes.c_int64)]
+                ("rounds_per_launch", ctypes.c_int32), ("staging_bytes", ctypes.c_int64),
+                ("direct_min_vertices", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "failed", "pending",
                                               "resident", "launches", "rounds", "hbm_bytes",
                                               "vertex_capacity", "entry_capacity")] + \
-               [(f, ctypes.c_double) for f in ("p50_ms", "p99_ms", "mean_ms", "graphs_per_s")]
+               [(f, ctypes.c_double) for f in ("p50_ms", "p99_ms", "mean_ms", "graphs_per_s")] + \
+               [("direct", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -287,9 +289,9 @@ class Server:
     graphs, poll for their colors."""
 
     def __init__(self, hbm_budget_bytes=1 << 30, max_inflight=0, mode="det", device=0,
-                 rounds_per_launch=0, staging_bytes=0):
+                 rounds_per_launch=0, staging_bytes=0, direct_min_vertices=0):
         cfg = ServerConfig(int(hbm_budget_bytes), int(max_inflight), _mode(mode), int(device),
-                           int(rounds_per_launch), int(staging_bytes))
+                           int(rounds_per_launch), int(staging_bytes), int(direct_min_vertices))
         h = ctypes.c_void_p()
         _check(_lib.sgr_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sgr_server_create")
         self._h = h

@@ -11,6 +11,9 @@ SGR (Algorithm 7 with Algorithms 4 and 5, lower id keeps, Sect. 3.1):
 * ``serve_sizes``: eight requests of the served workload's generator mix with
   n from 1.6k to 4M (``graphgen.mix_specs(400, 1000, 4000000, 7)``, the
   indices below), all four kinds, four of them above 3M vertices.
+* ``serve_pool``: the 24 graphs the served-stream benchmark draws its
+  requests from (``graphgen.mix_specs(24, 1000, 4000000, 7)``), so that every
+  served result can be checked.
 
 For each graph: n, m, a SHA-256 of its CSR, the det color count, round count
 and the SHA-256 of the det colors (int32 little-endian).  Nothing here touches
@@ -18,7 +21,7 @@ the GPU library.  The graphs come from the seeded, integer-only generators,
 so they are the same on every machine.  The oracle runs in a process pool
 (one graph per worker, single-threaded each).
 
-    python tests/golden/make_mix_golden.py     # several minutes on 8 cores
+    python tests/golden/make_mix_golden.py     # a few minutes on 8 cores
 """
 import hashlib
 import json
@@ -35,6 +38,7 @@ import numpy as np  # noqa: E402
 BATCH = ("batch_mix(512, 1000, 200000, 0)", 512, 1000, 200000, 0)
 SERVE_SPECS = ("mix_specs(400, 1000, 4000000, 7)", 400, 1000, 4000000, 7)
 SERVE_PICK = [142, 335, 338, 249, 21, 7, 5, 4]
+POOL = ("mix_specs(24, 1000, 4000000, 7)", 24, 1000, 4000000, 7)
 
 
 def digest(a) -> str:
@@ -69,7 +73,8 @@ def main():
     batch_specs = gg.mix_specs(*BATCH[1:])
     all_specs = gg.mix_specs(*SERVE_SPECS[1:])
     serve_specs = [all_specs[i] for i in SERVE_PICK]
-    work = list(serve_specs) + list(batch_specs)
+    pool_specs = gg.mix_specs(*POOL[1:])
+    work = list(serve_specs) + list(batch_specs) + list(pool_specs)
     work_order = sorted(range(len(work)), key=lambda i: -work[i][1])  # largest first
     ctx = mp.get_context("spawn")
     t0 = time.time()
@@ -82,6 +87,8 @@ def main():
                         "rule": "low_keeps", "graphs": [by[i] for i in range(ns)]},
         "batch512": {"generator": f"graphgen.{BATCH[0]}", "rule": "low_keeps",
                      "graphs": [by[ns + i] for i in range(len(batch_specs))]},
+        "serve_pool": {"generator": f"graphgen.{POOL[0]}", "rule": "low_keeps",
+                       "graphs": [by[ns + len(batch_specs) + i] for i in range(len(pool_specs))]},
     }
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mix_digests.json")
     with open(path, "w") as f:

@@ -10,8 +10,9 @@ generators.  Here the GPU colors the same graphs
   * all 512 at once through sgr_color_batch (one persistent kernel over their
     disjoint union), and
   * the served set through the continuous-batching server, all submitted at
-    once under a 64 GB budget so that they share the device's rounds, and one
-    at a time through sgr_color,
+    once under a 64 GB budget (once with the large requests colored alone
+    between the batched launches, once with every request in the batched
+    rounds), and one at a time through sgr_color,
 
 and every graph's colors must hash to the oracle's digest (bit-exact).
 """
@@ -77,9 +78,10 @@ def _serve_graphs():
 
 
 @pytest.mark.gpu
-def test_server_sized_requests_equal_the_oracle_in_the_mix(gpu_lib):
+@pytest.mark.parametrize("direct", [0, -1], ids=["large-alone", "all-batched"])
+def test_server_sized_requests_equal_the_oracle_in_the_mix(gpu_lib, direct):
     graphs, recs = _serve_graphs()
-    with gpu_lib.Server(hbm_budget_bytes=64 << 30, mode="det") as srv:
+    with gpu_lib.Server(hbm_budget_bytes=64 << 30, mode="det", direct_min_vertices=direct) as srv:
         ids = [srv.submit(g.row_offsets, g.col_idx) for g in graphs]  # all in flight together
         for rid, g, rec in zip(ids, graphs, recs):
             colors, k = srv.poll(rid, g.n, timeout_ms=600000)

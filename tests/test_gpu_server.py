@@ -139,3 +139,30 @@ def test_server_edge_cases(gpu_lib):
     with pytest.raises(gpu_lib.SgrError):
         gpu_lib.Server(mode="fast")  # deterministic mode only
 
+
+
+def test_server_colors_large_requests_alone_between_batched_launches(gpu_lib):
+    """Requests at or above direct_min_vertices run alone on the single-graph
+    kernels (activation lists, one-CTA tail) between the batched launches of
+    the small ones; every result still equals the oracle, whatever the mix."""
+    graphs = mix(21, 18, n_lo=2000, n_hi=150000)
+    expect = [oracle.det_sgr(g) for g in graphs]
+    big = sum(g.n >= 40000 for g in graphs)
+    assert 0 < big < len(graphs)
+    with gpu_lib.Server(hbm_budget_bytes=512 << 20, rounds_per_launch=4, direct_min_vertices=40000) as srv:
+        ids = [srv.submit(g.row_offsets, g.col_idx) for g in graphs]
+        for rid, g, ref in zip(ids, graphs, expect):
+            colors, k = srv.poll(rid, g.n, timeout_ms=60000)
+            assert np.array_equal(colors, ref.colors) and k == ref.num_colors
+        st = srv.stats()
+        assert st["direct"] == big and st["completed"] == len(graphs)
+
+
+def test_server_never_alone_when_disabled(gpu_lib):
+    graphs = mix(22, 6, n_lo=100000, n_hi=200000)
+    with gpu_lib.Server(hbm_budget_bytes=1 << 30, direct_min_vertices=-1) as srv:
+        ids = [srv.submit(g.row_offsets, g.col_idx) for g in graphs]
+        for rid, g in zip(ids, graphs):
+            colors, k = srv.poll(rid, g.n, timeout_ms=60000)
+            assert np.array_equal(colors, oracle.det_sgr(g).colors)
+        assert srv.stats()["direct"] == 0
