@@ -555,7 +555,7 @@ def run_suite(lib, dev, stream, args, flush):
     return out
 
 
-def measure_batch(lib, dev, stream, name, steps, warmup, flush, rank=0, world=1):
+def measure_batch(lib, dev, stream, name, steps, warmup, flush, rank=0, world=1, autotune=False):
     """Batched workload: graphs/s of one sgr_color_batch call over the whole mix,
     against the same graphs colored by one sgr_color call each (the plain path),
     with every graph's colors checked against the oracle's digest."""
@@ -574,6 +574,9 @@ def measure_batch(lib, dev, stream, name, steps, warmup, flush, rank=0, world=1)
     def step():
         lib.sgr_color_batch(G, b.vtx_off, b.edge_off, ro, ci, colors, kk, mode, stream)
 
+    tuned = None
+    if autotune:
+        tuned = lib.sgr_autotune_batch(G, b.vtx_off, b.edge_off, ro, ci, colors, kk, mode, 3000, stream)
     for _ in range(warmup):
         flush.fill_(1)
         step()
@@ -633,7 +636,8 @@ def measure_batch(lib, dev, stream, name, steps, warmup, flush, rank=0, world=1)
            "sequential_graphs_per_s": seq_value, "speedup_vs_sequential": value / seq_value,
            "clocks": clocks, "gpu_launches": steps * 5,
            "roofline": roofline_record(st, n, m, "det", statistics.mean(kms), name, "low_keeps"),
-           "batch_slices_equal_alone": same_as_alone}
+           "batch_slices_equal_alone": same_as_alone, "tuning": lib.sgr_get_tuning(),
+           "tuning_source": "autotuned (sgr_autotune_batch, 3 s budget)" if tuned else "default"}
     if name == "batch512" and world == 1:
         gold = golden("mix_digests.json")["batch512"]["graphs"]
         bad = sum(1 for i, gr in enumerate(gold)
@@ -670,7 +674,8 @@ def run_batch(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    rec = measure_batch(lib, dev, stream, args.workload, args.steps, args.warmup, flush, rank, world)
+    rec = measure_batch(lib, dev, stream, args.workload, args.steps, args.warmup, flush, rank, world,
+                        autotune=args.autotune)
     if rank == 0:
         line = {"metric": rec.pop("metric"), "value": rec.pop("value"), "unit": rec.pop("unit"),
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

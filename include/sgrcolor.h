@@ -302,18 +302,33 @@ int sgr_validate_csr(int32_t n, const int32_t *row_offsets, const int32_t *col_i
 
 /*
  * Pick the tuning for a graph by measurement: color it (sgr_color, device
- * buffers) under a grid of candidates -- degree bound of the lane-per-vertex
- * bin {32, 16}, hub chunk size {512, 256, 1024, 2048}, CTAs per SM {all, 2},
- * best of two runs each by the kernel's event time -- until budget_ms of
- * device time is spent (0: 2000 ms; at least one candidate always runs).  The
- * fastest candidate becomes the process-wide tuning and is returned in *best
- * (HOST) with its time in *best_ms (HOST, may be NULL).  colors_out receives
- * a valid coloring.  The paper leaves autotuning out of its scope (Sect. 3.2,
- * thread coarsening).  Errors as sgr_color; the tuning is restored on error.
+ * buffers) under a grid of candidates -- hub chunk size {1024, 512, 256, 2048}
+ * x degree bound of the lane-per-vertex bin {32, 16} x CTAs per SM {all, 2},
+ * and in deterministic mode x tail hand-over size {2048, 1024, 3072} -- best of
+ * two runs each by the kernels' event time, in that order (the library default
+ * first), until budget_ms of device time is spent (0: 2000 ms; at least one
+ * candidate always runs).  The fastest candidate becomes the process-wide
+ * tuning and is returned in *best (HOST) with its time in *best_ms (HOST, may
+ * be NULL).  colors_out receives the coloring of the last candidate run (a
+ * valid coloring; in deterministic mode the same for every candidate).  The
+ * paper leaves autotuning out of its scope (Sect. 3.2, thread coarsening).
+ * The threads per CTA are fixed at 256: the tile layout of the kernels is
+ * built for it.  Errors as sgr_color; the tuning is restored on error.
  */
 int sgr_autotune(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
                  int32_t *colors_out, int mode, int32_t budget_ms, sgr_tuning *best,
                  double *best_ms, sgr_stream_t stream);
+
+/*
+ * The same for a batch: measures sgr_color_batch on the given packed graphs
+ * (arguments as in sgr_color_batch) under the candidate grid of sgr_autotune
+ * and installs the fastest tuning; colors_out and num_colors receive the last
+ * run's results.  Errors as sgr_color_batch.
+ */
+int sgr_autotune_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
+                       const int32_t *row_offsets, const int32_t *col_idx, int32_t *colors_out,
+                       int32_t *num_colors, int mode, int32_t budget_ms, sgr_tuning *best,
+                       double *best_ms, sgr_stream_t stream);
 
 /* Statistics of the last sgr_color / sgr_color_host / sgr_color_batch call
  * on this host thread. */

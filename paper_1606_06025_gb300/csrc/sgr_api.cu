@@ -843,53 +843,92 @@ int sgr_color_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
     return SGR_OK;
 }
 
-int sgr_autotune(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
-                 int32_t *colors_out, int mode, int32_t budget_ms, sgr_tuning *best,
-                 double *best_ms, sgr_stream_t stream) {
-    if (!best || !valid_mode(mode) || n < 0) return SGR_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// The autotuner's candidate grid, measured in this order until the budget is
+// spent (the library default first): degree bound of the lane-per-vertex bin,
+// hub chunk size (also the warp-per-vertex bound), CTAs per SM (0 = as many
+// as fit) and, in deterministic mode, the hand-over size of the one-CTA tail.
+// run(t) makes one coloring call under tuning t and returns its status; the
+// call's device time is read from the thread's statistics.
+template <class Run>
+int autotune_grid(int mode, int32_t budget_ms, sgr_tuning *best, double *best_ms, Run run) {
     const sgr_tuning start = current_tuning();
-    if (n == 0) {
-        *best = start;
-        if (best_ms) *best_ms = 0;
-        return SGR_OK;
-    }
-    // Candidates: degree bound of the lane-per-vertex bin, hub chunk size (also
-    // the warp-per-vertex bound) and CTAs per SM (0 = as many as fit).
+    const bool det = (mode & SGR_MODE_MASK) == SGR_MODE_DETERMINISTIC;
+    const int32_t chunks[] = {1024, 512, 256, 2048};
     const int32_t lights[] = {32, 16};
-    const int32_t chunks[] = {512, 256, 1024, 2048};
     const int32_t ctas[] = {0, 2};
+    const int32_t tails[] = {0, 1024, 3072};
+    const int ntails = det ? 3 : 1;
     const double budget = budget_ms > 0 ? budget_ms : 2000.0;
     double spent = 0, best_t = 1e300;
     sgr_tuning bt = start;
-    int32_t k = 0;
     int tried = 0;
-    for (int32_t b : ctas)
-        for (int32_t c : chunks)
-            for (int32_t l : lights) {
-                if (tried > 0 && spent > budget) continue;
-                sgr_tuning t = {l, c, b, 0, start.tail_vertices};
-                int rc = sgr_set_tuning(&t);
-                if (rc != SGR_OK) continue;
-                double tmin = 1e300;
-                for (int rep = 0; rep < 2; ++rep) {  // the first run also warms caches
-                    rc = sgr_color(n, row_offsets, col_idx, colors_out, &k, mode, stream);
-                    if (rc != SGR_OK) {
-                        sgr_set_tuning(&start);
-                        return rc;
+    for (int ti = 0; ti < ntails; ++ti)
+        for (int32_t b : ctas)
+            for (int32_t c : chunks)
+                for (int32_t l : lights) {
+                    if (tried > 0 && spent > budget) continue;
+                    sgr_tuning t = {l, c, b, start.active_lists, det ? tails[ti] : start.tail_vertices};
+                    if (sgr_set_tuning(&t) != SGR_OK) continue;
+                    double tmin = 1e300;
+                    for (int rep = 0; rep < 2; ++rep) {  // the first run also warms caches
+                        const int rc = run();
+                        if (rc != SGR_OK) {
+                            sgr_set_tuning(&start);
+                            return rc;
+                        }
+                        tmin = std::min(tmin, t_stats.device_ms);
+                        spent += t_stats.device_ms;
                     }
-                    tmin = std::min(tmin, t_stats.device_ms);
-                    spent += t_stats.device_ms;
+                    ++tried;
+                    if (tmin < best_t) {
+                        best_t = tmin;
+                        bt = t;
+                    }
                 }
-                ++tried;
-                if (tmin < best_t) {
-                    best_t = tmin;
-                    bt = t;
-                }
-            }
     sgr_set_tuning(&bt);
     *best = bt;
     if (best_ms) *best_ms = best_t;
     return SGR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sgr_autotune(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,
+                 int32_t *colors_out, int mode, int32_t budget_ms, sgr_tuning *best,
+                 double *best_ms, sgr_stream_t stream) {
+    if (!best || !valid_mode(mode) || n < 0) return SGR_ERR_INVALID_ARG;
+    if (n == 0) {
+        *best = current_tuning();
+        if (best_ms) *best_ms = 0;
+        return SGR_OK;
+    }
+    int32_t k = 0;
+    return autotune_grid(mode, budget_ms, best, best_ms, [&] {
+        return sgr_color(n, row_offsets, col_idx, colors_out, &k, mode, stream);
+    });
+}
+
+int sgr_autotune_batch(int32_t G, const int64_t *vtx_off, const int64_t *edge_off,
+                       const int32_t *row_offsets, const int32_t *col_idx, int32_t *colors_out,
+                       int32_t *num_colors, int mode, int32_t budget_ms, sgr_tuning *best,
+                       double *best_ms, sgr_stream_t stream) {
+    if (!best || !valid_mode(mode) || G < 0 || (G > 0 && (!vtx_off || !num_colors))) return SGR_ERR_INVALID_ARG;
+    if (G == 0 || vtx_off[G] == 0) {
+        *best = current_tuning();
+        if (best_ms) *best_ms = 0;
+        return sgr_color_batch(G, vtx_off, edge_off, row_offsets, col_idx, colors_out, num_colors, mode,
+                               stream);
+    }
+    return autotune_grid(mode, budget_ms, best, best_ms, [&] {
+        return sgr_color_batch(G, vtx_off, edge_off, row_offsets, col_idx, colors_out, num_colors, mode,
+                               stream);
+    });
 }
 
 int sgr_validate_csr(int32_t n, const int32_t *row_offsets, const int32_t *col_idx,

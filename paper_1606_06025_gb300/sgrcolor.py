@@ -37,7 +37,8 @@ RULES = {"low_keeps": SGR_RULE_LOW_KEEPS, "low_loses": SGR_RULE_LOW_LOSES,
          "degree": SGR_RULE_DEGREE}
 
 # every symbol include/sgrcolor.h declares (checked by the tests)
-EXPORTS = ["sgr_color", "sgr_color_noalloc", "sgr_color_host", "sgr_autotune", "sgr_color_batch", "sgr_validate_csr",
+EXPORTS = ["sgr_color", "sgr_color_noalloc", "sgr_color_host", "sgr_autotune", "sgr_autotune_batch",
+           "sgr_color_batch", "sgr_validate_csr",
            "sgr_last_stats", "sgr_last_trace", "sgr_get_tuning", "sgr_set_tuning", "sgr_release_scratch",
            "sgr_status_string", "sgr_version", "sgr_server_create", "sgr_server_submit",
            "sgr_server_poll", "sgr_server_stats", "sgr_server_destroy", "sgr_set_wait_limit",
@@ -102,6 +103,8 @@ def _load():
     lib.sgr_validate_csr.argtypes = [i32, vp, vp, pi32, vp]
     lib.sgr_autotune.argtypes = [i32, vp, vp, vp, ctypes.c_int, i32, ctypes.POINTER(Tuning),
                                  ctypes.POINTER(ctypes.c_double), vp]
+    lib.sgr_autotune_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, ctypes.c_int, i32, ctypes.POINTER(Tuning),
+                                       ctypes.POINTER(ctypes.c_double), vp]
     lib.sgr_last_stats.argtypes = [ctypes.POINTER(Stats)]
     lib.sgr_last_trace.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64)]
     lib.sgr_get_tuning.argtypes = [ctypes.POINTER(Tuning)]
@@ -216,6 +219,19 @@ def sgr_autotune(n, row_offsets, col_idx, colors_out, mode=0, budget_ms=0, strea
     _check(_lib.sgr_autotune(int(n), _addr(row_offsets), _addr(col_idx), _addr(colors_out),
                              _mode(mode), int(budget_ms), ctypes.byref(t), ctypes.byref(ms),
                              _stream(stream)), "sgr_autotune")
+    return {f: getattr(t, f) for f, _ in Tuning._fields_}, float(ms.value)
+
+
+def sgr_autotune_batch(G, vtx_off, edge_off, row_offsets, col_idx, colors_out, num_colors, mode=0,
+                       budget_ms=0, stream=None):
+    """Measure the tuning candidates on a packed batch (sgr_color_batch);
+    installs and returns the fastest as (tuning dict, device ms)."""
+    t = Tuning()
+    ms = ctypes.c_double(0)
+    _check(_lib.sgr_autotune_batch(int(G), _addr(vtx_off), _addr(edge_off), _addr(row_offsets),
+                                   _addr(col_idx), _addr(colors_out), _addr(num_colors), _mode(mode),
+                                   int(budget_ms), ctypes.byref(t), ctypes.byref(ms), _stream(stream)),
+           "sgr_autotune_batch")
     return {f: getattr(t, f) for f, _ in Tuning._fields_}, float(ms.value)
 
 

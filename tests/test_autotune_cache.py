@@ -9,3 +9,10 @@ def test_signature_buckets():
     d = autotune.signature(7_077_888, 182_041_336, 26, "det")
     assert a == b and a != c and a != d
     assert autotune.signature(0, 0, 0, "det").endswith("n0:d0:D0")
+
+
+def test_batch_signature_buckets():
+    a = autotune.batch_signature(512, 19_302_282, 390_876_132, "det")
+    b = autotune.batch_signature(600, 19_000_000, 380_000_000, "det")
+    c = autotune.batch_signature(64, 19_302_282, 390_876_132, "det")
+    assert a == b and a != c and a.startswith("batch:")
