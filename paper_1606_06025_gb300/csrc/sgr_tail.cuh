@@ -592,7 +592,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         s.tk[i] = (1ull << 32) | rank;  // on the worklist (any nonzero color)
     }
     __syncthreads();
-    unsigned long long sum_w = 0, sum_d = 0, sum_next = 0, entries = 0, sum_rescan = 0;
+    unsigned long long sum_w = 0, sum_d = 0, sum_next = 0, sum_rescan = 0;
+    unsigned work = 0;  // this thread's W-adjacency entries read, over all rounds (a statistic)
     long long trounds = 0;
     int par = 0;
     const unsigned short *al = s.al;
@@ -654,7 +655,6 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         }
         __syncthreads();
         const unsigned nq = s_nq;
-        unsigned work = 0;
         unsigned long long kdeg = 0;
         int kmax = 0;
         {  // first blocks of every unsettled vertex: kTailGroup lanes each
@@ -767,15 +767,15 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
                 if (lane == 0 && warp % wpk == 0) work += (unsigned)n;
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            work += __shfl_xor_sync(kFull, work, o);
-            kdeg += __shfl_xor_sync(kFull, kdeg, o);
-            kmax = max(kmax, __shfl_xor_sync(kFull, kmax, o));
-        }
-        if (lane == 0) {
-            if (work) atomicAdd(&s_work, (unsigned long long)work);
-            if (kdeg) atomicAdd(&s_kdeg, kdeg);
-            if (kmax) atomicMax(&s_kmax, kmax);
+        if (__any_sync(kFull, kdeg != 0 || kmax != 0)) {  // only warps that committed keepers
+            for (int o = 16; o > 0; o >>= 1) {
+                kdeg += __shfl_xor_sync(kFull, kdeg, o);
+                kmax = max(kmax, __shfl_xor_sync(kFull, kmax, o));
+            }
+            if (lane == 0) {
+                if (kdeg) atomicAdd(&s_kdeg, kdeg);
+                if (kmax) atomicMax(&s_kmax, kmax);
+            }
         }
         __syncthreads();
         // ---- keepers leave the worklist (judged on this round's colors: only now)
@@ -798,11 +798,10 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             const unsigned left = s_alive - nk;
             sum_next += left;
             sum_rescan += nq;
-            entries += s_work;
             s_alive = left;
             s_D -= s_kdeg;
             s_nkeep = 0;
-            s_kdeg = s_work = 0;
+            s_kdeg = 0;
             s_nq = s_nlq = 0;
             s_nnext = 0;
             if (r <= kTraceCap) {
@@ -813,12 +812,14 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         ++trounds;
         __syncthreads();
     }
+    unsigned long long wsum = work;
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(kFull, wsum, o);
+    if (lane == 0 && wsum) atomicAdd(&ctr->tail_entries, wsum);
     if (tid == 0) {
         if (s_kmax) atomicMax(&ctr->kmax, s_kmax);
         atomicAdd(&ctr->sum_w, sum_w);
         atomicAdd(&ctr->sum_d, sum_d);
         atomicAdd(&ctr->sum_next, sum_next);
-        atomicAdd(&ctr->tail_entries, entries);
         atomicAdd(&ctr->sum_rescan, sum_rescan);
         ctr->tail_rounds = trounds;
         if (ok) {
