@@ -354,6 +354,10 @@ __device__ __forceinline__ TailSmem tail_smem(unsigned char *raw, int T) {
     return s;
 }
 
+// s.wit of a vertex that kept its color this round: it leaves the worklist in
+// the next round's FirstFit pass.
+constexpr short kTailKept = -2;
+
 __device__ __forceinline__ unsigned tk_color(unsigned long long x) { return (unsigned)(x >> 32); }
 __device__ __forceinline__ unsigned tk_rank(unsigned long long x) { return (unsigned)x; }
 
@@ -392,7 +396,7 @@ __device__ __forceinline__ bool tail_conflict(const TailSmem &s, int mode, int u
 // 16-byte block (8 entries) per lane and step, blocks in scan order by lane,
 // kTailGroupSteps steps at most; a warp scans 32 / kTailGroup vertices at a
 // time.  Vertices whose range goes on past these blocks without a conflict
-// are finished by whole warps, segment by segment (tail_scan_segment).
+// are finished by whole warps, segment by segment (tail_scan_segments).
 constexpr int kTailGroup = 8;
 constexpr int kTailGroupSteps = 1;
 constexpr int kTailGroupBlocks = kTailGroup * kTailGroupSteps;
@@ -414,12 +418,13 @@ __device__ __forceinline__ int tail_block_hit(const TailSmem &s, int mode, const
     return hit;
 }
 
-// Warp scan of segment j (128 blocks, four per lane, all loads in flight) of
-// the rest of i's range, from s.res[i] on in scan order.  Returns the
-// nearest conflicting winner in the segment as (distance from the start of
-// the rest << 16 | local id), the same on all lanes, or 0xffffffff.
-__device__ __forceinline__ unsigned tail_scan_segment(const Params &p, const TailSmem &s, int mode, int i,
-                                                      int j, unsigned &scanned) {
+// Warp scan of four segments of 32 blocks (one block a lane, all four loads
+// in flight) of the rest of i's range, from s.res[i] on in scan order: the
+// segments j0, j0 + step, j0 + 2 step and j0 + 3 step.  Returns the nearest
+// conflicting winner among them as (distance from the start of the rest << 16
+// | local id), the same on all lanes, or 0xffffffff.
+__device__ __forceinline__ unsigned tail_scan_segments(const Params &p, const TailSmem &s, int mode, int i,
+                                                       int j0, int step, unsigned &scanned) {
     const int lane = threadIdx.x & 31;
     const TailRange rg0 = tail_range(s, mode, i);
     const bool down = mode == 0;
@@ -431,11 +436,11 @@ __device__ __forceinline__ unsigned tail_scan_segment(const Params &p, const Tai
     int bb[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-        const int d = j * 128 + t * 32 + lane;  // distance in blocks from the start
+        const int d = (j0 + t * step) * 32 + lane;  // distance in blocks from the start
         bb[t] = down ? bh - d : bl + d;
         x[t] = (hi > lo && bb[t] >= bl && bb[t] <= bh) ? ld_run(run + bb[t]) : make_uint4(0, 0, 0, 0);
     }
-    unsigned best = 0xffffffffu;
+    unsigned best = 0xffffffffu, n = 0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         if (hi <= lo || bb[t] < bl || bb[t] > bh) continue;
@@ -443,6 +448,7 @@ __device__ __forceinline__ unsigned tail_scan_segment(const Params &p, const Tai
         for (int k = 0; k < 8; ++k) {
             const int pos = 8 * bb[t] + k;
             if (pos < lo || pos >= hi) continue;
+            ++n;
             const int u = tail_elem(x[t], k);
             if (tail_conflict(s, mode, u, tk_color(me), tk_rank(me))) {
                 const unsigned dist = (unsigned)(down ? hi - 1 - pos : pos - lo);
@@ -450,7 +456,7 @@ __device__ __forceinline__ unsigned tail_scan_segment(const Params &p, const Tai
             }
         }
     }
-    if (lane == 0) scanned += (unsigned)max(0, min(hi - lo - j * 1024, 1024));
+    scanned += n;
     return __reduce_min_sync(kFull, best);
 }
 
@@ -461,39 +467,52 @@ __device__ __forceinline__ int tail_rest_blocks(const TailSmem &s, int mode, int
     return hi > lo ? ((hi - 1) >> 3) - (lo >> 3) + 1 : 0;
 }
 
-// Drop the final vertices from i's run, in place and in order (one warp, 32
-// blocks a step; every write lands below every later read), and recount the
-// entries below the vertex.
+// Drop the final vertices from i's run, in place and in order, and recount
+// the entries below the vertex.  One warp, 128 blocks a step with all their
+// loads in flight: a step writes only below its own first block + 128, and
+// the next step reads from there on.
 __device__ __forceinline__ void tail_compact_run(const Params &p, const TailSmem &s, int i) {
     const int lane = threadIdx.x & 31;
     unsigned short *run = p.tadj + s.off[i];
     const int n = s.cnt[i], lo_old = s.low[i], nb = (n + 7) >> 3;
     unsigned put = 0, low = 0;
-    for (int b0 = 0; b0 < nb; b0 += 32) {
-        const int b = b0 + lane;
-        const uint4 x = b < nb ? ld_run(reinterpret_cast<const uint4 *>(run) + b) : make_uint4(0, 0, 0, 0);
-        unsigned keep = 0, kl = 0;
+    for (int b0 = 0; b0 < nb; b0 += 128) {
+        uint4 x[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int pos = 8 * b + k;
-            if (b < nb && pos < n && tk_color(s.tk[tail_elem(x, k)]) != 0) {
-                keep |= 1u << k;
-                kl += pos < lo_old ? 1u : 0u;
+        for (int t = 0; t < 4; ++t) {
+            const int b = b0 + 32 * t + lane;
+            x[t] = b < nb ? ld_run(reinterpret_cast<const uint4 *>(run) + b) : make_uint4(0, 0, 0, 0);
+        }
+        unsigned keep[4], kl = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int b = b0 + 32 * t + lane;
+            keep[t] = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int pos = 8 * b + k;
+                if (b < nb && pos < n && tk_color(s.tk[tail_elem(x[t], k)]) != 0) {
+                    keep[t] |= 1u << k;
+                    kl += pos < lo_old ? 1u : 0u;
+                }
             }
         }
-        const unsigned c = __popc(keep);
-        unsigned incl = c;
+        __syncwarp();  // every lane has read its blocks before any write
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
+        for (int t = 0; t < 4; ++t) {
+            const unsigned c = __popc(keep[t]);
+            unsigned incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
+            }
+            unsigned at = put + incl - c;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if ((keep[t] >> k) & 1u) run[at++] = (unsigned short)tail_elem(x[t], k);
+            put += __shfl_sync(kFull, incl, 31);
         }
-        unsigned at = put + incl - c;
-        __syncwarp();  // every lane has read its block before any write
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if ((keep >> k) & 1u) run[at++] = (unsigned short)tail_elem(x, k);
-        put += __shfl_sync(kFull, incl, 31);
         low += __reduce_add_sync(kFull, kl);
         __syncwarp();
     }
@@ -511,7 +530,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
     const int T = p.tail_max;
     const TailSmem s = tail_smem(s_raw, T);
     __shared__ unsigned s_nq, s_nlq, s_nfb, s_alive, s_nkeep, s_nnext, s_compact_at;
-    __shared__ unsigned long long s_D, s_kdeg, s_work;
+    __shared__ unsigned long long s_D, s_kdeg, s_kdegr, s_work, s_nres;
     __shared__ int s_kmax;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kTailThreads / 32;
     const int nT = (int)__ldcg(&ctr->tail_n);
@@ -592,42 +611,68 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         s.tk[i] = (1ull << 32) | rank;  // on the worklist (any nonzero color)
     }
     __syncthreads();
-    unsigned long long sum_w = 0, sum_d = 0, sum_next = 0, sum_rescan = 0;
-    unsigned work = 0;  // this thread's W-adjacency entries read, over all rounds (a statistic)
+    // Per-thread statistics, reduced once after the last round: keepers'
+    // degrees (K) and the same weighted by the local round they kept in (J),
+    // so that sum over rounds of D_r = R D_0 - ((R - 1) K - J); unsettled
+    // vertices (rescans); largest color; W-adjacency entries read.
+    unsigned long long kdeg = 0, kdegr = 0, nres = 0;
+    int kmax = 0;
+    unsigned work = 0;
+    unsigned long long sum_w = 0, sum_next = 0;  // thread 0
     long long trounds = 0;
     int par = 0;
-    const unsigned short *al = s.al;
+    unsigned lprev = (unsigned)nT;  // length of the list this round's FirstFit pass reads
     bool ok = true;
+    const unsigned lt = lanemask_lt();
     for (;; ++r) {
         const unsigned alive = s_alive;
         if (alive == 0) break;
-        if (alive <= s_compact_at) {  // most of the worklist has gone: drop it from the runs
-            for (unsigned k = warp; k < alive; k += nwarps) tail_compact_run(p, s, al[k]);
-            __syncthreads();
-            if (tid == 0) s_compact_at = alive / 2;
-        }
         if (r > p.max_rounds) {
             if (tid == 0) raise_error(p, kErrNoConvergence);
             ok = false;
             break;
         }
         if (tid == 0) {
+            // the previous round's counters have been read by every thread
+            // (before the round barrier), and nothing adds to them before
+            // this round's first barrier
+            s_nkeep = 0;
+            s_nlq = 0;
+            s_nq = 0;
             sum_w += alive;
-            sum_d += s_D;
             if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)alive;
         }
-        // ---- FirstFit from the bitmaps
-        for (unsigned k = tid; k < alive; k += kTailThreads) {
-            const int i = al[k];
-            const unsigned long long t = s.tk[i];
-            unsigned c = 0;
+        // ---- FirstFit from the bitmaps.  The previous round's keepers leave
+        // the worklist here (their tentative color becomes 0), and the others
+        // form this round's list, appended a warp at a time.
+        const unsigned short *al_prev = s.al + par * T;
+        unsigned short *al = s.al + (par ^ 1) * T;
+        par ^= 1;
+        for (unsigned k0 = (unsigned)warp * 32; k0 < lprev; k0 += kTailThreads) {
+            const unsigned k = k0 + lane;
+            const int i = k < lprev ? (int)al_prev[k] : -1;
+            bool stay = false;
+            if (i >= 0) {
+                const unsigned long long t = s.tk[i];
+                if (s.wit[i] == kTailKept) {
+                    s.tk[i] = (unsigned long long)tk_rank(t);
+                } else {
+                    stay = true;
+                    unsigned c = 0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const unsigned wv = s.bits[j * T + i];
-                if (c == 0 && ~wv) c = (unsigned)(j * 32 + __ffs(~wv));
+                    for (int j = 0; j < 8; ++j) {
+                        const unsigned wv = s.bits[j * T + i];
+                        if (c == 0 && ~wv) c = (unsigned)(j * 32 + __ffs(~wv));
+                    }
+                    if (c == 0) s.q[atomicAdd(&s_nfb, 1u)] = (unsigned short)i;  // 256 colors in use
+                    s.tk[i] = ((unsigned long long)(c ? c : 1u) << 32) | tk_rank(t);
+                }
             }
-            if (c == 0) s.q[atomicAdd(&s_nfb, 1u)] = (unsigned short)i;  // 256 colors in use
-            s.tk[i] = ((unsigned long long)(c ? c : 1u) << 32) | tk_rank(t);
+            const unsigned m = __ballot_sync(kFull, stay);
+            unsigned at = 0;
+            if (lane == 0 && m) at = atomicAdd(&s_nnext, (unsigned)__popc(m));
+            at = __shfl_sync(kFull, at, 0);
+            if (stay) al[at + __popc(m & lt)] = (unsigned short)i;
         }
         __syncthreads();
         if (s_nfb) {  // full bitmaps: first fit over the final colors of the whole row
@@ -643,30 +688,45 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             __syncthreads();
             if (tid == 0) s_nfb = 0;
         }
+        if (alive <= s_compact_at) {  // most of the worklist has gone: drop it from the runs
+            for (unsigned k = warp; k < alive; k += nwarps) tail_compact_run(p, s, al[k]);
+            __syncthreads();
+            if (tid == 0) s_compact_at = alive / 2;
+        }
         if (tid == 0 && r <= kTraceCap)
             p.trace[kTraceFields * (r - 1) + 1] = (long long)(globaltimer() - t0);
-        // ---- ConflictResolve: the witness first, a scan of the run if it does not settle
-        for (unsigned k = tid; k < alive; k += kTailThreads) {
-            const int i = al[k];
-            const unsigned c = tk_color(s.tk[i]);
-            const int w = s.wit[i];
-            if (w >= 0 && tk_color(s.tk[w]) == c) continue;  // loses again, to the same neighbour
-            s.q[atomicAdd(&s_nq, 1u)] = (unsigned short)i;
+        // ---- ConflictResolve: the witness first (a vertex that loses again
+        // to the same neighbour is settled by one read), then a scan of the
+        // run for the others, kTailGroup lanes a vertex
+        for (unsigned k0 = (unsigned)warp * 32; k0 < alive; k0 += kTailThreads) {
+            const unsigned k = k0 + lane;
+            const int i = k < alive ? (int)al[k] : -1;
+            bool uns = false;
+            if (i >= 0) {
+                const int w = s.wit[i];
+                uns = !(w >= 0 && tk_color(s.tk[w]) == tk_color(s.tk[i]));
+            }
+            const unsigned um = __ballot_sync(kFull, uns);
+            unsigned at = 0;
+            if (lane == 0 && um) {
+                at = atomicAdd(&s_nq, (unsigned)__popc(um));
+                nres += (unsigned)__popc(um);
+            }
+            at = __shfl_sync(kFull, at, 0);
+            if (uns) s.q[at + __popc(um & lt)] = (unsigned short)i;
         }
         __syncthreads();
         const unsigned nq = s_nq;
-        unsigned long long kdeg = 0;
-        int kmax = 0;
         {  // first blocks of every unsettled vertex: kTailGroup lanes each
             constexpr int kPerWarp = 32 / kTailGroup;
             const int g = lane / kTailGroup, gl = lane % kTailGroup;
             const unsigned gmask = ((1u << kTailGroup) - 1u) << (g * kTailGroup);
-            for (unsigned base = warp * kPerWarp; base < nq; base += nwarps * kPerWarp) {
+            const bool down = mode == 0;
+            for (unsigned base = (unsigned)warp * kPerWarp; base < nq; base += (unsigned)nwarps * kPerWarp) {
                 const unsigned idx = base + g;
                 const bool act = idx < nq;
                 const int i = act ? (int)s.q[idx] : 0;
                 const TailRange rg = act ? tail_range(s, mode, i) : TailRange{0, 0};
-                const bool down = mode == 0;
                 const unsigned long long me = s.tk[i];
                 const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + s.off[i]);
                 const int bl = rg.lo >> 3, bh = rg.hi > rg.lo ? (rg.hi - 1) >> 3 : bl - 1;
@@ -693,27 +753,29 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
                     } else if (nblk <= kTailGroupBlocks) {  // no winner with its color: keeps it
                         const unsigned c = tk_color(me);
                         s.kq[atomicAdd(&s_nkeep, 1u)] = (unsigned short)i;
+                        s.wit[i] = kTailKept;
                         __stcg(p.colors + s.vid[i], (int)c);
                         kmax = max(kmax, (int)c);
                         kdeg += (unsigned long long)s.deg[i];
+                        kdegr += (unsigned long long)s.deg[i] * (unsigned long long)trounds;
                     } else {  // the range goes on: a warp finishes it
                         s.res[i] = (unsigned short)(down ? 8 * (bh - kTailGroupBlocks + 1) : 8 * (bl + kTailGroupBlocks));
-                        const unsigned k = atomicAdd(&s_nlq, 1u);
-                        s.lq[k] = (unsigned short)i;
-                        s.lbest[k] = 0xffffffffu;
+                        const unsigned q = atomicAdd(&s_nlq, 1u);
+                        s.lq[q] = (unsigned short)i;
+                        s.lbest[q] = 0xffffffffu;
                     }
                 }
             }
         }
         __syncthreads();
         const unsigned nlq = s_nlq;
-        if (nlq) {  // the rest of long scans: segments of 1024 entries, 32 / nlq warps per vertex
+        if (nlq) {  // the rest of long scans: 32-block segments over 32 / nlq warps per vertex
             const unsigned wpe = max(1u, (unsigned)nwarps / nlq), stride = (unsigned)nwarps / wpe;
             for (unsigned k = warp / wpe; k < nlq && warp / wpe < stride; k += stride) {
                 const int i = s.lq[k];
-                const int nb = tail_rest_blocks(s, mode, i);
-                for (int j = warp % wpe; j * 128 < nb; j += wpe) {
-                    const unsigned b = tail_scan_segment(p, s, mode, i, j, work);
+                const int nseg = (tail_rest_blocks(s, mode, i) + 31) >> 5;
+                for (int j0 = (int)(warp % wpe); j0 < nseg; j0 += 4 * (int)wpe) {
+                    const unsigned b = tail_scan_segments(p, s, mode, i, j0, (int)wpe, work);
                     if (b != 0xffffffffu) {  // the nearer segments are other warps' or scanned already
                         if (lane == 0) atomicMin(s.lbest + k, b);
                         break;
@@ -729,15 +791,19 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
                 } else {
                     const unsigned c = tk_color(s.tk[i]);
                     s.kq[atomicAdd(&s_nkeep, 1u)] = (unsigned short)i;
+                    s.wit[i] = kTailKept;
                     __stcg(p.colors + s.vid[i], (int)c);
                     kmax = max(kmax, (int)c);
                     kdeg += (unsigned long long)s.deg[i];
+                    kdegr += (unsigned long long)s.deg[i] * (unsigned long long)trounds;
                 }
             }
         }
         __syncthreads();
-        // ---- keepers record their colors at their W-neighbours: segments of
-        // 128 blocks (four per lane, all loads in flight), 32 / nk warps per keeper
+        // ---- keepers record their colors at their W-neighbours: 32-block
+        // segments over 32 / nk warps per keeper, four segments a warp with all
+        // loads in flight.  Their tentative colors stay until the next FirstFit
+        // pass.
         const unsigned nk = s_nkeep;
         if (nk) {
             const unsigned wpk = max(1u, (unsigned)nwarps / nk), stride = (unsigned)nwarps / wpk;
@@ -748,17 +814,17 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
                 unsigned *plane = s.bits + (size_t)((c - 1) >> 5) * T;
                 const unsigned bit = 1u << ((c - 1) & 31);
                 const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + s.off[i]);
-                const int n = s.cnt[i], nb = (n + 7) >> 3;
-                for (int b0 = (int)(warp % wpk) * 128; b0 < nb; b0 += (int)wpk * 128) {
+                const int n = s.cnt[i], nb = (n + 7) >> 3, nseg = (nb + 31) >> 5;
+                for (int j0 = (int)(warp % wpk); j0 < nseg; j0 += 4 * (int)wpk) {
                     uint4 x[4];
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        const int b = b0 + t * 32 + lane;
+                        const int b = (j0 + t * (int)wpk) * 32 + lane;
                         x[t] = b < nb ? ld_run(run + b) : make_uint4(0, 0, 0, 0);
                     }
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        const int b = b0 + t * 32 + lane;
+                        const int b = (j0 + t * (int)wpk) * 32 + lane;
 #pragma unroll
                         for (int kk = 0; kk < 8; ++kk)
                             if (b < nb && 8 * b + kk < n) atomicOr(plane + tail_elem(x[t], kk), bit);
@@ -767,60 +833,48 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
                 if (lane == 0 && warp % wpk == 0) work += (unsigned)n;
             }
         }
-        if (__any_sync(kFull, kdeg != 0 || kmax != 0)) {  // only warps that committed keepers
-            for (int o = 16; o > 0; o >>= 1) {
-                kdeg += __shfl_xor_sync(kFull, kdeg, o);
-                kmax = max(kmax, __shfl_xor_sync(kFull, kmax, o));
-            }
-            if (lane == 0) {
-                if (kdeg) atomicAdd(&s_kdeg, kdeg);
-                if (kmax) atomicMax(&s_kmax, kmax);
-            }
-        }
-        __syncthreads();
-        // ---- keepers leave the worklist (judged on this round's colors: only now)
-        for (unsigned k = tid; k < nk; k += kTailThreads) {
-            const int i = s.kq[k];
-            s.tk[i] = (unsigned long long)tk_rank(s.tk[i]);
-        }
-        __syncthreads();
-        if (nk) {  // the next round's list: the vertices still on the worklist
-            unsigned short *nal = s.al + (par ^ 1) * T;
-            for (unsigned k = tid; k < alive; k += kTailThreads) {
-                const int i = al[k];
-                if (tk_color(s.tk[i]) != 0) nal[atomicAdd(&s_nnext, 1u)] = (unsigned short)i;
-            }
-            par ^= 1;
-            al = s.al + par * T;
-        }
-        __syncthreads();  // every thread has read the round's counters
         if (tid == 0) {
-            const unsigned left = s_alive - nk;
+            const unsigned left = alive - nk;
             sum_next += left;
-            sum_rescan += nq;
             s_alive = left;
-            s_D -= s_kdeg;
-            s_nkeep = 0;
-            s_kdeg = 0;
-            s_nq = s_nlq = 0;
-            s_nnext = 0;
+            s_nnext = 0;  // every append of this round came before its first barrier
             if (r <= kTraceCap) {
                 p.trace[kTraceFields * (r - 1) + 2] = (long long)(globaltimer() - t0);
                 p.trace[kTraceFields * (r - 1) + 3] = (long long)nq;
             }
         }
+        lprev = alive;
         ++trounds;
-        __syncthreads();
+        __syncthreads();  // bitmaps and the counters of the next round are complete
     }
+    // ---- statistics of all rounds: one reduction
     unsigned long long wsum = work;
-    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(kFull, wsum, o);
-    if (lane == 0 && wsum) atomicAdd(&ctr->tail_entries, wsum);
+    for (int o = 16; o > 0; o >>= 1) {
+        wsum += __shfl_xor_sync(kFull, wsum, o);
+        kdeg += __shfl_xor_sync(kFull, kdeg, o);
+        kdegr += __shfl_xor_sync(kFull, kdegr, o);
+        nres += __shfl_xor_sync(kFull, nres, o);
+        kmax = max(kmax, __shfl_xor_sync(kFull, kmax, o));
+    }
+    if (tid == 0) s_kdeg = s_kdegr = s_work = s_nres = 0;
+    __syncthreads();
+    if (lane == 0) {
+        if (wsum) atomicAdd(&s_work, wsum);
+        if (kdeg) atomicAdd(&s_kdeg, kdeg);
+        if (kdegr) atomicAdd(&s_kdegr, kdegr);
+        if (nres) atomicAdd(&s_nres, nres);
+        if (kmax) atomicMax(&s_kmax, kmax);
+    }
+    __syncthreads();
     if (tid == 0) {
+        const unsigned long long R = (unsigned long long)trounds;
+        const unsigned long long sum_d = R ? R * s_D - ((R - 1) * s_kdeg - s_kdegr) : 0;
+        if (s_work) atomicAdd(&ctr->tail_entries, s_work);
         if (s_kmax) atomicMax(&ctr->kmax, s_kmax);
         atomicAdd(&ctr->sum_w, sum_w);
         atomicAdd(&ctr->sum_d, sum_d);
         atomicAdd(&ctr->sum_next, sum_next);
-        atomicAdd(&ctr->sum_rescan, sum_rescan);
+        atomicAdd(&ctr->sum_rescan, s_nres);
         ctr->tail_rounds = trounds;
         if (ok) {
             ctr->rounds = r - 1;
