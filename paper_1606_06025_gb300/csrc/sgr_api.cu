@@ -216,6 +216,7 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     if (zero_bytes) *zero_bytes = j.fast ? zero_fast : off;
     int32_t *lowdeg = (int32_t *)take((size_t)j.n * 4);
     int32_t *witness = (int32_t *)take((size_t)j.n * 4);
+    int32_t *wold = (int32_t *)take(j.fast ? 16 : (size_t)j.n * 16);
     int32_t *sw = (int32_t *)take(sp.hub_max * 4);
     unsigned *scb = (unsigned *)take(sp.hub_max * 4);
     long long *trace = (long long *)take(sizeof(long long) * sgr::kTraceCap * sgr::kTraceFields);
@@ -296,6 +297,7 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         p->np = np;
         p->lowdeg = lowdeg;
         p->witness = witness;
+        p->wold = wold;
         p->sw = sw;
         p->scb = scb;
         p->ctr = ctr;

@@ -17,6 +17,8 @@
 //                        once a neighbour of v has committed color c (c <= 256).
 //   lowdeg[n]            det mode: entries below v in its (ascending) row.
 //   witness[n]           det mode: the neighbour that beat v last time, or -1.
+//   wold[4n]             det mode: the four before it (16 bytes a vertex),
+//                        most recent first, -1 where there is none.
 //   hub scatter list     det mode: hubs committed this round (slot + chunk
 //                        base), whose colors are scattered at the next round.
 //   activation lists     det mode al/am/ah(+acb), by parity: the worklist
@@ -148,6 +150,7 @@ struct Params {
     long long np;              // plane stride (>= n, multiple of 64)
     int32_t *lowdeg;           // det
     int32_t *witness;          // det: the neighbour that last beat v, or -1
+    int32_t *wold;             // det: [4n] the four neighbours that beat v before it, or -1
     int32_t *al[2];            // det: activation lists (light, medium, hub slots + chunk bases)
     int32_t *am[2];
     int32_t *ah[2];

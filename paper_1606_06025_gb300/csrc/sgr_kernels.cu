@@ -587,6 +587,94 @@ __device__ void flush_push(const Params &p, ListSet L) {
     __syncthreads();
 }
 
+// ------------------------------------------------------------ det: witness slots
+//
+// Five witness slots per vertex: witness[v] (slot 0) holds the neighbour that
+// beat v last time, wold[v] (16 bytes) the four before it, most recent first,
+// -1 where there is none.  Every slot holds -1 or a neighbour that wins
+// against v under the rule, so whichever slot's vertex holds v's tentative
+// color magnitude in the same round settles v's loss.  Medium vertices and
+// hubs on whole worklists check and keep all five (kMulti); light vertices,
+// whose rescans are short, and the rounds on the activation lists, which
+// track slot 0 as the witness whose change activates a dependent, use slot 0
+// only.
+
+__device__ __forceinline__ int mag(int x) { return x < 0 ? -x : x; }
+
+struct Wit {
+    int32_t w0;  // slot 0
+    int4 o;      // slots 1-4
+};
+
+__device__ __forceinline__ Wit wit_none() { return Wit{-1, make_int4(-1, -1, -1, -1)}; }
+
+__device__ __forceinline__ Wit wit_load(const Params &p, int32_t v) {
+    return Wit{__ldcg(p.witness + v), __ldcg(reinterpret_cast<const int4 *>(p.wold) + v)};
+}
+
+__device__ __forceinline__ int32_t wit_first(const Params &p, int32_t v) { return __ldcg(p.witness + v); }
+
+__device__ __forceinline__ void wit_reset(const Params &p, int32_t v) {
+    p.witness[v] = -1;
+    reinterpret_cast<int4 *>(p.wold)[v] = make_int4(-1, -1, -1, -1);
+}
+
+// Make f v's latest witness.  all: keep the older ones too (w: v's slots;
+// f's old slot, or else the oldest, is dropped); otherwise only slot 0.
+__device__ __forceinline__ void wit_record(const Params &p, int32_t v, int32_t f, const Wit &w, bool all) {
+    if (!all) {
+        __stcg(p.witness + v, f);
+        return;
+    }
+    if (f == w.w0) return;
+    const int4 o = w.o;
+    int4 n;
+    if (f == o.x)
+        n = make_int4(w.w0, o.y, o.z, o.w);
+    else if (f == o.y)
+        n = make_int4(w.w0, o.x, o.z, o.w);
+    else if (f == o.z)
+        n = make_int4(w.w0, o.x, o.y, o.w);
+    else
+        n = make_int4(w.w0, o.x, o.y, o.z);
+    __stcg(p.witness + v, f);
+    __stcg(reinterpret_cast<int4 *>(p.wold) + v, n);
+}
+
+// The first slot (0-4) of w whose vertex holds magnitude c (c >= 1), or -1;
+// the five colors are loaded together.
+__device__ __forceinline__ int wit_match(const Params &p, const Wit &w, int c) {
+    const int c0 = w.w0 >= 0 ? __ldcg(p.colors + w.w0) : 0;
+    const int c1 = w.o.x >= 0 ? __ldcg(p.colors + w.o.x) : 0;
+    const int c2 = w.o.y >= 0 ? __ldcg(p.colors + w.o.y) : 0;
+    const int c3 = w.o.z >= 0 ? __ldcg(p.colors + w.o.z) : 0;
+    const int c4 = w.o.w >= 0 ? __ldcg(p.colors + w.o.w) : 0;
+    return mag(c0) == c ? 0 : mag(c1) == c ? 1 : mag(c2) == c ? 2 : mag(c3) == c ? 3 : mag(c4) == c ? 4 : -1;
+}
+
+__device__ __forceinline__ int32_t wit_slot(const Wit &w, int q) {
+    return q == 0 ? w.w0 : q == 1 ? w.o.x : q == 2 ? w.o.y : q == 3 ? w.o.z : w.o.w;
+}
+
+// During FirstFit (bitmaps fixed): does worklist vertex w pick color c
+// (1..256)?  Yes iff colors 1..c-1 are all forbidden for w and c is not; the
+// bitmap words up to c's are loaded together.
+__device__ __forceinline__ bool picks_color(const Params &p, int32_t w, int c) {
+    const int P = (c - 1) >> 5, b = (c - 1) & 31;
+    unsigned pl[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) pl[j] = j <= P ? __ldcg(p.bm + (size_t)j * p.np + w) : 0u;
+    bool full = true;
+    unsigned x = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j < P) full = full && pl[j] == 0xffffffffu;
+        if (j == P) x = pl[j];
+    }
+    const unsigned low = b ? (0xffffffffu >> (32 - b)) : 0u;  // colors below c in its word
+    return full && (x & low) == low && !((x >> b) & 1u);
+}
+
 // ------------------------------------------------------------ det: FirstFit with witness split
 //
 // During FirstFit every bitmap is fixed, so a vertex can compute the
@@ -645,7 +733,7 @@ __device__ __forceinline__ void det_assign_lane(const Params &p, const bool (&ac
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         w0[u] = act[u] ? __ldcg(p.bm + v[u]) : 0u;
-        wit[u] = act[u] ? __ldcg(p.witness + v[u]) : -1;
+        wit[u] = act[u] ? wit_first(p, v[u]) : -1;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -737,8 +825,29 @@ __device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64
             row_of<kBatched>(p, v[0], rs, re, vb);
             ld = __ldcg(p.lowdeg + v[0]);
         }
+        const Wit wv = act[0] ? wit_load(p, v[0]) : wit_none();
         int c[1];
         det_assign_lane<kBatched, 1>(p, act, v, c, settled);
+        if (act[0] && !settled[0] && c[0] >= 1 && c[0] <= 256) {
+            // the older witnesses, checked against c from their bitmaps (one
+            // trip for all of them): a hub they settle needs no work items
+            const int32_t q[4] = {wv.o.x, wv.o.y, wv.o.z, wv.o.w};
+            int cq[4];
+            bool pk[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                cq[k] = q[k] >= 0 ? __ldcg(p.colors + q[k]) : 0;
+                pk[k] = q[k] >= 0 && picks_color(p, q[k], c[0]);
+            }
+            int hit = -1;
+#pragma unroll
+            for (int k = 3; k >= 0; --k)
+                if (pk[k] && cq[k] < 0) hit = k;
+            if (hit >= 0) {
+                settled[0] = true;
+                wit_record(p, v[0], q[hit], wv, true);
+            }
+        }
         if (act[0]) {
             const unsigned cb = __ldcg(p.hcb[par] + idx);
             const unsigned nchunks = (idx + 1 < cnt ? __ldcg(p.hcb[par] + idx + 1) : nch) - cb;
@@ -801,7 +910,7 @@ __device__ __forceinline__ void push_dependents_lane(const Params &p, int32_t y,
                 const long long i = ((q0 + k) << 2) + j;
                 z[k][j] = vb + elem(x[k], j);
                 const bool ok = i >= a && i < b && (unsigned)z[k][j] < (unsigned)p.n;
-                wz[k][j] = ok ? __ldcg(p.witness + z[k][j]) : -1;
+                wz[k][j] = ok ? wit_first(p, z[k][j]) : -1;
             }
 #pragma unroll
         for (int k = 0; k < 4; ++k)
@@ -827,7 +936,7 @@ __device__ __forceinline__ void push_dependents_warp(const Params &p, int32_t y,
             const long long i = (q << 2) + k;
             z[k] = vb + elem(x, k);
             const bool ok = i >= a && i < b && (unsigned)z[k] < (unsigned)p.n;
-            wz[k] = ok ? __ldcg(p.witness + z[k]) : -1;
+            wz[k] = ok ? wit_first(p, z[k]) : -1;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k)
@@ -941,8 +1050,6 @@ __device__ void front_assign_hubs(const Params &p, int par, unsigned long long h
 // a same-round worklist vertex: every final color of a neighbour was avoided
 // by v's FirstFit.  So the neighbour that beat v in an earlier round (its
 // witness) settles a repeat loss with one read; otherwise v scans its row.
-
-__device__ __forceinline__ int mag(int x) { return x < 0 ? -x : x; }
 
 // Lane-level scan of v's row for a conflict; returns the conflicting
 // neighbour or -1.  hi >= 0: entries [s, hi) are all below v (ascending row,
@@ -1128,7 +1235,7 @@ __device__ __forceinline__ bool det_resolve_slow(const Params &p, bool slow, int
         prefix ? scan_below(p, c, s, s + __ldcg(p.lowdeg + v), vb, acc.dscan)
                : det_scan_lane<kBatched>(p, v, c, (int32_t)(e - s), s, e, vb, -1, acc.dscan);
     if (found >= 0) {
-        __stcg(p.witness + v, found);
+        __stcg(p.witness + v, found);  // light rows keep slot 0 only
         return true;
     }
     __stcg(p.colors + v, c);
@@ -1184,7 +1291,7 @@ __device__ __forceinline__ void det_light_fast(const Params &p, const int32_t *l
     int32_t wit[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        wit[u] = act[u] ? __ldcg(p.witness + v[u]) : -1;
+        wit[u] = act[u] ? wit_first(p, v[u]) : -1;
         c[u] = act[u] ? -__ldcg(p.colors + v[u]) : 0;
     }
 #pragma unroll
@@ -1414,7 +1521,7 @@ __device__ __forceinline__ int32_t scan_below_16(const Params &p, int c, long lo
 // nearest of which becomes its witness); the rest are scanned by the whole
 // warp one vertex at a time, and keepers record their color in their
 // neighbours' bitmaps with the whole warp.
-template <bool kBatched>
+template <bool kBatched, bool kMulti>
 __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned cnt, int32_t *out,
                                   unsigned *out_cnt, bool prefix, bool round1, int act_r, ListSet A,
                                   Acc &acc) {
@@ -1423,17 +1530,29 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
     for (unsigned b = rot_warp(1) * B; b < cnt; b += NW * B) {
         const unsigned i = b + lane;
         const int nb = (int)min(B, cnt - b);
-        int32_t vl = 0, vbl = 0, wl = -1;
+        int32_t vl = 0, vbl = 0;
+        Wit wl = wit_none();
         long long sl = 0, el = 0, restl = 0;
         int cl = 0;
         bool settled = false, found = false, resolved = false;
         if (lane < nb) {
             vl = __ldcg(list + i);
-            wl = round1 ? -1 : __ldcg(p.witness + vl);
+            if (!round1) {
+                if (kMulti)
+                    wl = wit_load(p, vl);
+                else
+                    wl.w0 = wit_first(p, vl);
+            }
             cl = round1 ? 1 : -__ldcg(p.colors + vl);
             row_of<kBatched>(p, vl, sl, el, vbl);
             const int ld = prefix ? __ldcg(p.lowdeg + vl) : 0;
-            if (wl >= 0) settled = mag(__ldcg(p.colors + wl)) == cl;
+            if (kMulti) {  // every witness slot
+                const int q = round1 ? -1 : wit_match(p, wl, cl);
+                settled = q >= 0;
+                if (q > 0) wit_record(p, vl, wit_slot(wl, q), wl, true);
+            } else if (wl.w0 >= 0) {
+                settled = mag(__ldcg(p.colors + wl.w0)) == cl;
+            }
             restl = el;
             if (prefix && !settled) {
                 const long long split = sl + ld;
@@ -1446,7 +1565,7 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
                 } else {
                     const int32_t f = scan_below_16(p, cl, sl, split, vbl, &restl, acc.dscan);
                     found = f >= 0;
-                    if (found) __stcg(p.witness + vl, f);
+                    if (found) wit_record(p, vl, f, wl, kMulti);
                     resolved = found || restl <= sl;
                 }
             }
@@ -1466,7 +1585,7 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
                                                           prefix ? rest : e, vb, prefix, nullptr, acc.dscan);
                 if (f >= 0) {
                     lost |= 1u << j;
-                    if (lane == 0) __stcg(p.witness + v, f);
+                    if (lane == j) wit_record(p, v, f, wl, kMulti);
                     continue;
                 }
             }
@@ -1497,7 +1616,7 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
 // nearest of which becomes its witness) and no item scans.
 //   items / verts (lower_only lists, may be null): the entry of each work item
 // and the vertex of each entry, written when the list was built.
-template <bool kBatched>
+template <bool kBatched, bool kMulti>
 __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsigned *cbs,
                                const unsigned *items, const int32_t *verts, const unsigned *recs,
                                unsigned long long h64, int pn, bool prefix, bool push_losers,
@@ -1514,11 +1633,12 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
             const int c = (int)r0.z;
             const long long a = (long long)(((unsigned long long)r1.y << 32) | r1.x);
             const unsigned nchunks = r1.w;
+            const Wit wo = (kMulti && lane == 0) ? wit_load(p, v) : wit_none();
             const int32_t found = scan_range_down_warp(p, c, a, a + (long long)r1.z, vb, p.hconf + slot, acc.dscan);
             const bool conf = found >= 0;
             if (lane == 0) {
                 if (conf) {
-                    __stcg(p.witness + v, found);
+                    wit_record(p, v, found, wo, kMulti);
                     atomicOr(p.hconf + slot, 1u);  // stops the hub's other items early
                 }
                 // the decision travels in the completion counter (conflicts in
@@ -1566,20 +1686,32 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
         const long long a = s + (long long)j * CH, b = min(e, a + CH);
         const int c = -__ldcg(p.colors + v);
         bool conf = false;
+        Wit wo = wit_none();
+        if (!(round1 && prefix)) {
+            if (kMulti)
+                wo = wit_load(p, v);
+            else
+                wo.w0 = wit_first(p, v);
+        }
         if (round1 && prefix) {
             const int ld = __ldcg(p.lowdeg + v);
             conf = ld > 0;
             if (conf && j == 0 && lane == 0) __stcg(p.witness + v, vb + __ldg(p.ci + s + ld - 1));
-        } else if (j == 0) {  // the first item tries the witness
-            const int32_t w = __ldcg(p.witness + v);
-            conf = w >= 0 && mag(__ldcg(p.colors + w)) == c;
+        } else if (j == 0) {  // the first item tries the witness (every slot, except on the activation lists)
+            if (kMulti) {
+                const int q = wit_match(p, wo, c);
+                conf = q >= 0;
+                if (q > 0 && lane == 0) wit_record(p, v, wit_slot(wo, q), wo, true);
+            } else {
+                conf = wo.w0 >= 0 && mag(__ldcg(p.colors + wo.w0)) == c;
+            }
         }
         if (!conf && !(round1 && prefix) && !__ldcg(p.hconf + slot)) {
             const int32_t found = det_scan_warp<kBatched>(p, v, c, (int32_t)deg, s, a, b, vb, prefix,
                                                           p.hconf + slot, acc.dscan);
             if (found >= 0) {
                 conf = true;
-                if (lane == 0) __stcg(p.witness + v, found);
+                if (lane == 0) wit_record(p, v, found, wo, kMulti);
             }
         }
         const unsigned nchunks =
@@ -2047,7 +2179,7 @@ __device__ void init_phase(const Params &p) {
             row_of<kBatched>(p, v, s, e, vb);
             if (e > s && e < p.m && __ldg(p.ci + e - 1) >= __ldg(p.ci + e)) boundary++;
             __stcg(p.colors + v, kFast ? 0 : -1);
-            if (!kFast) p.witness[v] = -1;
+            if (!kFast) wit_reset(p, v);
             const long long deg = e - s;
             if (!kFast) {  // entries below v, assuming an ascending row (used only if it is)
                 long long lo = s, hi = e;
@@ -2337,13 +2469,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
                 }
             }
             const bool lower_only = prefix && !shortcut && !kFront;
-            det_hub_detect<kBatched>(p, shortcut ? p.hw[par] : p.uh[par],
+            det_hub_detect<kBatched, !kFront>(p, shortcut ? p.hw[par] : p.uh[par],
                                      shortcut ? p.hcb[par] : p.ucb[par],
                                      lower_only ? p.uitem[par] : nullptr,
                                      lower_only ? p.uvert[par] : nullptr,
                                      lower_only ? p.urec[par] : nullptr, bh, pn, prefix, !kFront,
                                      lower_only, shortcut, b);
-            det_medium_detect<kBatched>(p, shortcut ? p.mw[par] : p.um[par], bnm,
+            det_medium_detect<kBatched, !kFront>(p, shortcut ? p.mw[par] : p.um[par], bnm,
                                         kFront ? nullptr : p.mw[pn], &ctr->nm[pn], prefix, shortcut,
                                         act_r, ListSet{1, pn}, b);
             det_light_detect<kBatched>(p, shortcut ? p.lw[par] : p.ul[par], bnl,
@@ -2423,7 +2555,7 @@ __global__ void __launch_bounds__(kBlock) admit_kernel(const Params p, int g, lo
             const int32_t v = (int32_t)(vb + i);
             const_cast<int32_t *>(p.gid)[v] = g;
             __stcg(p.colors + v, -1);
-            p.witness[v] = -1;
+            wit_reset(p, v);
 #pragma unroll
             for (int j = 0; j < 8; ++j) p.bm[(size_t)j * p.np + v] = 0u;
             const long long eb = p.ebase[g];

@@ -154,10 +154,10 @@ struct sgr_server {
 
 namespace {
 
-// Per-vertex device bytes: colors, 8 bitmap words, lower count, witness, graph
-// id, two parities of three worklists and hub chunk bases, the same for the
-// unsettled lists, six hub arrays, one row offset.
-constexpr long long kVertexBytes = 4 + 32 + 4 + 4 + 4 + 2 * 4 * 4 + 2 * 4 * 4 + 6 * 4 + 4;
+// Per-vertex device bytes: colors, 8 bitmap words, lower count, five witness
+// slots, graph id, two parities of three worklists and hub chunk bases, the
+// same for the unsettled lists, six hub arrays, one row offset.
+constexpr long long kVertexBytes = 4 + 32 + 4 + 4 + 16 + 4 + 2 * 4 * 4 + 2 * 4 * 4 + 6 * 4 + 4;
 
 int carve(sgr_server *S) {
     // a quarter of the budget for the scratch of requests colored alone
@@ -193,6 +193,7 @@ int carve(sgr_server *S) {
     take((void **)&P.bm, (size_t)Vcap * 8 * 4);
     take((void **)&P.lowdeg, (size_t)Vcap * 4);
     take((void **)&P.witness, (size_t)Vcap * 4);
+    take((void **)&P.wold, (size_t)Vcap * 16);
     take((void **)&gid, (size_t)Vcap * 4);
     take((void **)&lw0, (size_t)Vcap * 4);
     take((void **)&lw1, (size_t)Vcap * 4);

@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             s.low[i] = (unsigned short)__ldcg(p.tlow + i);
 #pragma unroll
             for (int j = 0; j < 8; ++j) s.bits[j * T + i] = __ldcg(p.bm + (size_t)j * p.np + v);
-            lw[k] = __ldcg(p.witness + v);
+            lw[k] = wit_first(p, v);  // the latest witness
             s.al[i] = (unsigned short)i;
             dsum += d;
         }
