@@ -130,7 +130,7 @@ typedef struct {
                               vertices are left on the worklist, the remaining
                               rounds run in one CTA on the subgraph they
                               induce; 0 = library default (2048), -1 = never,
-                              else 1..3072.  The colors are the same. */
+                              else 1..2880.  The colors are the same. */
 } sgr_tuning;
 
 /*
@@ -304,7 +304,7 @@ int sgr_validate_csr(int32_t n, const int32_t *row_offsets, const int32_t *col_i
  * Pick the tuning for a graph by measurement: color it (sgr_color, device
  * buffers) under a grid of candidates -- hub chunk size {1024, 512, 256, 2048}
  * x degree bound of the lane-per-vertex bin {32, 16} x CTAs per SM {all, 2},
- * and in deterministic mode x tail hand-over size {2048, 1024, 3072} -- best of
+ * and in deterministic mode x tail hand-over size {2048, 1024, 2880} -- best of
  * two runs each by the kernels' event time, in that order (the library default
  * first), until budget_ms of device time is spent (0: 2000 ms; at least one
  * candidate always runs).  The fastest candidate becomes the process-wide

@@ -862,7 +862,7 @@ int autotune_grid(int mode, int32_t budget_ms, sgr_tuning *best, double *best_ms
     const int32_t chunks[] = {1024, 512, 256, 2048};
     const int32_t lights[] = {32, 16};
     const int32_t ctas[] = {0, 2};
-    const int32_t tails[] = {0, 1024, 3072};
+    const int32_t tails[] = {0, 1024, 2880};
     const int ntails = det ? 3 : 1;
     const double budget = budget_ms > 0 ? budget_ms : 2000.0;
     double spent = 0, best_t = 1e300;

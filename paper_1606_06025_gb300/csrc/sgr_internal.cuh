@@ -58,12 +58,15 @@ constexpr int kTraceCap = 1 << 16;               // rounds recorded in the timel
 constexpr int kTraceFields = 4;                  // |W_r|, ns at end of phase A / phase B, rescans
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;  // default limit of a bounded device wait
 constexpr int kTailThreads = 1024;               // threads of the tail CTA
-constexpr int kTailMax = 3072;                   // largest |W_r| the tail CTA takes
+constexpr int kTailMax = 2880;                   // largest |W_r| the tail CTA takes (shared memory)
 constexpr int kTailDefault = 2048;               // default hand-over size
 constexpr int kTailChunk = 1024;                 // row entries per warp item of the tail build
 constexpr long long kTailCapEntries = 24ll << 20;  // largest W-adjacency (16-bit entries)
 // dynamic shared memory of the tail CTA for t local vertices
-constexpr size_t tail_smem_bytes(int t) { return (size_t)t * (8 + 8 * 4 + 4 * 4 + 9 * 2) + 64; }
+// Shared memory of the tail CTA for hand-over size t (per local vertex: 64-bit
+// state, 8 bitmap words, four 32-bit and twelve 16-bit fields; arrays strided
+// by t rounded up to 8).
+constexpr size_t tail_smem_bytes(int t) { return (size_t)((t + 7) & ~7) * (8 + 8 * 4 + 4 * 4 + 12 * 2) + 64; }
 
 constexpr int kErrNoConvergence = SGR_ERR_NO_CONVERGENCE;
 constexpr int kErrTimeout = SGR_ERR_TIMEOUT;

@@ -324,16 +324,21 @@ struct TailSmem {
     int32_t *vid;            // [T] vertex id
     int32_t *deg;            // [T] degree
     unsigned *off;           // [T] start of the W-neighbour run in tadj
+    unsigned *lbest;         // [T] per long-queue entry: nearest conflict (distance << 16 | local id)
     unsigned short *cnt;     // [T] W-neighbours
     unsigned short *low;     // [T] W-neighbours below the vertex (row-ordered runs)
     short *wit;              // [T] local id of the neighbour that beat it last, or -1
+    short *wo;               // [3][T] the ones that beat it before, most recent first, or -1
     unsigned short *res;     // [T] run position where a warp resumes the scan
     unsigned short *q;       // [T] unsettled vertices of the round (also: full bitmaps)
     unsigned short *lq;      // [T] unsettled vertices whose scan continues past the lane's blocks
     unsigned short *kq;      // [T] keepers of the round
     unsigned short *al;      // [2][T]: the vertices still on the worklist, by round parity
-    unsigned *lbest;         // [T] per long-queue entry: nearest conflict (distance << 16 | local id)
 };
+
+// The arrays' stride: T rounded up to a multiple of 8, so that every array
+// starts on a 16-byte boundary whatever the hand-over size.
+__device__ __forceinline__ int tail_stride(int tail_max) { return (tail_max + 7) & ~7; }
 
 __device__ __forceinline__ TailSmem tail_smem(unsigned char *raw, int T) {
     TailSmem s;
@@ -342,16 +347,31 @@ __device__ __forceinline__ TailSmem tail_smem(unsigned char *raw, int T) {
     s.vid = (int32_t *)(s.bits + 8 * T);
     s.deg = s.vid + T;
     s.off = (unsigned *)(s.deg + T);
-    s.cnt = (unsigned short *)(s.off + T);
+    s.lbest = s.off + T;
+    s.cnt = (unsigned short *)(s.lbest + T);
     s.low = s.cnt + T;
     s.wit = (short *)(s.low + T);
-    s.res = (unsigned short *)(s.wit + T);
+    s.wo = s.wit + T;
+    s.res = (unsigned short *)(s.wo + 3 * T);
     s.q = s.res + T;
     s.lq = s.q + T;
     s.kq = s.lq + T;
     s.al = s.kq + T;
-    s.lbest = (unsigned *)(s.al + 2 * T);
     return s;
+}
+
+// Make f (a winning W-neighbour that conflicts) i's latest witness; the
+// earlier ones follow, f's old slot or else the oldest dropped.
+__device__ __forceinline__ void tail_wit_record(const TailSmem &s, int T, int i, int f) {
+    const int w0 = s.wit[i];
+    if (f == w0) return;
+    const short a = s.wo[i], b = s.wo[T + i];
+    if (f != a) {
+        if (f != b) s.wo[2 * T + i] = b;
+        s.wo[T + i] = a;
+    }
+    s.wo[i] = (short)w0;
+    s.wit[i] = (short)f;
 }
 
 // s.wit of a vertex that kept its color this round: it leaves the worklist in
@@ -527,7 +547,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
     Counters *ctr = p.ctr;
     if (__ldcg(&ctr->tail) == 0) return;
     extern __shared__ __align__(16) unsigned char s_raw[];
-    const int T = p.tail_max;
+    const int T = tail_stride(p.tail_max);
     const TailSmem s = tail_smem(s_raw, T);
     __shared__ unsigned s_nq, s_nlq, s_nfb, s_alive, s_nkeep, s_nnext, s_compact_at;
     __shared__ unsigned long long s_D, s_kdeg, s_kdegr, s_work, s_nres;
@@ -579,15 +599,26 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             dsum += d;
         }
     }
-    // the last witness, if it is still on the worklist (it is a neighbour
-    // that wins against v: the grid only records those)
-    bool wl[kLoadPer];
-#pragma unroll
-    for (int k = 0; k < kLoadPer; ++k) wl[k] = lw[k] >= 0 && lw[k] < p.n && __ldcg(p.colors + lw[k]) <= 0;
+    // the witnesses, if they are still on the worklist (each is a neighbour
+    // that wins against v: the grid only records those); the grid's slots 1-3
+    // become the earlier ones
 #pragma unroll
     for (int k = 0; k < kLoadPer; ++k) {
         const int i = tid + k * kTailThreads;
-        if (i < nT) s.wit[i] = (short)(wl[k] ? __ldcg(p.tloc + lw[k]) : -1);
+        if (i >= nT) continue;
+        const int4 o = __ldcg(reinterpret_cast<const int4 *>(p.wold) + lv[k]);
+        const int32_t w[4] = {lw[k], o.x, o.y, o.z};
+        bool on[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) on[j] = w[j] >= 0 && w[j] < p.n && __ldcg(p.colors + w[j]) <= 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const short l = (short)(on[j] ? __ldcg(p.tloc + w[j]) : -1);
+            if (j == 0)
+                s.wit[i] = l;
+            else
+                s.wo[(j - 1) * T + i] = l;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
     if (lane == 0 && dsum) atomicAdd(&s_D, dsum);
@@ -703,8 +734,20 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             const int i = k < alive ? (int)al[k] : -1;
             bool uns = false;
             if (i >= 0) {
+                const unsigned c = tk_color(s.tk[i]);
                 const int w = s.wit[i];
-                uns = !(w >= 0 && tk_color(s.tk[w]) == tk_color(s.tk[i]));
+                uns = !(w >= 0 && tk_color(s.tk[w]) == c);
+                if (uns) {  // the earlier witnesses; one that settles it moves to slot 0
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const int wj = s.wo[j * T + i];
+                        if (uns && wj >= 0 && tk_color(s.tk[wj]) == c) {
+                            uns = false;
+                            s.wo[j * T + i] = (short)w;
+                            s.wit[i] = (short)wj;
+                        }
+                    }
+                }
             }
             const unsigned um = __ballot_sync(kFull, uns);
             unsigned at = 0;
@@ -749,7 +792,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
                 }
                 if (act && gl == 0) {
                     if (found >= 0) {
-                        s.wit[i] = (short)found;
+                        tail_wit_record(s, T, i, found);
                     } else if (nblk <= kTailGroupBlocks) {  // no winner with its color: keeps it
                         const unsigned c = tk_color(me);
                         s.kq[atomicAdd(&s_nkeep, 1u)] = (unsigned short)i;
@@ -787,7 +830,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
                 const int i = s.lq[k];
                 const unsigned b = s.lbest[k];
                 if (b != 0xffffffffu) {
-                    s.wit[i] = (short)(b & 0xffffu);
+                    tail_wit_record(s, T, i, (int)(b & 0xffffu));
                 } else {
                     const unsigned c = tk_color(s.tk[i]);
                     s.kq[atomicAdd(&s_nkeep, 1u)] = (unsigned short)i;

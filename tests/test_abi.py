@@ -40,7 +40,7 @@ def test_host_only_calls_without_gpu():
     assert 1 <= t["light_max"] <= 32
     # invalid tunings are refused, valid ones round-trip
     for bad in [dict(active_lists=3), dict(light_max=33), dict(chunk=10), dict(blocks_per_sm=-1),
-                dict(tail_vertices=-2), dict(tail_vertices=3073)]:
+                dict(tail_vertices=-2), dict(tail_vertices=2881)]:
         try:
             sgrcolor.sgr_set_tuning(**bad)
         except sgrcolor.SgrError as e:
@@ -49,7 +49,7 @@ def test_host_only_calls_without_gpu():
             raise AssertionError(f"accepted {bad}")
     sgrcolor.sgr_set_tuning(light_max=8)
     assert sgrcolor.sgr_get_tuning()["light_max"] == 8
-    for tv in (-1, 1, 3072, 0):
+    for tv in (-1, 1, 2880, 0):
         sgrcolor.sgr_set_tuning(tail_vertices=tv)
         assert sgrcolor.sgr_get_tuning()["tail_vertices"] == tv
     sgrcolor.sgr_set_tuning(**t)

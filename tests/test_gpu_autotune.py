@@ -25,7 +25,7 @@ def test_autotune_installs_a_candidate_and_keeps_parity(gpu_lib, tmp_path):
         t = r1["tuning"]
         assert r1["source"] == "measured" and r1["ms"] > 0
         assert t["light_max"] in (16, 32) and t["chunk"] in (256, 512, 1024, 2048)
-        assert t["blocks_per_sm"] in (0, 2) and t["tail_vertices"] in (0, 1024, 3072)
+        assert t["blocks_per_sm"] in (0, 2) and t["tail_vertices"] in (0, 1024, 2880)
         assert gpu_lib.sgr_get_tuning() == t
         assert oracle.check(g, out.cpu().numpy())["valid"]
         k = gpu_lib.sgr_color(g.n, ro, ci, out, "det")

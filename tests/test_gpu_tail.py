@@ -77,8 +77,8 @@ def test_tail_handover_sizes(tuning, make, rule, policy):
 def test_tail_from_round_one_and_colors_above_256(tuning, rule):
     # n <= tail_vertices: the tail CTA runs every round; K_300 needs 300
     # colors, so the last 44 vertices fill their bitmaps and scan their rows
-    tuning.sgr_set_tuning(tail_vertices=3072)
-    for g in [complete(300), gg.from_edges(1, []), gg.from_edges(9, []), gg.uniform(3000, 30.0, seed=2),
+    tuning.sgr_set_tuning(tail_vertices=2880)
+    for g in [complete(300), gg.from_edges(1, []), gg.from_edges(9, []), gg.uniform(2800, 30.0, seed=2),
               gg.rmat(11, 16, seed=4)]:
         st = check(tuning, g, rule)
         assert st["tail_rounds"] == st["rounds"]
