@@ -256,6 +256,8 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
     unsigned short *tstage = tmax ? (unsigned short *)take((size_t)tch * sgr::kTailChunk * 2) : nullptr;
     int32_t *tloc = tmax ? (int32_t *)take((size_t)j.n * 4) : nullptr;
     unsigned short *tadj = tmax ? (unsigned short *)take((size_t)tcap * 2 + 16) : nullptr;
+    const int tmw = sgr::tail_mask_words(tmax);
+    unsigned *twin = (tmax && tmax <= sgr::kTailMaskMax) ? (unsigned *)take((size_t)tmax * tmw * 4) : nullptr;
     if (p && base) {
         std::memset(p, 0, sizeof(*p));
         p->ro = j.ro;
@@ -318,6 +320,8 @@ size_t layout(const Job &j, const sgr_tuning &t, char *base, Params *p, size_t *
         p->tstage = tstage;
         p->tloc = tloc;
         p->tadj = tadj;
+        p->twin = twin;
+        p->tail_mw = twin ? tmw : 0;
     }
     return off;
 }

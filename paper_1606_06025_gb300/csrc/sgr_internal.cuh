@@ -66,7 +66,15 @@ constexpr long long kTailCapEntries = 24ll << 20;  // largest W-adjacency (16-bi
 // Shared memory of the tail CTA for hand-over size t (per local vertex: 64-bit
 // state, 8 bitmap words, four 32-bit and twelve 16-bit fields; arrays strided
 // by t rounded up to 8).
-constexpr size_t tail_smem_bytes(int t) { return (size_t)((t + 7) & ~7) * (8 + 8 * 4 + 4 * 4 + 12 * 2) + 64; }
+constexpr int kTailMaskMax = 2048;               // largest hand-over with winner bit sets
+constexpr int kTailClasses = 32;                 // tentative colors with a class bit set per round
+// 32-bit words of one bit set over the local ids of a hand-over of size t
+// (a multiple of four: rows start on 16 bytes).
+constexpr int tail_mask_words(int t) { return ((t + 31) / 32 + 3) & ~3; }
+constexpr size_t tail_smem_bytes(int t) {
+    return (size_t)((t + 7) & ~7) * (8 + 8 * 4 + 4 * 4 + 12 * 2) + 64 +
+           (t <= kTailMaskMax ? (size_t)kTailClasses * tail_mask_words(t) * 4 : 0);
+}
 
 constexpr int kErrNoConvergence = SGR_ERR_NO_CONVERGENCE;
 constexpr int kErrTimeout = SGR_ERR_TIMEOUT;
@@ -176,6 +184,9 @@ struct Params {
     int tail_chunks;           // det tail: capacity of tcc / tcm
     unsigned short *tadj;      // det tail: W-neighbours as local ids, 16-byte aligned runs
     unsigned short *tstage;    // det tail: the same per chunk, kTailChunk entries a chunk
+    unsigned *twin;            // det tail: per local vertex, the bit set of the W-neighbours that
+                               // win against it (tail_mw words a row), or null
+    int tail_mw;               // det tail: words per row of twin
     int32_t *sw;               // det: hub scatter list slots
     unsigned int *scb;         // det: hub scatter list chunk bases
     Counters *ctr;

@@ -229,7 +229,8 @@ __device__ __noinline__ void tail_chunk_pass(const Params &p, unsigned nT, unsig
 
 // Copy of chunk q's staged entries to its place in the run of its vertex:
 // after the entries of the vertex's earlier chunks (their counts summed by
-// the warp).
+// the warp).  With winner bit sets, the entries that win against the vertex
+// under the rule get their bit in its row of twin.
 __device__ __noinline__ void tail_chunk_copy(const Params &p, unsigned q) {
     const int lane = threadIdx.x & 31;
     const unsigned i = __ldcg(p.tcm + q);
@@ -240,6 +241,24 @@ __device__ __noinline__ void tail_chunk_copy(const Params &p, unsigned q) {
     const unsigned short *src = p.tstage + (size_t)q * kTailChunk;
     unsigned short *dst = p.tadj + __ldcg(p.toff + i) + before;
     for (unsigned k = lane; k < n; k += 32) dst[k] = src[k];
+    if (!p.twin) return;
+    unsigned *wrow = p.twin + (size_t)i * p.tail_mw;
+    const int32_t v = __ldcg(p.tlist + i);
+    const unsigned dv = p.rule == 2 ? __ldcg(p.tdeg + i) : 0u;
+    for (unsigned k = lane; k < n; k += 32) {
+        const unsigned lu = src[k];
+        const int32_t u = __ldcg(p.tlist + lu);
+        bool win;
+        if (p.rule == 0) {
+            win = u < v;
+        } else if (p.rule == 1) {
+            win = u > v;
+        } else {  // higher degree, then lower id
+            const unsigned du = __ldcg(p.tdeg + lu);
+            win = du != dv ? du > dv : u < v;
+        }
+        if (win) atomicOr(wrow + (lu >> 5), 1u << (lu & 31));
+    }
 }
 
 // The grid's part of the hand-over at the top of round r (all CTAs call it
@@ -276,11 +295,18 @@ __device__ __noinline__ int tail_build(const Params &p, unsigned &gen, unsigned 
         if (blockIdx.x == 0 && threadIdx.x == 0) ctr->tail_fail = 1;
         return 0;  // every CTA sees the same nT and returns alike
     }
-    // (2) local ids, counts cleared; CTA 0: chunk prefix and chunk map
+    // (2) local ids, counts and winner bit sets cleared; CTA 0: chunk prefix
+    // and chunk map
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += gridDim.x * blockDim.x) {
         p.tloc[__ldcg(p.tlist + i)] = (int32_t)i;
         p.tcnt[i] = 0;
         p.tlow[i] = 0;
+    }
+    if (p.twin) {
+        const size_t words = (size_t)nT * p.tail_mw;
+        for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+             w += (size_t)gridDim.x * blockDim.x)
+            p.twin[w] = 0u;
     }
     if (blockIdx.x == 0) tail_chunk_prefix(p, nT);
     if (!grid_barrier(p, gen)) return -1;
@@ -549,7 +575,13 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
     extern __shared__ __align__(16) unsigned char s_raw[];
     const int T = tail_stride(p.tail_max);
     const TailSmem s = tail_smem(s_raw, T);
-    __shared__ unsigned s_nq, s_nlq, s_nfb, s_alive, s_nkeep, s_nnext, s_compact_at;
+    __shared__ unsigned s_nq, s_nlq, s_nfb, s_alive, s_nkeep, s_nnext, s_compact_at, s_cbase, s_cmin;
+    // winner bit sets (hand-overs up to kTailMaskMax): class masks, per
+    // tentative color cbase .. cbase + kTailClasses - 1, of the vertices that
+    // hold it this round, after the per-vertex arrays
+    const bool masks = p.twin != nullptr;
+    const int MW = p.tail_mw;
+    unsigned *cls = reinterpret_cast<unsigned *>(s_raw + (size_t)T * 80);
     __shared__ unsigned long long s_D, s_kdeg, s_kdegr, s_work, s_nres;
     __shared__ int s_kmax;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kTailThreads / 32;
@@ -567,7 +599,11 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         s_nq = s_nlq = s_nfb = s_nkeep = s_nnext = 0;
         s_compact_at = (unsigned)nT / 8;
         s_kdeg = s_work = 0;
+        s_cbase = 1;  // no color is lower
+        s_cmin = 0xffffffffu;
     }
+    if (masks)
+        for (int k = tid; k < kTailClasses * MW; k += kTailThreads) cls[k] = 0u;
     __syncthreads();
     // every thread's vertices (kLoadPer at most) load together, one step of
     // the chain vertex -> bitmaps, witness -> its color -> its local id at a
@@ -655,9 +691,14 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
     unsigned lprev = (unsigned)nT;  // length of the list this round's FirstFit pass reads
     bool ok = true;
     const unsigned lt = lanemask_lt();
+    const int mw4 = (nT + 127) / 128;  // 16-byte words of a bit set that hold local ids
     for (;; ++r) {
         const unsigned alive = s_alive;
         if (alive == 0) break;
+        // every tentative color from a bitmap is at least the last round's
+        // least one (bitmaps only gain bits, the worklist only shrinks)
+        const unsigned cbase = s_cbase;
+        unsigned cmin = 0xffffffffu;
         if (r > p.max_rounds) {
             if (tid == 0) raise_error(p, kErrNoConvergence);
             ok = false;
@@ -697,6 +738,11 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
                     }
                     if (c == 0) s.q[atomicAdd(&s_nfb, 1u)] = (unsigned short)i;  // 256 colors in use
                     s.tk[i] = ((unsigned long long)(c ? c : 1u) << 32) | tk_rank(t);
+                    if (c) {
+                        cmin = min(cmin, c);
+                        if (masks && c - cbase < (unsigned)kTailClasses)
+                            atomicOr(cls + (c - cbase) * MW + (i >> 5), 1u << (i & 31));
+                    }
                 }
             }
             const unsigned m = __ballot_sync(kFull, stay);
@@ -705,6 +751,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             at = __shfl_sync(kFull, at, 0);
             if (stay) al[at + __popc(m & lt)] = (unsigned short)i;
         }
+        cmin = __reduce_min_sync(kFull, cmin);
+        if (lane == 0 && cmin != 0xffffffffu) atomicMin(&s_cmin, cmin);
         __syncthreads();
         if (s_nfb) {  // full bitmaps: first fit over the final colors of the whole row
             const unsigned nfb = s_nfb;
@@ -774,10 +822,29 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
                 const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + s.off[i]);
                 const int bl = rg.lo >> 3, bh = rg.hi > rg.lo ? (rg.hi - 1) >> 3 : bl - 1;
                 const int nblk = bh - bl + 1;
+                // its color has a class mask: the winners that hold it are the
+                // bits of (its winner set) & (the class), 16 bytes a lane and step
+                const unsigned cme = tk_color(me);
+                const bool mk = act && masks && cme <= 256 && cme - cbase < (unsigned)kTailClasses;
+                int mhit = -1;
+                if (mk) {
+                    const uint4 *wr = reinterpret_cast<const uint4 *>(p.twin + (size_t)i * MW);
+                    const uint4 *cr = reinterpret_cast<const uint4 *>(cls + (cme - cbase) * MW);
+                    for (int k4 = gl; k4 < mw4; k4 += kTailGroup) {
+                        const uint4 a = __ldg(wr + k4), b = cr[k4];
+                        const unsigned x[4] = {a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w};
+#pragma unroll
+                        for (int w = 0; w < 4; ++w)
+                            if (x[w]) mhit = max(mhit, 32 * (4 * k4 + w) + 31 - __clz(x[w]));
+                        work += 8;
+                    }
+                }
+#pragma unroll
+                for (int o = kTailGroup / 2; o > 0; o >>= 1) mhit = max(mhit, __shfl_xor_sync(kFull, mhit, o));
                 int found = -1;
                 for (int step = 0; step < kTailGroupSteps; ++step) {
                     const int d = step * kTailGroup + gl;
-                    const bool have = act && found < 0 && d < nblk;
+                    const bool have = act && !mk && found < 0 && d < nblk;
                     int hit = -1;
                     if (have) {
                         const int b = down ? bh - d : bl + d;
@@ -788,12 +855,13 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
                     const int src = gb ? __ffs(gb) - 1 : lane;
                     const int h = __shfl_sync(kFull, hit, src);
                     if (gb && found < 0) found = h;
-                    if (!__any_sync(kFull, act && found < 0 && (step + 1) * kTailGroup < nblk)) break;
+                    if (!__any_sync(kFull, act && !mk && found < 0 && (step + 1) * kTailGroup < nblk)) break;
                 }
+                if (mk) found = mhit;
                 if (act && gl == 0) {
                     if (found >= 0) {
                         tail_wit_record(s, T, i, found);
-                    } else if (nblk <= kTailGroupBlocks) {  // no winner with its color: keeps it
+                    } else if (mk || nblk <= kTailGroupBlocks) {  // no winner with its color: keeps it
                         const unsigned c = tk_color(me);
                         s.kq[atomicAdd(&s_nkeep, 1u)] = (unsigned short)i;
                         s.wit[i] = kTailKept;
@@ -843,6 +911,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             }
         }
         __syncthreads();
+        if (masks)  // every class mask has been read
+            for (int k = tid; k < kTailClasses * MW; k += kTailThreads) cls[k] = 0u;
         // ---- keepers record their colors at their W-neighbours: 32-block
         // segments over 32 / nk warps per keeper, four segments a warp with all
         // loads in flight.  Their tentative colors stay until the next FirstFit
@@ -881,6 +951,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
             sum_next += left;
             s_alive = left;
             s_nnext = 0;  // every append of this round came before its first barrier
+            if (s_cmin != 0xffffffffu) s_cbase = s_cmin;
+            s_cmin = 0xffffffffu;
             if (r <= kTraceCap) {
                 p.trace[kTraceFields * (r - 1) + 2] = (long long)(globaltimer() - t0);
                 p.trace[kTraceFields * (r - 1) + 3] = (long long)nq;

@@ -107,7 +107,8 @@ def test_every_params_pointer_is_set_by_both_arenas():
     # lists) and tail_max = 0 (no tail); uitem / uvert / urec are optional (every
     # write checks for null and ConflictResolve then searches the chunk bases)
     server_unused = {"uitem", "uvert", "urec", "al", "am", "ah", "acb", "astamp", "vslot",
-                     "tlist", "tloc", "toff", "tcnt", "tlow", "tdeg", "tcp", "tcc", "tcm", "tadj", "tstage"}
+                     "tlist", "tloc", "toff", "tcnt", "tlow", "tdeg", "tcp", "tcc", "tcm", "tadj", "tstage",
+                     "twin"}
     for f in fields:
         assert re.search(r"p->" + f + r"\b", api), f"layout() leaves Params::{f} unset"
         if f not in server_unused:
