@@ -452,6 +452,32 @@ __device__ __forceinline__ unsigned lower_chunks(int lowdeg, int chunk) {
 }
 
 // Append a hub slot with its chunk count to a (count << 32 | chunks) list.
+// Warp-aggregated reservation in a hub list: the lanes that want in (each
+// with its number of work items) get their entry k and their first item cb
+// from one atomic on the list's counter (entries << 32 | items).  Call with
+// the whole warp.
+__device__ __forceinline__ void hub_list_reserve(bool want, unsigned items, unsigned long long *ctr64,
+                                                 unsigned &k, unsigned &cb) {
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(kFull, want);
+    k = cb = 0;
+    if (!m) return;
+    const unsigned x = want ? items : 0u;
+    unsigned incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned tot = __shfl_sync(kFull, incl, 31);
+    const int leader = __ffs(m) - 1;
+    unsigned long long old = 0;
+    if (lane == leader) old = atomicAdd(ctr64, ((unsigned long long)__popc(m) << 32) | tot);
+    old = __shfl_sync(kFull, old, leader);
+    k = (unsigned)(old >> 32) + __popc(m & lanemask_lt());
+    cb = (unsigned)old + incl - x;
+}
+
 __device__ __forceinline__ void hub_list_push(unsigned long long *ctr64, int32_t *slots,
                                               unsigned *cb, int32_t slot, unsigned nchunks) {
     const unsigned long long old = atomicAdd(ctr64, (1ull << 32) | (unsigned long long)nchunks);
@@ -686,6 +712,17 @@ __device__ __forceinline__ bool picks_color(const Params &p, int32_t w, int c) {
 
 // First-fit color from the bitmap of v given its first word; 0 if colors
 // 1..256 are all forbidden.
+__device__ __forceinline__ int bitmap_color(const Params &p, int32_t v, unsigned w0);
+
+// First color whose bit is clear in the eight words of a bitmap, or 0.
+__device__ __forceinline__ int first_zero_bit(const unsigned (&pl)[8]) {
+    int c = 0;
+#pragma unroll
+    for (int j = 7; j >= 0; --j)
+        if (~pl[j]) c = j * 32 + __ffs(~pl[j]);
+    return c;
+}
+
 __device__ __forceinline__ int bitmap_color(const Params &p, int32_t v, unsigned w0) {
     if (~w0) return __ffs(~w0);
     for (int j = 1; j < 8; ++j) {
@@ -699,12 +736,24 @@ __device__ __forceinline__ int bitmap_color(const Params &p, int32_t v, unsigned
 // first word of its bitmap).  A vertex whose bitmap is full (colors 1..256
 // all forbidden) is resolved by a scan of its row by the whole warp.
 template <bool kBatched, int U>
+__device__ __forceinline__ void full_first_fit(const Params &p, const bool (&act)[U], const int32_t (&v)[U],
+                                               int (&c)[U]);
+
+template <bool kBatched, int U>
 __device__ __forceinline__ void first_fit_lane(const Params &p, const bool (&act)[U],
                                                const int32_t (&v)[U], const unsigned (&w0)[U],
                                                int (&c)[U]) {
-    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int u = 0; u < U; ++u) c[u] = act[u] ? bitmap_color(p, v[u], w0[u]) : 0;
+    full_first_fit<kBatched, U>(p, act, v, c);
+}
+
+// Lanes whose bitmap is full (c == 0: colors 1..256 all forbidden) get their
+// first-fit color from a scan of their row by the whole warp.
+template <bool kBatched, int U>
+__device__ __forceinline__ void full_first_fit(const Params &p, const bool (&act)[U], const int32_t (&v)[U],
+                                               int (&c)[U]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         unsigned need = __ballot_sync(kFull, act[u] && c[u] == 0);
@@ -808,7 +857,8 @@ __device__ void det_assign_medium(const Params &p, int par, unsigned cnt, Acc &a
 // (p.urec), each item gets a 32-byte record {v, slot, c, vb | start, length,
 // items of the hub}, so that ConflictResolve starts scanning after one load.
 template <bool kBatched>
-__device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64, bool prefix, Acc &acc) {
+__device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64, bool prefix, int kmax,
+                                Acc &acc) {
     const int pn = par ^ 1;
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const unsigned NW = total_warps();
@@ -826,8 +876,21 @@ __device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64
             ld = __ldcg(p.lowdeg + v[0]);
         }
         const Wit wv = act[0] ? wit_load(p, v[0]) : wit_none();
-        int c[1];
-        det_assign_lane<kBatched, 1>(p, act, v, c, settled);
+        // FirstFit and the latest witness's color from whole bitmaps: the
+        // words of the hub's and of its witness's in one trip (hubs are few).
+        // Words above the largest committed color are clear and not read.
+        unsigned pv[8], pw[8];
+        const int pmax = p.resume ? 7 : min(7, kmax >> 5);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pv[j] = (act[0] && j <= pmax) ? __ldcg(p.bm + (size_t)j * p.np + v[0]) : 0u;
+        const bool has_w = act[0] && wv.w0 >= 0;
+        const int cw = has_w ? __ldcg(p.colors + wv.w0) : 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pw[j] = (has_w && j <= pmax) ? __ldcg(p.bm + (size_t)j * p.np + wv.w0) : 0u;
+        int c[1] = {act[0] ? first_zero_bit(pv) : 0};
+        full_first_fit<kBatched, 1>(p, act, v, c);
+        settled[0] = has_w && cw < 0 && first_zero_bit(pw) == c[0] && c[0] > 0;
+        if (act[0]) __stcg(p.colors + v[0], -c[0]);
         if (act[0] && !settled[0] && c[0] >= 1 && c[0] <= 256) {
             // the older witnesses, checked against c from their bitmaps (one
             // trip for all of them): a hub they settle needs no work items
@@ -848,30 +911,36 @@ __device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64
                 wit_record(p, v[0], q[hit], wv, true);
             }
         }
+        unsigned nchunks = 0, nu = 0;
         if (act[0]) {
             const unsigned cb = __ldcg(p.hcb[par] + idx);
-            const unsigned nchunks = (idx + 1 < cnt ? __ldcg(p.hcb[par] + idx + 1) : nch) - cb;
-            if (settled[0]) {
-                hub_list_push(&p.ctr->h64[pn], p.hw[pn], p.hcb[pn], slot, nchunks);
-                acc.next += 1;
-            } else {
-                const unsigned nu = prefix ? lower_chunks(ld, p.chunk) : nchunks;
-                const unsigned long long old =
-                    atomicAdd(&p.ctr->uh64[par], (1ull << 32) | (unsigned long long)nu);
-                const unsigned k = (unsigned)(old >> 32), cbu = (unsigned)old;
-                p.uh[par][k] = slot;
-                p.ucb[par][k] = cbu;
-                if (records) {
-                    const long long split = rs + ld;
-                    uint4 *rec = reinterpret_cast<uint4 *>(p.urec[par]) + 2 * (size_t)cbu;
-                    for (unsigned t = 0; t < nu; ++t) {  // item t: the t-th chunk below the split
-                        const long long hi = split - (long long)t * p.chunk;
-                        const long long lo = max(rs, hi - (long long)p.chunk);
-                        __stcg(rec + 2 * t, make_uint4((unsigned)v[0], (unsigned)slot, (unsigned)c[0], (unsigned)vb));
-                        __stcg(rec + 2 * t + 1, make_uint4((unsigned)(unsigned long long)lo,
-                                                           (unsigned)((unsigned long long)lo >> 32),
-                                                           (unsigned)max(0ll, hi - lo), nu));
-                    }
+            nchunks = (idx + 1 < cnt ? __ldcg(p.hcb[par] + idx + 1) : nch) - cb;
+            nu = prefix ? lower_chunks(ld, p.chunk) : nchunks;
+        }
+        // settled hubs onto W_{r+1}'s hub list, the others onto U_r's, one
+        // atomic per warp and list
+        const bool ps = act[0] && settled[0], pu = act[0] && !settled[0];
+        unsigned ks, cbs, k, cbu;
+        hub_list_reserve(ps, nchunks, &p.ctr->h64[pn], ks, cbs);
+        hub_list_reserve(pu, nu, &p.ctr->uh64[par], k, cbu);
+        if (ps) {
+            p.hw[pn][ks] = slot;
+            p.hcb[pn][ks] = cbs;
+            acc.next += 1;
+        }
+        if (pu) {
+            p.uh[par][k] = slot;
+            p.ucb[par][k] = cbu;
+            if (records) {
+                const long long split = rs + ld;
+                uint4 *rec = reinterpret_cast<uint4 *>(p.urec[par]) + 2 * (size_t)cbu;
+                for (unsigned t = 0; t < nu; ++t) {  // item t: the t-th chunk below the split
+                    const long long hi = split - (long long)t * p.chunk;
+                    const long long lo = max(rs, hi - (long long)p.chunk);
+                    __stcg(rec + 2 * t, make_uint4((unsigned)v[0], (unsigned)slot, (unsigned)c[0], (unsigned)vb));
+                    __stcg(rec + 2 * t + 1, make_uint4((unsigned)(unsigned long long)lo,
+                                                       (unsigned)((unsigned long long)lo >> 32),
+                                                       (unsigned)max(0ll, hi - lo), nu));
                 }
             }
         }
@@ -2430,7 +2499,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) sgr_color_kernel(const Par
             front_assign_light<kBatched>(p, par, anl, (int)r, prefix, ListSet{0, par});
             flush_push<kBatched>(p, ListSet{0, par});
         } else if (!shortcut) {
-            det_assign_hubs<kBatched>(p, par, h64, prefix, acc);
+            det_assign_hubs<kBatched>(p, par, h64, prefix, hc.kmax, acc);
             det_assign_medium<kBatched>(p, par, nm, acc);
             det_assign_light<kBatched>(p, par, nl, acc);
         }
