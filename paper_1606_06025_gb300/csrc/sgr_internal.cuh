@@ -62,7 +62,6 @@ constexpr int kTailMax = 2880;                   // largest |W_r| the tail CTA t
 constexpr int kTailDefault = 2048;               // default hand-over size
 constexpr int kTailChunk = 1024;                 // row entries per warp item of the tail build
 constexpr long long kTailCapEntries = 24ll << 20;  // largest W-adjacency (16-bit entries)
-// dynamic shared memory of the tail CTA for t local vertices
 // Shared memory of the tail CTA for hand-over size t (per local vertex: 64-bit
 // state, 8 bitmap words, four 32-bit and twelve 16-bit fields; arrays strided
 // by t rounded up to 8).
@@ -74,6 +73,23 @@ constexpr int tail_mask_words(int t) { return ((t + 31) / 32 + 3) & ~3; }
 constexpr size_t tail_smem_bytes(int t) {
     return (size_t)((t + 7) & ~7) * (8 + 8 * 4 + 4 * 4 + 12 * 2) + 64 +
            (t <= kTailMaskMax ? (size_t)kTailClasses * tail_mask_words(t) * 4 : 0);
+}
+// The tail CTA's bit-matrix rounds (at most kEngMax vertices left, one a
+// thread): the induced subgraph as kEngMax rows of kEngStride words (one
+// word of padding, so that the threads of a warp read a column without bank
+// conflicts), kEngWin class sets and their nonzero-word masks, the keeper
+// set, tentative colors, vertex ids and degrees; and, only while the matrix
+// is built, ranks, the general rounds' local ids, run offsets and ranges,
+// bitmaps and the map from those local ids.
+constexpr int kEngMax = 512;
+constexpr int kEngStride = kEngMax / 32 + 1;
+constexpr int kEngWin = 32;
+constexpr size_t kEngBytes =
+    4 * ((size_t)kEngMax * kEngStride + (size_t)kEngWin * kEngStride + kEngWin + 32 +
+         (1 + 2 + 1 + 4 + 8) * (size_t)kEngMax) +
+    2 * (size_t)kTailMax;
+constexpr size_t tail_launch_smem(int t) {
+    return tail_smem_bytes(t) > kEngBytes ? tail_smem_bytes(t) : kEngBytes;
 }
 
 constexpr int kErrNoConvergence = SGR_ERR_NO_CONVERGENCE;

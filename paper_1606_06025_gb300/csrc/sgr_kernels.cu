@@ -2890,7 +2890,7 @@ cudaError_t launch_color_front(const Params &p, bool batched, int grid, cudaStre
 
 cudaError_t launch_color_tail(const Params &p, bool batched, cudaStream_t s) {
     const void *fn = batched ? (const void *)sgr_tail_kernel<true> : (const void *)sgr_tail_kernel<false>;
-    const size_t smem = tail_smem_bytes(p.tail_max);
+    const size_t smem = tail_launch_smem(p.tail_max);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&p};

@@ -568,6 +568,379 @@ __device__ __forceinline__ void tail_compact_run(const Params &p, const TailSmem
     }
 }
 
+// ------------------------------------------------------------ bit-matrix rounds
+//
+// Once at most kEngMax vertices are left, a round of the general loop above
+// still costs five CTA barriers and a few trips to the runs and the winner
+// sets in global memory, for little work.  The CTA then switches to a form
+// of the same rounds that reads nothing from global memory:
+// * the subgraph the survivors induce becomes a bit matrix in shared memory,
+//   rows and columns ordered by rank, so that the bits of row v below column
+//   v are v's winners under the loser rule and the bits above it the
+//   neighbours v wins against.  It is built once: the winners from each
+//   survivor's run (only the part that holds winners when the run is in row
+//   order), then the rest by transposing 32 x 32 bit blocks;
+// * thread v owns survivor v and is the only one to read or write its
+//   forbidden-color bitmap (colors 1..256);
+// * a round is three passes between CTA barriers:
+//   1. FirstFit from the bitmap (a full bitmap: the whole row over the final
+//      colors, one warp); v's bit goes into the class set of its tentative
+//      color, for the kEngWin colors from the last round's least one up
+//      (tentative colors never decrease: bitmaps only gain bits);
+//   2. ConflictResolve: v loses iff the part of its row below v and the class
+//      set of its color meet, over the words of the class set that are not
+//      zero (for a color outside the window, a loop over the winners'
+//      tentative colors); keepers commit and join the keeper set;
+//   3. the others add the colors of their neighbours in the keeper set to
+//      their bitmaps, over the words of the keeper set that are not zero.
+// These are the rounds of the general loop (the same bitmaps, tentative
+// colors and winners), with the conflict test done on sets.
+
+struct TailStats {
+    unsigned long long kdeg, kdegr, nres, sum_w, sum_next;
+    unsigned work;
+    int kmax;
+    long long trounds;
+};
+
+// Color cu + 1 (cu < 256) into an 8-word bitmap held in registers.
+__device__ __forceinline__ void eng_add_color(unsigned (&add)[8], unsigned cu) {
+    if (cu < 256u) {
+        const unsigned bit = 1u << (cu & 31), wd = cu >> 5;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) add[j] |= (wd == (unsigned)j) ? bit : 0u;
+    }
+}
+
+template <bool kBatched>
+__device__ __forceinline__ bool tail_engine(const Params &p, const TailSmem &s, int T, int mode,
+                                            unsigned char *raw, const unsigned short *list, unsigned len,
+                                            unsigned cbase0, unsigned long long t0, long long &r,
+                                            TailStats &st) {
+    __shared__ unsigned e_n, e_alive, e_nkeep, e_nfb, e_cmin, e_cbase, e_kz;
+    constexpr int S = kEngStride;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kTailThreads / 32;
+    const unsigned lt = lanemask_lt();
+    unsigned *M = reinterpret_cast<unsigned *>(raw);  // [kEngMax][S]
+    unsigned *cls = M + kEngMax * S;                  // [kEngWin][S] class sets
+    unsigned *cz = cls + kEngWin * S;                 // [kEngWin] their words that are not zero
+    unsigned *K = cz + kEngWin;                       // [32] the round's keepers
+    unsigned *tc = K + 32;                            // [kEngMax] tentative color, 0 once final
+    int32_t *ev = reinterpret_cast<int32_t *>(tc + kEngMax);
+    int32_t *ed = ev + kEngMax;
+    unsigned *rk = reinterpret_cast<unsigned *>(ed + kEngMax);  // build: ranks; rounds: full bitmaps
+    unsigned *eold = rk + kEngMax;  // the general rounds' local id
+    unsigned *eoff = eold + kEngMax;
+    unsigned *elo = eoff + kEngMax;
+    unsigned *ehi = elo + kEngMax;
+    unsigned *ebm = ehi + kEngMax;  // [8][kEngMax] forbidden colors 1..256, plane-major
+    unsigned short *map = reinterpret_cast<unsigned short *>(ebm + 8 * kEngMax);  // [kTailMax]
+    // ---- the survivors: the list's vertices that did not keep last round
+    if (tid == 0) e_n = 0;
+    __syncthreads();
+    for (unsigned k0 = (unsigned)warp * 32; k0 < len; k0 += kTailThreads) {
+        const unsigned k = k0 + lane;
+        const int i = k < len ? (int)list[k] : -1;
+        const bool sv = i >= 0 && s.wit[i] != kTailKept;
+        const unsigned m = __ballot_sync(kFull, sv);
+        unsigned at = 0;
+        if (lane == 0 && m) at = atomicAdd(&e_n, (unsigned)__popc(m));
+        at = __shfl_sync(kFull, at, 0);
+        if (sv) s.q[at + __popc(m & lt)] = (unsigned short)i;
+    }
+    __syncthreads();
+    const unsigned E = e_n;
+    int i0 = -1;
+    unsigned b[8], rank = 0;
+    int32_t vid = 0, deg = 0;
+    unsigned off = 0;
+    TailRange rg{0, 0};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) b[j] = 0u;
+    if ((unsigned)tid < E) {
+        i0 = s.q[tid];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[j] = s.bits[j * T + i0];
+        vid = s.vid[i0];
+        deg = s.deg[i0];
+        off = s.off[i0];
+        rg = tail_range(s, mode, i0);  // the part of the run that holds the winners
+        rank = tk_rank(s.tk[i0]);
+    }
+    __syncthreads();  // the general loop's arrays are dead from here on
+    for (int k = tid; k < kEngMax * S + kEngWin * S + kEngWin + 32 + kEngMax; k += kTailThreads) M[k] = 0u;
+    for (int k = tid; k < kTailMax; k += kTailThreads) map[k] = 0xffffu;
+    if ((unsigned)tid < E) rk[tid] = rank;
+    __syncthreads();
+    if ((unsigned)tid < E) {  // index = the number of survivors with a higher rank
+        unsigned idx = 0;
+        const uint4 *r4 = reinterpret_cast<const uint4 *>(rk);
+        const unsigned n4 = E >> 2;
+        for (unsigned u = 0; u < n4; ++u) {
+            const uint4 x = r4[u];
+            idx += (x.x > rank ? 1u : 0u) + (x.y > rank ? 1u : 0u) + (x.z > rank ? 1u : 0u) +
+                   (x.w > rank ? 1u : 0u);
+        }
+        for (unsigned u = n4 << 2; u < E; ++u) idx += rk[u] > rank ? 1u : 0u;
+        map[i0] = (unsigned short)idx;
+        eold[idx] = (unsigned)i0;
+        ev[idx] = vid;
+        ed[idx] = deg;
+        eoff[idx] = off;
+        elo[idx] = (unsigned)rg.lo;
+        ehi[idx] = (unsigned)rg.hi;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ebm[j * kEngMax + idx] = b[j];
+    }
+    __syncthreads();
+    // ---- the winners of each row, one warp a row: from the winner bit sets
+    // written at the hand-over (the row's words gathered through the map of
+    // new to old local ids, one ballot a word), else from the run (entries no
+    // longer on the worklist map to nothing; a lane takes one 16-byte block
+    // and ORs the bits of one word at a time into the row)
+    unsigned work = 0;
+    if (p.twin) {
+        const int MW = p.tail_mw;  // at most 64
+        unsigned n0 = 0u, n1 = 0u;  // the next row's bit set, loaded one row ahead
+        if ((unsigned)warp < E) {
+            const unsigned *tw = p.twin + (size_t)eold[warp] * MW;
+            n0 = lane < MW ? __ldg(tw + lane) : 0u;
+            n1 = lane + 32 < MW ? __ldg(tw + 32 + lane) : 0u;
+        }
+        for (unsigned v = (unsigned)warp; v < E; v += nwarps) {
+            const unsigned t0 = n0, t1 = n1;
+            if (v + nwarps < E) {
+                const unsigned *tw = p.twin + (size_t)eold[v + nwarps] * MW;
+                n0 = lane < MW ? __ldg(tw + lane) : 0u;
+                n1 = lane + 32 < MW ? __ldg(tw + 32 + lane) : 0u;
+            }
+            for (unsigned w = 0; w <= (v >> 5); ++w) {
+                const unsigned u = 32 * w + (unsigned)lane;
+                const unsigned o = u < v ? eold[u] : 0u;
+                const unsigned a0 = __shfl_sync(kFull, t0, (int)((o >> 5) & 31u));
+                const unsigned a1 = __shfl_sync(kFull, t1, (int)((o >> 5) & 31u));
+                const unsigned word = (o >> 10) ? a1 : a0;
+                const unsigned m = __ballot_sync(kFull, u < v && ((word >> (o & 31)) & 1u));
+                if (lane == 0) M[v * S + w] = m;
+            }
+            if (lane == 0) work += (unsigned)MW * 2u;  // a bit set, in 16-bit entries
+        }
+    } else for (unsigned v = (unsigned)warp; v < E; v += nwarps) {
+        const uint4 *run = reinterpret_cast<const uint4 *>(p.tadj + eoff[v]);
+        const int lo = (int)elo[v], hi = (int)ehi[v];
+        unsigned *row = M + v * S;
+        if (hi > lo) {
+            for (int bb = (lo >> 3) + lane; bb <= ((hi - 1) >> 3); bb += 32) {
+                const uint4 x = ld_run(run + bb);
+                unsigned cw = 0xffffffffu, cbits = 0u;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int pos = 8 * bb + k;
+                    if (pos < lo || pos >= hi) continue;
+                    const unsigned u = map[tail_elem(x, k)];
+                    if (u >= v) continue;  // gone from the worklist, or not a winner
+                    if ((u >> 5) != cw) {
+                        if (cbits) atomicOr(row + cw, cbits);
+                        cw = u >> 5;
+                        cbits = 0u;
+                    }
+                    cbits |= 1u << (u & 31);
+                }
+                if (cbits) atomicOr(row + cw, cbits);
+            }
+        }
+        if (lane == 0) work += (unsigned)(hi > lo ? hi - lo : 0);
+    }
+    __syncthreads();
+    // ---- the neighbours each row wins against: 32 x 32 blocks of the part
+    // below the diagonal, transposed (lane l holds row 32 bi + l of block
+    // (bi, bj); column j of the block is row 32 bj + j's word bi)
+    {
+        const unsigned EB = (E + 31) >> 5;
+        for (unsigned q = (unsigned)warp; q < EB * (EB + 1) / 2; q += nwarps) {
+            unsigned bi = 0;
+            while ((bi + 1) * (bi + 2) / 2 <= q) ++bi;
+            const unsigned bj = q - bi * (bi + 1) / 2;  // bj <= bi
+            const unsigned a = M[(32 * bi + lane) * S + bj];
+            __syncwarp();
+            unsigned mine = 0u;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const unsigned t = __ballot_sync(kFull, (a >> j) & 1u);
+                if (lane == j) mine = t;
+            }
+            if (mine) M[(32 * bj + lane) * S + bi] |= mine;  // above the diagonal: no winners there
+        }
+    }
+    bool live = (unsigned)tid < E, kept = false;
+    if (live) {
+        vid = ev[tid];
+        deg = ed[tid];
+    }
+    if (tid == 0) {
+        e_alive = E;
+        e_nkeep = 0;
+        e_nfb = 0;
+        e_kz = 0;
+        e_cmin = 0xffffffffu;
+        e_cbase = cbase0;
+    }
+    __syncthreads();
+    // ---- the rounds
+    const unsigned vw = (unsigned)tid >> 5, vbit = 1u << (tid & 31), lowm = vbit - 1u;
+    const unsigned wmask = vw >= 31u ? 0xffffffffu : (2u << vw) - 1u;  // words 0 .. vw
+    const unsigned *row = M + (live ? tid : 0) * S;
+    unsigned long long kdeg = 0, kdegr = 0, nres = 0;
+    int kmax = 0;
+    bool ok = true;
+    for (;; ++r) {
+        const unsigned alive = e_alive;
+        if (alive == 0) break;
+        if (r > p.max_rounds) {
+            if (tid == 0) raise_error(p, kErrNoConvergence);
+            ok = false;
+            break;
+        }
+        const unsigned cb = e_cbase;
+        if (tid == 0) {  // the last round read these before its last barrier
+            e_nkeep = 0;
+            e_kz = 0;
+            st.sum_w += alive;
+            if (r <= kTraceCap) p.trace[kTraceFields * (r - 1)] = (long long)alive;
+        }
+        // 1. FirstFit; class sets written a warp word at a time
+        if (kept) {
+            tc[tid] = 0u;
+            kept = false;
+        }
+        unsigned c = 0;
+        if (live) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const unsigned wv = ebm[j * kEngMax + tid];
+                if (c == 0 && ~wv) c = (unsigned)(j * 32 + __ffs(~wv));
+            }
+            if (c == 0)
+                rk[atomicAdd(&e_nfb, 1u)] = (unsigned)tid;  // 256 colors in use
+            else
+                tc[tid] = c;
+        }
+        {
+            const unsigned sl = (live && c && c - cb < (unsigned)kEngWin) ? c - cb : 0xffffffffu;
+            const unsigned grp = __match_any_sync(kFull, sl);
+            if (sl != 0xffffffffu && (grp & lt) == 0u) {
+                cls[sl * S + vw] = grp;
+                atomicOr(cz + sl, 1u << vw);
+            }
+        }
+        const unsigned cm = __reduce_min_sync(kFull, live && c ? c : 0xffffffffu);
+        if (lane == 0 && cm != 0xffffffffu) atomicMin(&e_cmin, cm);
+        __syncthreads();
+        if (e_nfb) {  // full bitmaps: first fit over the final colors of the whole row
+            const unsigned nfb = e_nfb;
+            for (unsigned k = (unsigned)warp; k < nfb; k += nwarps) {
+                const unsigned v = rk[k];
+                long long rs, re;
+                int32_t vb;
+                row_of<kBatched>(p, ev[v], rs, re, vb);
+                const unsigned cc = (unsigned)warp_first_fit(p.ci, p.m, p.colors, rs, re, vb, lane, p.n);
+                if (lane == 0) {
+                    tc[v] = cc;
+                    if (cc - cb < (unsigned)kEngWin) {
+                        atomicOr(cls + (cc - cb) * S + (v >> 5), 1u << (v & 31));
+                        atomicOr(cz + (cc - cb), 1u << (v >> 5));
+                    }
+                    atomicMin(&e_cmin, cc);
+                }
+            }
+            __syncthreads();
+            if (live && c == 0) c = tc[tid];
+        }
+        if (tid == 0 && r <= kTraceCap) p.trace[kTraceFields * (r - 1) + 1] = (long long)(globaltimer() - t0);
+        // 2. ConflictResolve on the winners (the row below v)
+        bool keep = false;
+        if (live) {
+            bool lose = false;
+            const unsigned sl = c - cb;
+            if (sl < (unsigned)kEngWin) {
+                const unsigned *cs = cls + sl * S;
+                for (unsigned z = cz[sl] & wmask; z && !lose; z &= z - 1u) {
+                    const unsigned w = (unsigned)__ffs(z) - 1u;
+                    lose = (row[w] & cs[w] & (w == vw ? lowm : 0xffffffffu)) != 0u;
+                }
+            } else {
+                for (unsigned w = 0; w <= vw && !lose; ++w) {
+                    unsigned x = row[w] & (w == vw ? lowm : 0xffffffffu);
+                    while (x && !lose) {
+                        const unsigned u = (w << 5) + (unsigned)__ffs(x) - 1u;
+                        x &= x - 1u;
+                        lose = tc[u] == c;
+                    }
+                }
+            }
+            if (!lose) {
+                keep = true;
+                __stcg(p.colors + vid, (int)c);
+                kmax = max(kmax, (int)c);
+                kdeg += (unsigned long long)deg;
+                kdegr += (unsigned long long)deg * (unsigned long long)st.trounds;
+            }
+        }
+        {
+            const unsigned km = __ballot_sync(kFull, keep), lm = __ballot_sync(kFull, live);
+            if (lane == 0) {
+                K[warp] = km;
+                if (km) {
+                    atomicAdd(&e_nkeep, (unsigned)__popc(km));
+                    atomicOr(&e_kz, 1u << warp);
+                }
+                nres += (unsigned)__popc(lm);
+            }
+        }
+        __syncthreads();
+        // 3. the keepers' colors into the others' bitmaps; class sets cleared
+        for (int k = tid; k < kEngWin * S; k += kTailThreads) cls[k] = 0u;
+        if (tid < kEngWin) cz[tid] = 0u;
+        if (keep) {
+            live = false;
+            kept = true;
+        }
+        if (live) {
+            unsigned add[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) add[j] = 0u;
+            for (unsigned z = e_kz; z; z &= z - 1u) {
+                const unsigned w = (unsigned)__ffs(z) - 1u;
+                for (unsigned x = row[w] & K[w]; x; x &= x - 1u)
+                    eng_add_color(add, tc[(w << 5) + (unsigned)__ffs(x) - 1u] - 1u);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (add[j]) ebm[j * kEngMax + tid] |= add[j];
+        }
+        if (tid == 0) {
+            const unsigned left = alive - e_nkeep;
+            st.sum_next += left;
+            e_alive = left;
+            e_nfb = 0;
+            if (e_cmin != 0xffffffffu) e_cbase = e_cmin;
+            e_cmin = 0xffffffffu;
+            if (r <= kTraceCap) {
+                p.trace[kTraceFields * (r - 1) + 2] = (long long)(globaltimer() - t0);
+                p.trace[kTraceFields * (r - 1) + 3] = (long long)alive;
+            }
+        }
+        ++st.trounds;
+        __syncthreads();
+    }
+    st.work += work;
+    st.kdeg += kdeg;
+    st.kdegr += kdegr;
+    st.nres += nres;
+    st.kmax = max(st.kmax, kmax);
+    return ok;
+}
+
 template <bool kBatched>
 __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params p) {
     Counters *ctr = p.ctr;
@@ -692,9 +1065,14 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
     bool ok = true;
     const unsigned lt = lanemask_lt();
     const int mw4 = (nT + 127) / 128;  // 16-byte words of a bit set that hold local ids
+    bool engine = false;
     for (;; ++r) {
         const unsigned alive = s_alive;
         if (alive == 0) break;
+        if (alive <= (unsigned)kEngMax) {  // the bit-matrix rounds take the rest
+            engine = true;
+            break;
+        }
         // every tentative color from a bitmap is at least the last round's
         // least one (bitmaps only gain bits, the worklist only shrinks)
         const unsigned cbase = s_cbase;
@@ -961,6 +1339,18 @@ __global__ void __launch_bounds__(kTailThreads, 1) sgr_tail_kernel(const Params 
         lprev = alive;
         ++trounds;
         __syncthreads();  // bitmaps and the counters of the next round are complete
+    }
+    if (engine) {
+        TailStats st{kdeg, kdegr, nres, sum_w, sum_next, work, kmax, trounds};
+        ok = tail_engine<kBatched>(p, s, T, mode, s_raw, s.al + par * T, lprev, s_cbase, t0, r, st);
+        kdeg = st.kdeg;
+        kdegr = st.kdegr;
+        nres = st.nres;
+        sum_w = st.sum_w;
+        sum_next = st.sum_next;
+        work = st.work;
+        kmax = st.kmax;
+        trounds = st.trounds;
     }
     // ---- statistics of all rounds: one reduction
     unsigned long long wsum = work;
