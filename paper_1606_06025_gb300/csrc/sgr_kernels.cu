@@ -229,6 +229,13 @@ __device__ __forceinline__ unsigned rot_warp(int part) {
     return (rot_block(part) * blockDim.x + threadIdx.x) >> 5;
 }
 
+// A warp's slot in a CTA-major order of all warps (warp 0 of every CTA, then
+// warp 1 of every CTA, ...), rotated like rot_block: consecutive batches of a
+// short list land on different SMs.
+__device__ __forceinline__ unsigned spread_warp(int part) {
+    return (threadIdx.x >> 5) * gridDim.x + rot_block(part);
+}
+
 // Batch of worklist entries a warp takes at a time: spread a short list over
 // all warps, up to 32 entries (one per lane) for long lists.
 __device__ __forceinline__ unsigned warp_batch(unsigned cnt) {
@@ -423,6 +430,40 @@ __device__ __forceinline__ void warp_push(bool flag, int32_t item, unsigned *cou
     if (flag) out[pos + __popc(bal & lanemask_lt())] = item;
 }
 
+// Warp-level order-preserving pushes of U flags per lane into two lists at
+// once: one atomic per list for all U (both issued before either result is
+// used), entries in (u, lane) order.
+template <int U>
+__device__ __forceinline__ void warp_push2(const bool (&fa)[U], const bool (&fb)[U],
+                                           const int32_t (&item)[U], unsigned *ca, int32_t *outa,
+                                           unsigned *cb, int32_t *outb, unsigned long long &pushed_a) {
+    const int lane = threadIdx.x & 31;
+    unsigned ba[U], bb[U], ta = 0, tb = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        ba[u] = __ballot_sync(kFull, fa[u]);
+        bb[u] = __ballot_sync(kFull, fb[u]);
+        ta += (unsigned)__popc(ba[u]);
+        tb += (unsigned)__popc(bb[u]);
+    }
+    unsigned oa = 0, ob = 0;
+    if (lane == 0) {
+        if (ta) oa = atomicAdd(ca, ta);
+        if (tb) ob = atomicAdd(cb, tb);
+        pushed_a += ta;
+    }
+    oa = __shfl_sync(kFull, oa, 0);
+    ob = __shfl_sync(kFull, ob, 0);
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (fa[u]) outa[oa + __popc(ba[u] & lt)] = item[u];
+        if (fb[u]) outb[ob + __popc(bb[u] & lt)] = item[u];
+        oa += (unsigned)__popc(ba[u]);
+        ob += (unsigned)__popc(bb[u]);
+    }
+}
+
 // Position of (tile t, warp w, sub-tile u, lane l) in a light list.
 __device__ __forceinline__ unsigned tile_index(unsigned t, int u) {
     return t * kLightTile + ((threadIdx.x >> 5) * kLightUnroll + u) * 32 + (threadIdx.x & 31);
@@ -451,33 +492,42 @@ __device__ __forceinline__ unsigned lower_chunks(int lowdeg, int chunk) {
     return lowdeg > 0 ? (unsigned)((lowdeg + chunk - 1) / chunk) : 1u;
 }
 
-// Append a hub slot with its chunk count to a (count << 32 | chunks) list.
-// Warp-aggregated reservation in a hub list: the lanes that want in (each
-// with its number of work items) get their entry k and their first item cb
-// from one atomic on the list's counter (entries << 32 | items).  Call with
-// the whole warp.
-__device__ __forceinline__ void hub_list_reserve(bool want, unsigned items, unsigned long long *ctr64,
-                                                 unsigned &k, unsigned &cb) {
+// Warp-aggregated reservations in two hub lists: the lanes that want in
+// (each with its number of work items) get their entry k and their first
+// item cb from one atomic on each list's counter (entries << 32 | items),
+// both atomics issued before either result is used.  Call with the whole
+// warp.
+__device__ __forceinline__ void hub_list_reserve2(bool wa, unsigned ia, unsigned long long *ca,
+                                                  unsigned &ka, unsigned &cba, bool wb, unsigned ib,
+                                                  unsigned long long *cb, unsigned &kb, unsigned &cbb) {
     const int lane = threadIdx.x & 31;
-    const unsigned m = __ballot_sync(kFull, want);
-    k = cb = 0;
-    if (!m) return;
-    const unsigned x = want ? items : 0u;
-    unsigned incl = x;
+    const unsigned ma = __ballot_sync(kFull, wa), mb = __ballot_sync(kFull, wb);
+    const unsigned xa = wa ? ia : 0u, xb = wb ? ib : 0u;
+    unsigned sa = xa, sb = xb;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
+        const unsigned ya = __shfl_up_sync(kFull, sa, o), yb = __shfl_up_sync(kFull, sb, o);
+        if (lane >= o) {
+            sa += ya;
+            sb += yb;
+        }
     }
-    const unsigned tot = __shfl_sync(kFull, incl, 31);
-    const int leader = __ffs(m) - 1;
-    unsigned long long old = 0;
-    if (lane == leader) old = atomicAdd(ctr64, ((unsigned long long)__popc(m) << 32) | tot);
-    old = __shfl_sync(kFull, old, leader);
-    k = (unsigned)(old >> 32) + __popc(m & lanemask_lt());
-    cb = (unsigned)old + incl - x;
+    const unsigned ta = __shfl_sync(kFull, sa, 31), tb = __shfl_sync(kFull, sb, 31);
+    unsigned long long oa = 0, ob = 0;
+    if (lane == 0) {
+        if (ma) oa = atomicAdd(ca, ((unsigned long long)__popc(ma) << 32) | ta);
+        if (mb) ob = atomicAdd(cb, ((unsigned long long)__popc(mb) << 32) | tb);
+    }
+    oa = __shfl_sync(kFull, oa, 0);
+    ob = __shfl_sync(kFull, ob, 0);
+    const unsigned lt = lanemask_lt();
+    ka = (unsigned)(oa >> 32) + __popc(ma & lt);
+    cba = (unsigned)oa + sa - xa;
+    kb = (unsigned)(ob >> 32) + __popc(mb & lt);
+    cbb = (unsigned)ob + sb - xb;
 }
 
+// Append a hub slot with its chunk count to a (count << 32 | chunks) list.
 __device__ __forceinline__ void hub_list_push(unsigned long long *ctr64, int32_t *slots,
                                               unsigned *cb, int32_t slot, unsigned nchunks) {
     const unsigned long long old = atomicAdd(ctr64, (1ull << 32) | (unsigned long long)nchunks);
@@ -723,6 +773,40 @@ __device__ __forceinline__ int first_zero_bit(const unsigned (&pl)[8]) {
     return c;
 }
 
+// First-fit color from planes j0.. of v's bitmap (the planes below j0 full),
+// one plane a trip; 0 if colors 1..256 are all forbidden.
+__device__ __forceinline__ int bitmap_color_from(const Params &p, int32_t v, int j0) {
+    for (int j = j0; j < 8; ++j) {
+        const unsigned wv = __ldcg(p.bm + (size_t)j * p.np + v);
+        if (~wv) return j * 32 + __ffs(~wv);
+    }
+    return 0;
+}
+
+// During FirstFit: does worklist vertex w, whose tentative color last round
+// was tw (so that colors 1 .. tw-1 are all forbidden for it) and whose first
+// bitmap word is x0, pick color c (1..256)?  Planes from tw's to c's are
+// loaded together, and only when c > 32.
+__device__ __forceinline__ bool picks_color_after(const Params &p, int32_t w, int c, int tw, unsigned x0) {
+    if (tw > c) return false;  // its color is at least tw
+    const int P = (c - 1) >> 5, b = (c - 1) & 31;
+    const unsigned low = b ? (0xffffffffu >> (32 - b)) : 0u;  // colors below c in its word
+    if (P == 0) return (x0 & low) == low && !((x0 >> b) & 1u);
+    if (~x0) return false;  // its color is at most 32
+    const int P0 = max(1, (tw - 1) >> 5);
+    unsigned pl[8];
+#pragma unroll
+    for (int j = 1; j < 8; ++j) pl[j] = (j >= P0 && j <= P) ? __ldcg(p.bm + (size_t)j * p.np + w) : 0xffffffffu;
+    bool full = true;
+    unsigned x = 0;
+#pragma unroll
+    for (int j = 1; j < 8; ++j) {
+        if (j < P) full = full && pl[j] == 0xffffffffu;
+        if (j == P) x = pl[j];
+    }
+    return full && (x & low) == low && !((x >> b) & 1u);
+}
+
 __device__ __forceinline__ int bitmap_color(const Params &p, int32_t v, unsigned w0) {
     if (~w0) return __ffs(~w0);
     for (int j = 1; j < 8; ++j) {
@@ -776,24 +860,47 @@ template <bool kBatched, int U>
 __device__ __forceinline__ void det_assign_lane(const Params &p, const bool (&act)[U],
                                                 const int32_t (&v)[U], int (&c)[U],
                                                 bool (&settled)[U]) {
-    unsigned w0[U], ww0[U];
+    // A worklist vertex's color word holds -(its tentative color of the last
+    // round), t: bitmaps only gain bits, so colors 1 .. t-1 are still all
+    // forbidden, and the search starts at t's plane.  Three trips: (bitmap
+    // plane 0, witness, t), then (two planes from t's, the witness's color
+    // and plane 0), then the witness's planes up to c's only when c > 32.
+    unsigned w0[U], ww0[U], wa[U], wb[U];
     int32_t wit[U];
-    int cw[U];
+    int cw[U], t[U], P[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         w0[u] = act[u] ? __ldcg(p.bm + v[u]) : 0u;
         wit[u] = act[u] ? wit_first(p, v[u]) : -1;
+        t[u] = act[u] ? -__ldcg(p.colors + v[u]) : 0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         cw[u] = wit[u] >= 0 ? __ldcg(p.colors + wit[u]) : 0;
         ww0[u] = wit[u] >= 0 ? __ldcg(p.bm + wit[u]) : 0u;
+        const bool more = act[u] && !~w0[u];
+        P[u] = min(6, max(1, (t[u] - 1) >> 5));
+        wa[u] = more ? __ldcg(p.bm + (size_t)P[u] * p.np + v[u]) : 0xffffffffu;
+        wb[u] = more ? __ldcg(p.bm + (size_t)(P[u] + 1) * p.np + v[u]) : 0xffffffffu;
     }
-    first_fit_lane<kBatched, U>(p, act, v, w0, c);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const int tw = (act[u] && wit[u] >= 0 && cw[u] < 0) ? bitmap_color(p, wit[u], ww0[u]) : 0;
-        settled[u] = act[u] && tw > 0 && tw == c[u];
+        if (!act[u])
+            c[u] = 0;
+        else if (~w0[u])
+            c[u] = __ffs(~w0[u]);
+        else if (~wa[u])
+            c[u] = P[u] * 32 + __ffs(~wa[u]);
+        else if (~wb[u])
+            c[u] = (P[u] + 1) * 32 + __ffs(~wb[u]);
+        else
+            c[u] = bitmap_color_from(p, v[u], P[u] + 2);
+    }
+    full_first_fit<kBatched, U>(p, act, v, c);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        settled[u] = act[u] && wit[u] >= 0 && cw[u] < 0 && c[u] >= 1 && c[u] <= 256 &&
+                     picks_color_after(p, wit[u], c[u], -cw[u], ww0[u]);
         if (act[u]) __stcg(p.colors + v[u], -c[u]);
     }
 }
@@ -830,8 +937,7 @@ __device__ void det_assign_medium(const Params &p, int par, unsigned cnt, Acc &a
     const int pn = par ^ 1;
     const int32_t *list = p.mw[par];
     const unsigned NW = total_warps();
-    unsigned long long dummy = 0;
-    for (unsigned base = rot_warp(1) * 32 * U; base < cnt; base += NW * 32 * U) {
+    for (unsigned base = spread_warp(1) * 32 * U; base < cnt; base += NW * 32 * U) {
         bool act[U], settled[U];
         int32_t v[U];
         int c[U];
@@ -842,11 +948,10 @@ __device__ void det_assign_medium(const Params &p, int par, unsigned cnt, Acc &a
             v[u] = act[u] ? __ldcg(list + idx) : 0;
         }
         det_assign_lane<kBatched, U>(p, act, v, c, settled);
+        bool open[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            warp_push(settled[u], v[u], &p.ctr->nm[pn], p.mw[pn], acc.next);
-            warp_push(act[u] && !settled[u], v[u], &p.ctr->num[par], p.um[par], dummy);
-        }
+        for (int u = 0; u < U; ++u) open[u] = act[u] && !settled[u];
+        warp_push2<U>(settled, open, v, &p.ctr->nm[pn], p.mw[pn], &p.ctr->num[par], p.um[par], acc.next);
     }
 }
 
@@ -863,10 +968,16 @@ __device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64
     const unsigned cnt = (unsigned)(h64 >> 32), nch = (unsigned)h64;
     const unsigned NW = total_warps();
     const bool records = prefix && p.urec[par] != nullptr;
-    for (unsigned base = global_warp() * 32; base < cnt; base += NW * 32) {
+    // at least four hubs a warp (fewer list atomics), more on long lists, in
+    // CTA-major warp order (the hubs' scattered loads spread over the SMs)
+    const unsigned B = max(4u, warp_batch(cnt));
+    for (unsigned base = spread_warp(0) * B; base < cnt; base += NW * B) {
         const unsigned idx = base + (threadIdx.x & 31);
-        bool act[1] = {idx < cnt}, settled[1];
+        bool act[1] = {(threadIdx.x & 31) < B && idx < cnt}, settled[1];
         int32_t slot = act[0] ? __ldcg(p.hw[par] + idx) : 0;
+        // the entry's chunk range, loaded with the slot (not after the stores below)
+        const unsigned cb0 = act[0] ? __ldcg(p.hcb[par] + idx) : 0u;
+        const unsigned cb1 = act[0] ? (idx + 1 < cnt ? __ldcg(p.hcb[par] + idx + 1) : nch) : 0u;
         int32_t v[1] = {act[0] ? __ldcg(p.hvert + slot) : 0};
         long long rs = 0, re = 0;
         int32_t vb = 0;
@@ -913,16 +1024,14 @@ __device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64
         }
         unsigned nchunks = 0, nu = 0;
         if (act[0]) {
-            const unsigned cb = __ldcg(p.hcb[par] + idx);
-            nchunks = (idx + 1 < cnt ? __ldcg(p.hcb[par] + idx + 1) : nch) - cb;
+            nchunks = cb1 - cb0;
             nu = prefix ? lower_chunks(ld, p.chunk) : nchunks;
         }
         // settled hubs onto W_{r+1}'s hub list, the others onto U_r's, one
         // atomic per warp and list
         const bool ps = act[0] && settled[0], pu = act[0] && !settled[0];
         unsigned ks, cbs, k, cbu;
-        hub_list_reserve(ps, nchunks, &p.ctr->h64[pn], ks, cbs);
-        hub_list_reserve(pu, nu, &p.ctr->uh64[par], k, cbu);
+        hub_list_reserve2(ps, nchunks, &p.ctr->h64[pn], ks, cbs, pu, nu, &p.ctr->uh64[par], k, cbu);
         if (ps) {
             p.hw[pn][ks] = slot;
             p.hcb[pn][ks] = cbs;
