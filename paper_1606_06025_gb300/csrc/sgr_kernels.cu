@@ -987,39 +987,47 @@ __device__ void det_assign_hubs(const Params &p, int par, unsigned long long h64
             ld = __ldcg(p.lowdeg + v[0]);
         }
         const Wit wv = act[0] ? wit_load(p, v[0]) : wit_none();
-        // FirstFit and the latest witness's color from whole bitmaps: the
-        // words of the hub's and of its witness's in one trip (hubs are few).
-        // Words above the largest committed color are clear and not read.
-        unsigned pv[8], pw[8];
+        // FirstFit from the hub's whole bitmap (its words in one trip; words
+        // above the largest committed color are clear and not read)
+        unsigned pv[8];
         const int pmax = p.resume ? 7 : min(7, kmax >> 5);
 #pragma unroll
         for (int j = 0; j < 8; ++j) pv[j] = (act[0] && j <= pmax) ? __ldcg(p.bm + (size_t)j * p.np + v[0]) : 0u;
-        const bool has_w = act[0] && wv.w0 >= 0;
-        const int cw = has_w ? __ldcg(p.colors + wv.w0) : 0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) pw[j] = (has_w && j <= pmax) ? __ldcg(p.bm + (size_t)j * p.np + wv.w0) : 0u;
         int c[1] = {act[0] ? first_zero_bit(pv) : 0};
         full_first_fit<kBatched, 1>(p, act, v, c);
-        settled[0] = has_w && cw < 0 && first_zero_bit(pw) == c[0] && c[0] > 0;
         if (act[0]) __stcg(p.colors + v[0], -c[0]);
-        if (act[0] && !settled[0] && c[0] >= 1 && c[0] <= 256) {
-            // the older witnesses, checked against c from their bitmaps (one
-            // trip for all of them): a hub they settle needs no work items
-            const int32_t q[4] = {wv.o.x, wv.o.y, wv.o.z, wv.o.w};
-            int cq[4];
-            bool pk[4];
+        // the witness slots, latest first: does one of them, still on the
+        // worklist, pick c too?  Their colors and their words of c's plane in
+        // one trip; a slot's color word holds -(its last tentative color) t,
+        // and colors below t are all forbidden for it, so the word decides
+        // when t is in c's plane (else its planes up to c's, one more trip).
+        // A hub a slot settles needs no work items.
+        settled[0] = false;
+        if (act[0] && c[0] >= 1 && c[0] <= 256) {
+            const int P = (c[0] - 1) >> 5, b = (c[0] - 1) & 31;
+            const unsigned low = b ? (0xffffffffu >> (32 - b)) : 0u;  // colors below c in its word
+            const int32_t q[5] = {wv.w0, wv.o.x, wv.o.y, wv.o.z, wv.o.w};
+            int cq[5];
+            unsigned xq[5];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 5; ++k) {
                 cq[k] = q[k] >= 0 ? __ldcg(p.colors + q[k]) : 0;
-                pk[k] = q[k] >= 0 && picks_color(p, q[k], c[0]);
+                xq[k] = q[k] >= 0 ? __ldcg(p.bm + (size_t)P * p.np + q[k]) : 0xffffffffu;
             }
             int hit = -1;
 #pragma unroll
-            for (int k = 3; k >= 0; --k)
-                if (pk[k] && cq[k] < 0) hit = k;
+            for (int k = 4; k >= 0; --k) {
+                const int t = -cq[k];
+                bool pk = false;
+                if (cq[k] < 0 && t <= c[0]) {
+                    pk = ((t - 1) >> 5) == P ? ((xq[k] & low) == low && !((xq[k] >> b) & 1u))
+                                             : picks_color(p, q[k], c[0]);
+                }
+                if (pk) hit = k;
+            }
             if (hit >= 0) {
                 settled[0] = true;
-                wit_record(p, v[0], q[hit], wv, true);
+                if (hit > 0) wit_record(p, v[0], q[hit], wv, true);
             }
         }
         unsigned nchunks = 0, nu = 0;
