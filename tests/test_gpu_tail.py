@@ -84,6 +84,25 @@ def test_tail_from_round_one_and_colors_above_256(tuning, rule):
         assert st["tail_rounds"] == st["rounds"]
 
 
+def clique_and_falling_path():
+    # K_45 on ids 0..44 beside a path 299-298-...-100 whose ids fall along
+    # it: from round 33 to 45 the path's vertices still try color 1 while the
+    # clique's try colors 33..45
+    edges = [(i, j) for i in range(45) for j in range(i + 1, 45)]
+    edges += [(v, v - 1) for v in range(299, 100, -1)]
+    return gg.from_edges(300, edges)
+
+
+@pytest.mark.parametrize("rule", ["low_keeps", "low_loses", "degree"])
+def test_bit_matrix_rounds_with_colors_far_apart(tuning, rule):
+    # at most 512 vertices: every round runs on the bit matrix, whose class
+    # sets cover 32 tentative colors from the round's least one; colors above
+    # that window are decided by a loop over the winners' tentative colors
+    tuning.sgr_set_tuning(tail_vertices=0)
+    st = check(tuning, clique_and_falling_path(), rule)
+    assert st["tail_rounds"] == st["rounds"]
+
+
 def test_tail_with_hubs_split_and_small_bins(tuning):
     for tune in [dict(light_max=4, chunk=64), dict(light_max=1, chunk=2048, blocks_per_sm=1)]:
         for tv in (100, 0):
