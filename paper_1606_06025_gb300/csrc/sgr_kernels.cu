@@ -1303,10 +1303,12 @@ __device__ __forceinline__ void activate(const Params &p, int32_t w, int cw, int
 }
 
 // Record final color c in the bitmaps of the neighbours [a, b) (lanes lane0,
-// lane0 + stride, ... over 16-byte blocks).  Colors above 256 are not
-// recorded; FirstFit then falls back to a scan.  act_r > 0: also activate
-// the neighbours that hold tentative color c.
-template <bool kBatched>
+// lane0 + stride, ... over 16-byte blocks; kDeep: four blocks a lane with all
+// their loads in flight before any atomic, for the whole-list rounds, whose
+// kernel has the registers for it).  Colors above 256 are not recorded;
+// FirstFit then falls back to a scan.  act_r > 0: also activate the
+// neighbours that hold tentative color c.
+template <bool kBatched, bool kDeep = false>
 __device__ __forceinline__ void scatter_color(const Params &p, int c, long long a, long long b,
                                               int32_t vb, int lane0, int stride, int act_r,
                                               ListSet A) {
@@ -1314,24 +1316,55 @@ __device__ __forceinline__ void scatter_color(const Params &p, int c, long long 
     if (!bits && !act_r) return;
     unsigned *plane = p.bm + (size_t)((c - 1) >> 5) * p.np;
     const unsigned bit = 1u << ((c - 1) & 31);
-    for (long long q = (a >> 2) + lane0; (q << 2) < b; q += stride) {
-        const int4 x = load4(p.ci, q, p.m);
-        const long long i0 = q << 2;
-        int32_t w[4];
-        bool ok[4];
-        int cw[4];
+    if constexpr (kDeep) {
+        for (long long q0 = (a >> 2) + lane0; (q0 << 2) < b; q0 += 4 * (long long)stride) {
+            int4 x[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long i = i0 + k;
-            w[k] = vb + elem(x, k);
-            ok[k] = i >= a && i < b && (unsigned)w[k] < (unsigned)p.n;
-            cw[k] = (act_r && ok[k]) ? __ldcg(p.colors + w[k]) : 0;
+            for (int t = 0; t < 4; ++t) {
+                const long long q = q0 + (long long)t * stride;
+                x[t] = (q << 2) < b ? load4(p.ci, q, p.m) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const long long i0 = (q0 + (long long)t * stride) << 2;
+                int32_t w[4];
+                bool ok[4];
+                int cw[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const long long i = i0 + k;
+                    w[k] = vb + elem(x[t], k);
+                    ok[k] = i >= a && i < b && (unsigned)w[k] < (unsigned)p.n;
+                    cw[k] = (act_r && ok[k]) ? __ldcg(p.colors + w[k]) : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!ok[k]) continue;
+                    if (bits) atomicOr(plane + w[k], bit);
+                    if (act_r) activate<kBatched>(p, w[k], cw[k], c, act_r, A);
+                }
+            }
         }
+    } else {
+        for (long long q = (a >> 2) + lane0; (q << 2) < b; q += stride) {
+            const int4 x = load4(p.ci, q, p.m);
+            const long long i0 = q << 2;
+            int32_t w[4];
+            bool ok[4];
+            int cw[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (!ok[k]) continue;
-            if (bits) atomicOr(plane + w[k], bit);
-            if (act_r) activate<kBatched>(p, w[k], cw[k], c, act_r, A);
+            for (int k = 0; k < 4; ++k) {
+                const long long i = i0 + k;
+                w[k] = vb + elem(x, k);
+                ok[k] = i >= a && i < b && (unsigned)w[k] < (unsigned)p.n;
+                cw[k] = (act_r && ok[k]) ? __ldcg(p.colors + w[k]) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!ok[k]) continue;
+                if (bits) atomicOr(plane + w[k], bit);
+                if (act_r) activate<kBatched>(p, w[k], cw[k], c, act_r, A);
+            }
         }
     }
 }
@@ -1559,9 +1592,10 @@ __device__ void det_light_detect(const Params &p, const int32_t *list, unsigned 
 
 // Warp-wide det scan of entries [a, b) of v's row (s = row start); returns
 // the conflicting neighbour or -1.  prefix: entries below v, [a, min(b,
-// split)), 128 per step from the top down; `stop` (may be null) is polled
-// between steps.
-template <bool kBatched>
+// split)), 128 per step from the top down (kPipe: each step's blocks loaded
+// during the step before, for the whole-list rounds); `stop` (may be null) is
+// polled between steps.
+template <bool kBatched, bool kPipe = false>
 __device__ __forceinline__ int32_t det_scan_warp(const Params &p, int32_t v, int c, int32_t dv,
                                                  long long s, long long a, long long b, int32_t vb,
                                                  bool prefix, const unsigned *stop,
@@ -1571,33 +1605,69 @@ __device__ __forceinline__ int32_t det_scan_warp(const Params &p, int32_t v, int
         const long long split = s + __ldcg(p.lowdeg + v);
         const long long hi = min(b, split);
         if (hi <= a) return -1;
-        for (long long top = (hi - 1) >> 2; top >= (a >> 2); top -= 32) {
-            const long long q = top - lane;
-            int32_t my = -1;
-            if (q >= (a >> 2)) {
-                const int4 x = load4(p.ci, q, p.m);
-                const long long i0 = q << 2;
-                int cw[4];
-                bool ok[4];
+        if constexpr (kPipe) {
+            const long long qa = a >> 2;
+            long long top = (hi - 1) >> 2, q = top - lane;
+            int4 x = q >= qa ? load4(p.ci, q, p.m) : make_int4(0, 0, 0, 0);
+            for (;;) {  // the next step's blocks are loaded before this step's gathers
+                const bool more = top - 32 >= qa;
+                const long long nq = q - 32;
+                const int4 nx = (more && nq >= qa) ? load4(p.ci, nq, p.m) : make_int4(0, 0, 0, 0);
+                int32_t my = -1;
+                if (q >= qa) {
+                    const long long i0 = q << 2;
+                    int cw[4];
+                    bool ok[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const long long i = i0 + k;
-                    const int32_t w = vb + elem(x, k);
-                    ok[k] = i >= a && i < hi && (unsigned)w < (unsigned)p.n;
-                    cw[k] = ok[k] ? __ldcg(p.colors + w) : 0;
-                }
+                    for (int k = 0; k < 4; ++k) {
+                        const long long i = i0 + k;
+                        const int32_t w = vb + elem(x, k);
+                        ok[k] = i >= a && i < hi && (unsigned)w < (unsigned)p.n;
+                        cw[k] = ok[k] ? __ldcg(p.colors + w) : 0;
+                    }
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (!ok[k]) continue;
-                    scanned++;
-                    if (mag(cw[k]) == c) my = vb + elem(x, k);
+                    for (int k = 0; k < 4; ++k) {
+                        if (!ok[k]) continue;
+                        scanned++;
+                        if (mag(cw[k]) == c) my = vb + elem(x, k);
+                    }
                 }
+                const unsigned bal = __ballot_sync(kFull, my >= 0);
+                if (bal) return __shfl_sync(kFull, my, __ffs(bal) - 1);
+                if ((stop && __ldcg(stop)) || !more) return -1;
+                top -= 32;
+                q = nq;
+                x = nx;
             }
-            const unsigned bal = __ballot_sync(kFull, my >= 0);
-            if (bal) return __shfl_sync(kFull, my, __ffs(bal) - 1);
-            if (stop && __ldcg(stop)) return -1;
+        } else {
+            for (long long top = (hi - 1) >> 2; top >= (a >> 2); top -= 32) {
+                const long long q = top - lane;
+                int32_t my = -1;
+                if (q >= (a >> 2)) {
+                    const int4 x = load4(p.ci, q, p.m);
+                    const long long i0 = q << 2;
+                    int cw[4];
+                    bool ok[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const long long i = i0 + k;
+                        const int32_t w = vb + elem(x, k);
+                        ok[k] = i >= a && i < hi && (unsigned)w < (unsigned)p.n;
+                        cw[k] = ok[k] ? __ldcg(p.colors + w) : 0;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (!ok[k]) continue;
+                        scanned++;
+                        if (mag(cw[k]) == c) my = vb + elem(x, k);
+                    }
+                }
+                const unsigned bal = __ballot_sync(kFull, my >= 0);
+                if (bal) return __shfl_sync(kFull, my, __ffs(bal) - 1);
+                if (stop && __ldcg(stop)) return -1;
+            }
+            return -1;
         }
-        return -1;
     }
     for (long long q0 = a >> 2; (q0 << 2) < b; q0 += 32) {
         const long long q = q0 + lane;
@@ -1634,40 +1704,83 @@ __device__ __forceinline__ int32_t det_scan_warp(const Params &p, int32_t v, int
 // Warp scan of entries [a, hi) of an ascending row, all below the vertex,
 // from the top down (128 entries a step); returns the nearest neighbour
 // holding magnitude c, or -1.  The stop flag is read with each step's loads
-// and ends the scan after that step.
+// and ends the scan after that step.  kPipe: each step's blocks are loaded
+// during the step before (whole-list rounds).
+template <bool kPipe>
 __device__ __forceinline__ int32_t scan_range_down_warp(const Params &p, int c, long long a, long long hi,
                                                         int32_t vb, const unsigned *stop,
                                                         unsigned long long &scanned) {
-    const int lane = threadIdx.x & 31;
-    for (long long top = (hi - 1) >> 2; hi > a && top >= (a >> 2); top -= 32) {
-        const long long q = top - lane;
-        const bool in = q >= (a >> 2);
-        const int4 x = in ? load4(p.ci, q, p.m) : make_int4(0, 0, 0, 0);
-        const unsigned halt = __ldcg(stop);
-        int32_t my = -1;
-        if (in) {
-            const long long i0 = q << 2;
-            int cw[4];
-            bool ok[4];
+    if constexpr (kPipe) {
+        const int lane = threadIdx.x & 31;
+        if (hi <= a) return -1;
+        const long long qa = a >> 2;
+        long long top = (hi - 1) >> 2, q = top - lane;
+        int4 x = q >= qa ? load4(p.ci, q, p.m) : make_int4(0, 0, 0, 0);
+        for (;;) {
+            // the next step's blocks are loaded before this step's gathers, so
+            // that a step waits for one dependent trip, not two
+            const bool more = top - 32 >= qa;
+            const long long nq = q - 32;
+            const int4 nx = (more && nq >= qa) ? load4(p.ci, nq, p.m) : make_int4(0, 0, 0, 0);
+            const unsigned halt = __ldcg(stop);
+            int32_t my = -1;
+            if (q >= qa) {
+                const long long i0 = q << 2;
+                int cw[4];
+                bool ok[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const long long i = i0 + k;
-                const int32_t w = vb + elem(x, k);
-                ok[k] = i >= a && i < hi && (unsigned)w < (unsigned)p.n;
-                cw[k] = ok[k] ? __ldcg(p.colors + w) : 0;
-            }
+                for (int k = 0; k < 4; ++k) {
+                    const long long i = i0 + k;
+                    const int32_t w = vb + elem(x, k);
+                    ok[k] = i >= a && i < hi && (unsigned)w < (unsigned)p.n;
+                    cw[k] = ok[k] ? __ldcg(p.colors + w) : 0;
+                }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (!ok[k]) continue;
-                scanned++;
-                if (mag(cw[k]) == c) my = vb + elem(x, k);
+                for (int k = 0; k < 4; ++k) {
+                    if (!ok[k]) continue;
+                    scanned++;
+                    if (mag(cw[k]) == c) my = vb + elem(x, k);
+                }
             }
+            const unsigned bal = __ballot_sync(kFull, my >= 0);
+            if (bal) return __shfl_sync(kFull, my, __ffs(bal) - 1);
+            if (halt || !more) return -1;
+            top -= 32;
+            q = nq;
+            x = nx;
         }
-        const unsigned bal = __ballot_sync(kFull, my >= 0);
-        if (bal) return __shfl_sync(kFull, my, __ffs(bal) - 1);
-        if (halt) return -1;
+    } else {
+        const int lane = threadIdx.x & 31;
+        for (long long top = (hi - 1) >> 2; hi > a && top >= (a >> 2); top -= 32) {
+            const long long q = top - lane;
+            const bool in = q >= (a >> 2);
+            const int4 x = in ? load4(p.ci, q, p.m) : make_int4(0, 0, 0, 0);
+            const unsigned halt = __ldcg(stop);
+            int32_t my = -1;
+            if (in) {
+                const long long i0 = q << 2;
+                int cw[4];
+                bool ok[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const long long i = i0 + k;
+                    const int32_t w = vb + elem(x, k);
+                    ok[k] = i >= a && i < hi && (unsigned)w < (unsigned)p.n;
+                    cw[k] = ok[k] ? __ldcg(p.colors + w) : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!ok[k]) continue;
+                    scanned++;
+                    if (mag(cw[k]) == c) my = vb + elem(x, k);
+                }
+            }
+            const unsigned bal = __ballot_sync(kFull, my >= 0);
+            if (bal) return __shfl_sync(kFull, my, __ffs(bal) - 1);
+            if (halt) return -1;
+        }
+        return -1;
     }
-    return -1;
 }
 
 // Lane scan of the (at most) 16 entries of [s, hi) nearest below hi, all
@@ -1767,7 +1880,7 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
             const int c = __shfl_sync(kFull, cl, j);
             if ((open >> j) & 1u) {
                 // prefix: the part below the lane's entries; otherwise the whole row
-                const int32_t f = det_scan_warp<kBatched>(p, v, c, (int32_t)(e - s), s, s,
+                const int32_t f = det_scan_warp<kBatched, kMulti>(p, v, c, (int32_t)(e - s), s, s,
                                                           prefix ? rest : e, vb, prefix, nullptr, acc.dscan);
                 if (f >= 0) {
                     lost |= 1u << j;
@@ -1782,7 +1895,7 @@ __device__ void det_medium_detect(const Params &p, const int32_t *list, unsigned
                 acc.kdeg += (unsigned long long)(e - s);
                 acc.scatter += (unsigned long long)(e - s);
             }
-            scatter_color<kBatched>(p, c, s, e, vb, lane, 32, act_r, A);
+            scatter_color<kBatched, kMulti>(p, c, s, e, vb, lane, 32, act_r, A);
         }
         if (lost) {
             if (lane == 0) acc.next += (unsigned long long)__popc(lost);
@@ -1820,7 +1933,7 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
             const long long a = (long long)(((unsigned long long)r1.y << 32) | r1.x);
             const unsigned nchunks = r1.w;
             const Wit wo = (kMulti && lane == 0) ? wit_load(p, v) : wit_none();
-            const int32_t found = scan_range_down_warp(p, c, a, a + (long long)r1.z, vb, p.hconf + slot, acc.dscan);
+            const int32_t found = scan_range_down_warp<kMulti>(p, c, a, a + (long long)r1.z, vb, p.hconf + slot, acc.dscan);
             const bool conf = found >= 0;
             if (lane == 0) {
                 if (conf) {
@@ -1893,7 +2006,7 @@ __device__ void det_hub_detect(const Params &p, const int32_t *slots, const unsi
             }
         }
         if (!conf && !(round1 && prefix) && !__ldcg(p.hconf + slot)) {
-            const int32_t found = det_scan_warp<kBatched>(p, v, c, (int32_t)deg, s, a, b, vb, prefix,
+            const int32_t found = det_scan_warp<kBatched, kMulti>(p, v, c, (int32_t)deg, s, a, b, vb, prefix,
                                                           p.hconf + slot, acc.dscan);
             if (found >= 0) {
                 conf = true;
